@@ -1,0 +1,127 @@
+/*
+ * pfsp.h -- C ABI of the GB300 (sm_103a) permutation flow-shop branch-and-bound
+ * library: batched lower bounds for the children of many partial schedules,
+ * and a device-resident depth-first explorer pool that solves instances.
+ *
+ * Problem (Gmys, arXiv 2012.09511, Section 2.1): n jobs, m machines, integer
+ * processing times p[j][k]; find a permutation minimising the completion time
+ * of the last job on the last machine (Eq. 1 gives the completion times).
+ *
+ * General rules of every call:
+ *   - Every function returns PFSP_OK (0) or a negative PFSP_ERR_* code; on an
+ *     error nothing is written to the outputs and pfsp_last_error() holds a
+ *     one-line message for the calling thread.
+ *   - Host-pointer functions are synchronous: they return after the results
+ *     are in the caller's buffers.  Buffers are owned by the caller and only
+ *     read or written during the call.
+ *   - Functions with the _dev suffix take device pointers and a CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream); they only
+ *     enqueue work and return.  The caller keeps the buffers alive until the
+ *     stream has passed the work.
+ *   - Jobs and machines are numbered from 0.  p is job-major: p[j*m + k].
+ *   - Limits: 1 <= n <= 64, 1 <= m <= 32, 0 <= p[j][k] < 2^22 and the sum of
+ *     all p[j][k] below 2^28 (all bound arithmetic is int32 and exact);
+ *     otherwise PFSP_ERR_UNSUPPORTED.  LB2 also needs its per-pair tables to
+ *     fit in shared memory (m(m-1)/2 pairs x n jobs x 8 bytes <= 160 KiB).
+ *   - All calls act on the CUDA device that is current in the calling thread
+ *     when pfsp_load_instance runs; the instance lives on that device.
+ */
+#ifndef PFSP_H
+#define PFSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define PFSP_OK 0
+#define PFSP_ERR_INVALID (-1)      /* bad argument: NULL pointer, size, depth, negative time */
+#define PFSP_ERR_OOM (-2)          /* device or host allocation failed */
+#define PFSP_ERR_CUDA (-3)         /* a CUDA runtime call failed (message has the CUDA error) */
+#define PFSP_ERR_UNSUPPORTED (-4)  /* outside the limits above */
+#define PFSP_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up; the context stays usable */
+
+/* Outcome of a solve (not an error). */
+#define PFSP_OPTIMAL 0             /* search finished; best_cmax is optimal */
+#define PFSP_PROVEN_NO_BETTER 1    /* search finished; no schedule below init_ub exists */
+#define PFSP_LIMIT_NODES 2         /* stopped at node_limit; best_cmax is the best found */
+#define PFSP_LIMIT_TIME 3          /* stopped at time_limit_s; best_cmax is the best found */
+
+/* Bound kinds (bit mask for pfsp_bound_batch; a single value for solves). */
+#define PFSP_LB1 1   /* one-machine bound, Section 2.4 steps 1-4 */
+#define PFSP_LB2 2   /* two-machine Johnson bound over all m(m-1)/2 machine pairs, Section 2.4 */
+
+/* MinMin variants (Section 2.3). */
+#define PFSP_MINMIN 0          /* the paper's rule on the exact bounds of all children */
+#define PFSP_MINMIN_CAPPED 1   /* the same rule on min(bound, incumbent) */
+
+typedef struct pfsp_instance pfsp_instance; /* opaque, owned by the library */
+
+/*
+ * Load an instance (Section 2.1): copies p (n*m int32, job-major) and builds
+ * the device tables used by the bounds: processing times by machine, the
+ * per-machine totals, and for every machine pair k < l the Johnson order of
+ * the jobs on (p[j][k] + g_j, p[j][l] + g_j) with lag g_j the sum of job j's
+ * times on the machines strictly between k and l (Section 2.4, LB2 with
+ * pre-sorted Johnson schedules).  *out receives the new instance.
+ * Errors: PFSP_ERR_INVALID (NULL, n < 1, m < 1, negative time),
+ * PFSP_ERR_UNSUPPORTED (limits), PFSP_ERR_OOM, PFSP_ERR_CUDA.
+ */
+int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out);
+
+/* Release an instance and every device buffer it holds.  NULL is ignored. */
+void pfsp_free_instance(pfsp_instance *inst);
+
+/*
+ * Bounds of both children sets of num_nodes partial schedules (Sections 2.3
+ * and 2.4).  Node i is perm[i*n .. i*n+n-1] (a permutation of 0..n-1) with
+ * depths d1[i], d2[i], d1 + d2 <= n: positions [0, d1) hold sigma1 in order,
+ * positions [n-d2, n) hold sigma2 in order, the rest are unscheduled.
+ * For every unscheduled job j the forward child is (sigma1 j, sigma2) and the
+ * backward child is (sigma1, j sigma2).  Outputs are int32 arrays of
+ * num_nodes*2*n entries laid out [node][dir][job] (dir 0 = forward,
+ * 1 = backward); entries of scheduled jobs are -1.  kind is a bit mask of
+ * PFSP_LB1 | PFSP_LB2; the output of a kind not requested may be NULL and is
+ * not touched.  With m = 1 there is no machine pair and LB2 equals LB1.
+ * Bounds are exact int32 values, identical to their definitions.
+ * num_nodes = 0 is allowed and does nothing.
+ * Errors: PFSP_ERR_INVALID (NULL pointer for a requested output or input,
+ * d1 + d2 > n, kind not in 1..3), PFSP_ERR_UNSUPPORTED (LB2 tables too large),
+ * PFSP_ERR_OOM, PFSP_ERR_CUDA.
+ */
+int pfsp_bound_batch(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                     const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out);
+
+/* Same as pfsp_bound_batch on device buffers, enqueued on `stream`.  Depths
+ * are not validated on the device beyond clamping (a node with d1 + d2 > n
+ * gets all -1 outputs); the host variant validates them. */
+int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                         const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out,
+                         void *stream);
+
+/* Counters of the last pfsp_bound_batch / pfsp_solve call on an instance. */
+typedef struct {
+    uint64_t decomposed;       /* parents whose children were bounded (root counts 1) */
+    uint64_t bounded_children; /* children bounded: sum of 2(n - d1 - d2) over parents */
+    uint64_t leaves;           /* complete schedules evaluated */
+    uint64_t pruned;           /* children of the chosen direction discarded (bound >= incumbent) */
+    uint64_t steals;           /* successful device work-stealing operations */
+    uint64_t iterations;       /* explorer loop iterations summed over explorers */
+    double seconds;            /* wall time of the call (host clock) */
+    double kernel_seconds;     /* device time of the main kernel (CUDA events) */
+    int32_t final_ub;          /* incumbent at the end of a solve */
+    int32_t explorers;         /* explorers used by a solve */
+} pfsp_stats_t;
+
+int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
+
+/* Message of the last error in the calling thread ("" if none). */
+const char *pfsp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFSP_H */

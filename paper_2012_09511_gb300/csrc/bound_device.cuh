@@ -1,0 +1,340 @@
+// bound_device.cuh -- warp-level decomposition of one parent node: front,
+// back and remaining work (Section 2.4, steps 1-3), LB1 of all 2u children by
+// the incremental rule of Section 2.4, and LB2 of all children over all
+// machine pairs.
+//
+// LB2 per pair (k, l) runs the unscheduled jobs of the child, in the pair's
+// Johnson order, through  t0 += p_jk;  t1 = max(t1, t0 + g_j) + p_jl  from
+// (t0, t1) = (F_k, F_l) and takes max(t0 + B_k, t1 + B_l).  Written in the gap
+// u = t1 - t0, one job is the max-plus map  u -> max(u + a_j, b_j)  with
+// a_j = p_jl - p_jk and b_j = g_j + p_jl.  Maps of this form compose into a
+// map of the same form, (A1, B1) then (A2, B2) = (A1 + A2, max(B1 + A2, B2)),
+// so for the child that leaves out job j the composed map is the prefix of
+// the order before j followed by the suffix after it: its constant part is
+//     C_j = max(PB_j + SA_j, SB_j).
+// Expanding the pair value with it gives
+//     v_kl = max(F_k + R_k + B_k,  F_l + R_l + B_l,  F_k + R_k + C_j + B_l)
+// with F, R, B the child's front, remaining work and back.  The first two
+// terms, maximised over pairs, are exactly LB1 of the child (m >= 2), so
+//     LB2(child) = max(LB1(child), max_{k<l} (F_k + R_k + C_j(k,l) + B_l)).
+// All arithmetic is exact int32: the result is bit-identical to running the
+// recurrence job by job, at O(P u) work per parent instead of O(P u^2).
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "pfsp_internal.h"
+
+namespace pfsp {
+
+#define PFSP_FULL 0xffffffffu
+
+template <int NW>
+using umask_t = typename std::conditional<NW == 1, uint32_t, unsigned long long>::type;
+
+template <int NW>
+__device__ __forceinline__ bool has_job(umask_t<NW> U, int j) {
+    return (U >> j) & 1;
+}
+
+template <int NW>
+__device__ __forceinline__ umask_t<NW> low_bits(int j) {
+    return (umask_t<NW>(1) << j) - 1;
+}
+
+template <int NW>
+__device__ __forceinline__ int popcnt(umask_t<NW> x) {
+    if constexpr (NW == 1) return __popc(x);
+    else return __popcll(x);
+}
+
+// Shared-memory views of one CTA's instance tables.
+struct SmemTables {
+    const int *pm;    // [m][nj]
+    const int *tot;   // [32]
+    const int *kl;    // [S*32]
+    const int2 *ptab; // [S][n][32]
+};
+
+// Per-warp scratch layout (int32 words); see warp_words().
+struct WarpScratch {
+    int *F, *R, *B;   // [32] each: parent front, remaining work, back
+    int *ul;          // [64] compact list of unscheduled jobs
+    int *Gf;          // [n][mp] forward child: F'_k + R_k - p_jk
+    int *Gb;          // [n][mp] backward child: F_k + R_k - p_jk
+    int *Bb;          // [n][mp] backward child back B'_k
+    int *PB;          // [n][32] prefix map constants by position (per lane)
+    int *Cb;          // [n][32] C_j per job (per lane); PB..Cb doubles as int2 [n][32]
+    int *Acc;         // [n][32] int2 accumulators (only when not kept in registers)
+};
+
+// Every region starts on a multiple of 4 words (16 bytes) so that the int2
+// views of PB..Cb and Acc are aligned whatever n and m are.
+__host__ __device__ inline int round4(int w) { return (w + 3) & ~3; }
+
+// LB1 alone uses only F, R, B and the compact list (the first 160 words).
+__host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2) {
+    if (!lb2) return 160;
+    int g = round4(n * (m | 1));
+    return 160 + 3 * g + 2 * n * 32 + (smem_acc ? 2 * n * 32 : 0);
+}
+
+__device__ inline WarpScratch carve_warp(int *base, int n, int m) {
+    int g = round4(n * (m | 1));
+    WarpScratch w;
+    w.F = base;
+    w.R = base + 32;
+    w.B = base + 64;
+    w.ul = base + 96;
+    w.Gf = base + 160;
+    w.Gb = w.Gf + g;
+    w.Bb = w.Gb + g;
+    w.PB = w.Bb + g;
+    w.Cb = w.PB + n * 32;
+    w.Acc = w.Cb + n * 32;
+    return w;
+}
+
+// Result of one decomposition, distributed over lanes: lane c (and c + 32)
+// holds the bounds of the children of compact index c (the c-th unscheduled
+// job in ascending id order).
+template <int NW>
+struct ChildBounds {
+    umask_t<NW> U;  // unscheduled jobs
+    int u;          // number of unscheduled jobs
+    int lb1f[NW], lb1b[NW];
+    int lb2f[NW], lb2b[NW];
+};
+
+// Decompose the node whose permutation entries are held one per lane
+// (job0 = position lane, job1 = position lane + 32) with depths d1, d2.
+// kind: bit 0 = LB1 wanted, bit 1 = LB2 wanted.  All 32 lanes must call.
+template <int NW, bool REGACC>
+__device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m,
+                                               int S, int kind, int job0, int job1, int d1, int d2,
+                                               ChildBounds<NW> &out) {
+    using mask_t = umask_t<NW>;
+    const int lane = threadIdx.x & 31;
+    const int mp = m | 1;
+    const int nj = (n + 3) & ~3;
+
+    // ---- unscheduled set and its compact list --------------------------------
+    bool un0 = lane < n && lane >= d1 && lane < n - d2;
+    bool un1 = (NW == 2) && (lane + 32 < n) && (lane + 32 >= d1) && (lane + 32 < n - d2);
+    mask_t mine = (un0 ? (mask_t(1) << job0) : mask_t(0));
+    if constexpr (NW == 2) mine |= (un1 ? (mask_t(1) << job1) : mask_t(0));
+    mask_t U;
+    if constexpr (NW == 1) {
+        U = __reduce_or_sync(PFSP_FULL, mine);
+    } else {
+        unsigned lo = __reduce_or_sync(PFSP_FULL, (unsigned)(mine & 0xffffffffull));
+        unsigned hi = __reduce_or_sync(PFSP_FULL, (unsigned)(mine >> 32));
+        U = ((mask_t)hi << 32) | lo;
+    }
+    const int u = popcnt<NW>(U);
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        int j = lane + 32 * h;
+        if (j < n && has_job<NW>(U, j)) W.ul[popcnt<NW>(U & low_bits<NW>(j))] = j;
+    }
+
+    // ---- step 1: front (Eq. 1 over sigma1) as a wavefront over machines -------
+    int Fk = 0, Sk = 0;
+    {
+        int steps = d1 > 0 ? d1 + m - 1 : 0;
+        for (int s = 0; s < steps; ++s) {
+            int i = s - lane;
+            int left = __shfl_up_sync(PFSP_FULL, Fk, 1);
+            if (lane == 0) left = 0;
+            int ja = __shfl_sync(PFSP_FULL, job0, i & 31);
+            int j = ja;
+            if constexpr (NW == 2) {
+                int jb = __shfl_sync(PFSP_FULL, job1, i & 31);
+                j = i >= 32 ? jb : ja;
+            }
+            if (lane < m && i >= 0 && i < d1) {
+                int pk = T.pm[lane * nj + j];
+                Fk = max(Fk, left) + pk;
+                Sk += pk;
+            }
+        }
+    }
+    // ---- step 3: back (reversed sigma2 on reversed machines) ------------------
+    int Bk = 0;
+    {
+        int steps = d2 > 0 ? d2 + m - 1 : 0;
+        int r = m - 1 - lane;
+        for (int s = 0; s < steps; ++s) {
+            int i = s - r;
+            int right = __shfl_down_sync(PFSP_FULL, Bk, 1);
+            if (lane == m - 1) right = 0;
+            int pos = n - 1 - i;
+            int ja = __shfl_sync(PFSP_FULL, job0, pos & 31);
+            int j = ja;
+            if constexpr (NW == 2) {
+                int jb = __shfl_sync(PFSP_FULL, job1, pos & 31);
+                j = pos >= 32 ? jb : ja;
+            }
+            if (lane < m && i >= 0 && i < d2) {
+                int pk = T.pm[lane * nj + j];
+                Bk = max(Bk, right) + pk;
+                Sk += pk;
+            }
+        }
+    }
+    // ---- step 2: remaining work = totals minus scheduled work -----------------
+    if (lane < m) {
+        W.F[lane] = Fk;
+        W.R[lane] = T.tot[lane] - Sk;
+        W.B[lane] = Bk;
+    }
+    __syncwarp();
+
+    // ---- LB1 of all children, incrementally from the parent (Section 2.4) -----
+    const bool want2 = (kind & PFSP_LB2) && m >= 2;
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        out.lb1f[h] = kNegInf;
+        out.lb1b[h] = kNegInf;
+        int c = lane + 32 * h;
+        if (c < u) {
+            int j = W.ul[c];
+            int f = 0, lf = kNegInf;
+            for (int k = 0; k < m; ++k) {
+                int pk = T.pm[k * nj + j];
+                f = max(f, W.F[k]) + pk;
+                int g = f + W.R[k] - pk;
+                lf = max(lf, g + W.B[k]);
+                if (want2) W.Gf[c * mp + k] = g;
+            }
+            int b = 0, lb = kNegInf;
+            for (int k = m - 1; k >= 0; --k) {
+                int pk = T.pm[k * nj + j];
+                b = max(b, W.B[k]) + pk;
+                int g = W.F[k] + W.R[k] - pk;
+                lb = max(lb, g + b);
+                if (want2) {
+                    W.Gb[c * mp + k] = g;
+                    W.Bb[c * mp + k] = b;
+                }
+            }
+            out.lb1f[h] = lf;
+            out.lb1b[h] = lb;
+        }
+        out.lb2f[h] = out.lb1f[h];
+        out.lb2b[h] = out.lb1b[h];
+    }
+    out.U = U;
+    out.u = u;
+
+    if (!want2 || u == 0) return;
+    __syncwarp();
+
+    // ---- LB2: lanes = machine pairs, S slots of 32 pairs ----------------------
+    int accf[REGACC ? 32 : 1], accb[REGACC ? 32 : 1];
+    if constexpr (REGACC) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) { accf[c] = kNegInf; accb[c] = kNegInf; }
+    } else {
+        int2 *A = reinterpret_cast<int2 *>(W.Acc);
+        for (int c = 0; c < u; ++c) A[c * 32 + lane] = make_int2(kNegInf, kNegInf);
+    }
+    for (int s = 0; s < S; ++s) {
+        const int klw = T.kl[s * 32 + lane];
+        const int k = klw & 0xff, l = klw >> 8;
+        const bool real = l > 0;  // lanes past the last pair of the last slot hold no pair
+        const int Bl = W.B[l];
+        const int2 *pt = T.ptab + (size_t)s * n * 32 + lane;
+        // pass 1: prefix constants PB before each position of the order
+        int PB = kNegInf;
+#pragma unroll 4
+        for (int t = 0; t < n; ++t) {
+            int2 e = pt[t * 32];
+            int j = e.x & 0xff;
+            W.PB[t * 32 + lane] = PB;
+            int nb = max(PB + (e.x >> 8), e.y);
+            PB = has_job<NW>(U, j) ? nb : PB;
+        }
+        // pass 2: suffix maps (SA, SB) and C_j of every unscheduled job j
+        int SA = 0, SB = kNegInf;
+#pragma unroll 4
+        for (int t = n - 1; t >= 0; --t) {
+            int2 e = pt[t * 32];
+            int j = e.x & 0xff;
+            if (has_job<NW>(U, j)) {
+                int C = max(W.PB[t * 32 + lane] + SA, SB);
+                W.Cb[j * 32 + lane] = C;
+                SB = max(e.y + SA, SB);
+                SA += e.x >> 8;
+            }
+        }
+        // evaluation: the third pair term of every child of this parent
+        if constexpr (REGACC) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c >= u) break;
+                int j = W.ul[c];
+                int C = real ? W.Cb[j * 32 + lane] : kNegInf;
+                int ef = W.Gf[c * mp + k] + C + Bl;
+                int eb = W.Gb[c * mp + k] + C + W.Bb[c * mp + l];
+                accf[c] = max(accf[c], ef);
+                accb[c] = max(accb[c], eb);
+            }
+        } else {
+            int2 *A = reinterpret_cast<int2 *>(W.Acc);
+            for (int c = 0; c < u; ++c) {
+                int j = W.ul[c];
+                int C = real ? W.Cb[j * 32 + lane] : kNegInf;
+                int ef = W.Gf[c * mp + k] + C + Bl;
+                int eb = W.Gb[c * mp + k] + C + W.Bb[c * mp + l];
+                int2 v = A[c * 32 + lane];
+                v.x = max(v.x, ef);
+                v.y = max(v.y, eb);
+                A[c * 32 + lane] = v;
+            }
+        }
+    }
+    // ---- max over lanes (pairs) per child: skewed transpose through smem ------
+    __syncwarp();
+    int2 *X = reinterpret_cast<int2 *>(W.PB);  // [n][32], aliases PB and Cb
+    if constexpr (REGACC) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (c >= u) break;
+            X[c * 32 + ((lane + c) & 31)] = make_int2(accf[c], accb[c]);
+        }
+    } else {
+        const int2 *A = reinterpret_cast<const int2 *>(W.Acc);
+        for (int c = 0; c < u; ++c) X[c * 32 + ((lane + c) & 31)] = A[c * 32 + lane];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        int c = lane + 32 * h;
+        if (c < u) {
+            int mf = kNegInf, mb = kNegInf;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                int2 v = X[c * 32 + ((i + c) & 31)];
+                mf = max(mf, v.x);
+                mb = max(mb, v.y);
+            }
+            out.lb2f[h] = max(out.lb1f[h], mf);
+            out.lb2b[h] = max(out.lb1b[h], mb);
+        }
+    }
+}
+
+// Value of child compact index c held by lanes (c & 31) of register h = c >> 5.
+template <int NW>
+__device__ __forceinline__ int gather_child(const int (&v)[NW], int c) {
+    int a = __shfl_sync(PFSP_FULL, v[0], c & 31);
+    if constexpr (NW == 2) {
+        int b = __shfl_sync(PFSP_FULL, v[1], c & 31);
+        return c >= 32 ? b : a;
+    }
+    return a;
+}
+
+}  // namespace pfsp

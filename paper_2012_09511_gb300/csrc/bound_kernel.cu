@@ -1,0 +1,216 @@
+// bound_kernel.cu -- batched bounding of the children of many partial
+// schedules (the bounding operator of Sections 2.3-2.4 applied to a batch).
+//
+// One warp decomposes one parent at a time; the grid is persistent (a whole
+// number of CTAs per SM) and walks the batch with a warp-stride loop.  Each
+// CTA stages the instance tables (processing times by machine, machine
+// totals, per-pair Johnson tables) into shared memory once with a bulk copy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bound_device.cuh"
+#include "pfsp_internal.h"
+
+namespace pfsp {
+
+struct BoundArgs {
+    const uint8_t *perm, *d1, *d2;
+    int32_t *lb1, *lb2;
+    long long num_nodes;
+    const int32_t *tab;
+    int tab_words;
+    int n, m, S;
+    int off_pm, off_tot, off_kl, off_ptab;
+    int warp_words;
+    int kind;
+};
+
+// Stage `words` int32 (a multiple of 4, 16-byte aligned on both sides) from
+// global into shared memory with the bulk-copy engine, completion tracked by
+// an mbarrier.  The wait is bounded; on expiry the block falls back to plain
+// loads so that no thread can wait forever.
+__device__ inline void stage_tables(int *dst, const int32_t *src, int words, uint64_t *bar) {
+    const unsigned bytes = (unsigned)words * 4u;
+    const unsigned sbar = (unsigned)__cvta_generic_to_shared(bar);
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(bytes)
+                     : "memory");
+        const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+        // copies of at most 64 KiB - 16 bytes each
+        unsigned done = 0;
+        while (done < bytes) {
+            unsigned chunk = min(bytes - done, 65536u - 16u);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    sdst + done),
+                "l"(reinterpret_cast<const char *>(src) + done), "r"(chunk), "r"(sbar)
+                : "memory");
+            done += chunk;
+        }
+    }
+    // phase 0 completes when all bytes have landed
+    unsigned ready = 0;
+    for (int it = 0; it < (1 << 22) && !ready; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ready)
+            : "r"(sbar)
+            : "memory");
+    }
+    ok = ready != 0;
+    if (!__syncthreads_and(ok)) {
+        // bounded wait expired (never expected): copy with plain loads instead
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+}
+
+template <int NW, bool REGACC>
+__global__ void __launch_bounds__(256) bound_batch_kernel(BoundArgs a) {
+    extern __shared__ __align__(16) int smem[];
+    __shared__ uint64_t bar;
+    stage_tables(smem, a.tab, a.tab_words, &bar);
+
+    SmemTables T;
+    T.pm = smem + a.off_pm;
+    T.tot = smem + a.off_tot;
+    T.kl = smem + a.off_kl;
+    T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int n = a.n, m = a.m;
+    WarpScratch W = carve_warp(smem + a.tab_words + wib * a.warp_words, n, m);
+
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long node = (long long)blockIdx.x * (blockDim.x >> 5) + wib; node < a.num_nodes; node += nwarps) {
+        int d1 = a.d1[node], d2 = a.d2[node];
+        const uint8_t *pr = a.perm + node * n;
+        int job0 = lane < n ? pr[lane] : 0;
+        int job1 = (NW == 2 && lane + 32 < n) ? pr[lane + 32] : 0;
+        job0 = job0 < n ? job0 : 0;  // keep indexes in range on malformed rows
+        job1 = job1 < n ? job1 : 0;
+        int32_t *o1 = a.lb1 ? a.lb1 + node * 2 * n : nullptr;
+        int32_t *o2 = a.lb2 ? a.lb2 + node * 2 * n : nullptr;
+        if (d1 + d2 > n) {
+            for (int i = lane; i < 2 * n; i += 32) {
+                if (o1) o1[i] = -1;
+                if (o2) o2[i] = -1;
+            }
+            continue;
+        }
+        ChildBounds<NW> cb;
+        decompose_node<NW, REGACC>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+            int j = lane + 32 * h;
+            bool in = j < n && has_job<NW>(cb.U, j);
+            int c = in ? popcnt<NW>(cb.U & low_bits<NW>(j)) : 0;
+            int v1f = gather_child<NW>(cb.lb1f, c), v1b = gather_child<NW>(cb.lb1b, c);
+            int v2f = gather_child<NW>(cb.lb2f, c), v2b = gather_child<NW>(cb.lb2b, c);
+            if (j < n) {
+                if (o1 && (a.kind & PFSP_LB1)) {
+                    o1[j] = in ? v1f : -1;
+                    o1[n + j] = in ? v1b : -1;
+                }
+                if (o2 && (a.kind & PFSP_LB2)) {
+                    o2[j] = in ? v2f : -1;
+                    o2[n + j] = in ? v2b : -1;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+static int g_num_sms = 0;
+
+static int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+static int g_smem_optin = 0;
+
+static int smem_optin() {
+    if (g_smem_optin == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (g_smem_optin <= 0) g_smem_optin = 48 * 1024;
+    }
+    return g_smem_optin;
+}
+
+// Warps per CTA: up to `want`, as many as the shared-memory cap allows.
+static int fit_warps(const BoundArgs &a, int want) {
+    long long avail = (long long)smem_optin() - 64 - (long long)a.tab_words * 4;
+    long long w = avail / ((long long)a.warp_words * 4);
+    return (int)std::max<long long>(0, std::min<long long>(want, w));
+}
+
+template <int NW, bool REGACC>
+static cudaError_t launch_t(const BoundArgs &a, int want_warps, cudaStream_t stream) {
+    const int warps = fit_warps(a, want_warps);
+    if (warps < 1) return cudaErrorInvalidConfiguration;
+    size_t smem = (size_t)(a.tab_words + warps * a.warp_words) * 4;
+    auto kern = bound_batch_kernel<NW, REGACC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long blocks_needed = (a.num_nodes + warps - 1) / warps;
+    long long grid = std::min<long long>((long long)num_sms() * per_sm, blocks_needed);
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, warps * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long num_nodes, const uint8_t *perm,
+                               const uint8_t *d1, const uint8_t *d2, int32_t *lb1, int32_t *lb2,
+                               cudaStream_t stream) {
+    if (num_nodes <= 0) return cudaSuccess;
+    const TableLayout &L = inst->lay;
+    BoundArgs a;
+    a.perm = perm;
+    a.d1 = d1;
+    a.d2 = d2;
+    a.lb1 = lb1;
+    a.lb2 = lb2;
+    a.num_nodes = num_nodes;
+    a.tab = inst->d_tab;
+    // LB1 alone needs only the processing times, totals and pair indexes
+    a.tab_words = (kind & PFSP_LB2) ? L.words : L.off_ptab;
+    a.n = L.n;
+    a.m = L.m;
+    a.S = (kind & PFSP_LB2) ? L.S : 0;
+    a.off_pm = L.off_pm;
+    a.off_tot = L.off_tot;
+    a.off_kl = L.off_kl;
+    a.off_ptab = L.off_ptab;
+    a.kind = kind;
+    const int warps = 8;
+    const bool want2 = (kind & PFSP_LB2) && L.m >= 2;
+    if (L.n <= 32) {
+        a.warp_words = warp_words(L.n, L.m, false, want2);
+        return launch_t<1, true>(a, warps, stream);
+    }
+    a.warp_words = warp_words(L.n, L.m, true, want2);
+    return launch_t<2, false>(a, warps, stream);
+}
+
+}  // namespace pfsp

@@ -1,0 +1,268 @@
+// capi.cu -- the library's C ABI: instance loading (with the host-built
+// LB2 tables), batched bounding entry points, statistics and error messages.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "bound_device.cuh"
+#include "pfsp_internal.h"
+
+namespace pfsp {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+TableLayout table_layout(int n, int m) {
+    TableLayout L;
+    L.n = n;
+    L.m = m;
+    L.P = m * (m - 1) / 2;
+    L.S = (L.P + 31) / 32;
+    L.nj = (n + 3) & ~3;
+    L.off_pm = 0;
+    L.off_tot = L.off_pm + m * L.nj;
+    L.off_kl = L.off_tot + 32;
+    L.off_ptab = L.off_kl + L.S * 32;
+    L.words = L.off_ptab + 2 * L.S * n * 32;
+    return L;
+}
+
+// Johnson's rule extended to time lags (Mitten) for the pair (k, l): jobs
+// with p_jk <= p_jl first by ascending p_jk + g_j, then the rest by
+// descending p_jl + g_j; ties by ascending job id (Section 2.4, LB2).
+static std::vector<int> johnson_lag_order(int n, int m, const int32_t *p, int k, int l,
+                                          const std::vector<int> &lag) {
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    auto first = [&](int j) { return p[j * m + k] <= p[j * m + l]; };
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+        bool fx = first(x), fy = first(y);
+        if (fx != fy) return fx;
+        if (fx) {
+            int kx = p[x * m + k] + lag[x], ky = p[y * m + k] + lag[y];
+            if (kx != ky) return kx < ky;
+        } else {
+            int kx = p[x * m + l] + lag[x], ky = p[y * m + l] + lag[y];
+            if (kx != ky) return kx > ky;
+        }
+        return x < y;
+    });
+    return ord;
+}
+
+static void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob) {
+    const int n = L.n, m = L.m;
+    blob.assign(L.words, 0);
+    for (int k = 0; k < m; ++k)
+        for (int j = 0; j < n; ++j) blob[L.off_pm + k * L.nj + j] = p[j * m + k];
+    for (int k = 0; k < m; ++k) {
+        int32_t t = 0;
+        for (int j = 0; j < n; ++j) t += p[j * m + k];
+        blob[L.off_tot + k] = t;
+    }
+    int2 *ptab = reinterpret_cast<int2 *>(blob.data() + L.off_ptab);
+    for (int s = 0; s < L.S; ++s)
+        for (int t = 0; t < n; ++t)
+            for (int lane = 0; lane < 32; ++lane) ptab[(s * n + t) * 32 + lane] = make_int2(0, kNegInf);
+    int q = 0;
+    std::vector<int> lag(n);
+    for (int k = 0; k < m; ++k)
+        for (int l = k + 1; l < m; ++l, ++q) {
+            const int s = q / 32, lane = q % 32;
+            blob[L.off_kl + q] = k | (l << 8);
+            for (int j = 0; j < n; ++j) {
+                int g = 0;
+                for (int r = k + 1; r < l; ++r) g += p[j * m + r];
+                lag[j] = g;
+            }
+            std::vector<int> ord = johnson_lag_order(n, m, p, k, l, lag);
+            for (int t = 0; t < n; ++t) {
+                int j = ord[t];
+                int a = p[j * m + l] - p[j * m + k];
+                int b = lag[j] + p[j * m + l];
+                ptab[(s * n + t) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
+            }
+        }
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return set_error(PFSP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int ensure_scratch(pfsp_instance *inst, size_t bytes) {
+    if (inst->scratch_bytes >= bytes) return PFSP_OK;
+    if (inst->d_scratch) cudaFree(inst->d_scratch);
+    inst->d_scratch = nullptr;
+    inst->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&inst->d_scratch, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PFSP_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    inst->scratch_bytes = bytes;
+    return PFSP_OK;
+}
+
+static int check_bound_args(const pfsp_instance *inst, int kind, int64_t num_nodes, const void *perm,
+                            const void *d1, const void *d2, const void *lb1, const void *lb2) {
+    if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
+    if (kind < 1 || kind > 3) return set_error(PFSP_ERR_INVALID, "kind must be a non-empty mask of LB1|LB2");
+    if (num_nodes < 0) return set_error(PFSP_ERR_INVALID, "num_nodes < 0");
+    if (num_nodes == 0) return PFSP_OK;
+    if (!perm || !d1 || !d2) return set_error(PFSP_ERR_INVALID, "NULL node input");
+    if ((kind & PFSP_LB1) && !lb1) return set_error(PFSP_ERR_INVALID, "LB1 requested but lb1_out is NULL");
+    if ((kind & PFSP_LB2) && !lb2) return set_error(PFSP_ERR_INVALID, "LB2 requested but lb2_out is NULL");
+    if ((kind & PFSP_LB2) && !inst->lb2_ok)
+        return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables of %d pairs x %d jobs exceed shared memory",
+                         inst->lay.P, inst->n);
+    return PFSP_OK;
+}
+
+}  // namespace pfsp
+
+using namespace pfsp;
+
+extern "C" {
+
+const char *pfsp_last_error(void) { return g_err; }
+
+int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out) {
+    g_err[0] = 0;
+    if (!p || !out) return set_error(PFSP_ERR_INVALID, "NULL argument");
+    if (n < 1 || m < 1) return set_error(PFSP_ERR_INVALID, "n and m must be >= 1 (n=%d, m=%d)", n, m);
+    if (n > kMaxJobs || m > kMaxMachines)
+        return set_error(PFSP_ERR_UNSUPPORTED, "n <= %d and m <= %d required (n=%d, m=%d)", kMaxJobs,
+                         kMaxMachines, n, m);
+    long long total = 0;
+    for (long long i = 0; i < (long long)n * m; ++i) {
+        if (p[i] < 0) return set_error(PFSP_ERR_INVALID, "negative processing time at index %lld", i);
+        if (p[i] > kMaxTime) return set_error(PFSP_ERR_UNSUPPORTED, "processing time above 2^22-1 at %lld", i);
+        total += p[i];
+    }
+    if (total >= kMaxTotal) return set_error(PFSP_ERR_UNSUPPORTED, "sum of processing times >= 2^28");
+
+    pfsp_instance *inst = (pfsp_instance *)calloc(1, sizeof(pfsp_instance));
+    if (!inst) return set_error(PFSP_ERR_OOM, "host allocation failed");
+    inst->n = n;
+    inst->m = m;
+    cudaGetDevice(&inst->device);
+    inst->p_host = (int32_t *)malloc(sizeof(int32_t) * n * m);
+    if (!inst->p_host) {
+        free(inst);
+        return set_error(PFSP_ERR_OOM, "host allocation failed");
+    }
+    memcpy(inst->p_host, p, sizeof(int32_t) * n * m);
+    inst->lay = table_layout(n, m);
+    inst->lb2_ok = (size_t)inst->lay.words * 4 <= (size_t)kMaxTableBytes;
+    std::vector<int32_t> blob;
+    build_tables(inst->lay, p, blob);
+    cudaError_t e = cudaMalloc(&inst->d_tab, blob.size() * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free(inst->p_host);
+        free(inst);
+        return set_error(PFSP_ERR_OOM, "cudaMalloc of instance tables failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(inst->d_tab, blob.data(), blob.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(inst->d_tab);
+        free(inst->p_host);
+        free(inst);
+        return cuda_fail(e, "upload of instance tables");
+    }
+    *out = inst;
+    return PFSP_OK;
+}
+
+void pfsp_free_instance(pfsp_instance *inst) {
+    if (!inst) return;
+    if (inst->d_tab) cudaFree(inst->d_tab);
+    if (inst->d_scratch) cudaFree(inst->d_scratch);
+    free(inst->p_host);
+    free(inst);
+}
+
+int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                         const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out, void *stream) {
+    g_err[0] = 0;
+    int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out);
+    if (rc != PFSP_OK || num_nodes == 0) return rc;
+    cudaError_t e = launch_bound_batch(inst, kind, num_nodes, perm, d1, d2, (kind & PFSP_LB1) ? lb1_out : nullptr,
+                                       (kind & PFSP_LB2) ? lb2_out : nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bound kernel launch");
+    return PFSP_OK;
+}
+
+int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, const uint8_t *perm,
+                     const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out) {
+    g_err[0] = 0;
+    pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
+    int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out);
+    if (rc != PFSP_OK) return rc;
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = inst->n;
+    for (int64_t i = 0; i < num_nodes; ++i)
+        if ((int)d1[i] + (int)d2[i] > n)
+            return set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i], n);
+    if (num_nodes == 0) return PFSP_OK;
+    const size_t in_bytes = (size_t)num_nodes * (n + 2);
+    const size_t out_bytes = (size_t)num_nodes * 2 * n * sizeof(int32_t);
+    const size_t off_out1 = (in_bytes + 255) & ~(size_t)255;
+    const size_t off_out2 = off_out1 + (((kind & PFSP_LB1) ? out_bytes : 0) + 255) / 256 * 256;
+    rc = ensure_scratch(inst, off_out2 + ((kind & PFSP_LB2) ? out_bytes : 0));
+    if (rc != PFSP_OK) return rc;
+    char *base = (char *)inst->d_scratch;
+    uint8_t *dperm = (uint8_t *)base;
+    uint8_t *dd1 = dperm + (size_t)num_nodes * n;
+    uint8_t *dd2 = dd1 + num_nodes;
+    int32_t *o1 = (kind & PFSP_LB1) ? (int32_t *)(base + off_out1) : nullptr;
+    int32_t *o2 = (kind & PFSP_LB2) ? (int32_t *)(base + off_out2) : nullptr;
+    cudaStream_t st = 0;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaError_t e = cudaMemcpyAsync(dperm, perm, (size_t)num_nodes * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1, num_nodes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2, num_nodes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) e = launch_bound_batch(inst, kind, num_nodes, dperm, dd1, dd2, o1, o2, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess && o1) e = cudaMemcpyAsync(lb1_out, o1, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && o2) e = cudaMemcpyAsync(lb2_out, o2, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "pfsp_bound_batch");
+    memset(&inst->stats, 0, sizeof(inst->stats));
+    uint64_t children = 0;
+    for (int64_t i = 0; i < num_nodes; ++i) children += 2 * (uint64_t)(n - d1[i] - d2[i]);
+    inst->stats.decomposed = (uint64_t)num_nodes;
+    inst->stats.bounded_children = children;
+    inst->stats.kernel_seconds = ms * 1e-3;
+    inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PFSP_OK;
+}
+
+int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out) {
+    if (!inst || !out) return set_error(PFSP_ERR_INVALID, "NULL argument");
+    *out = inst->stats;
+    return PFSP_OK;
+}
+
+}  // extern "C"

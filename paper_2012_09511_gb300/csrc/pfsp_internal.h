@@ -1,0 +1,61 @@
+// pfsp_internal.h -- host/device layout shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pfsp.h"
+
+namespace pfsp {
+
+constexpr int kMaxJobs = 64;
+constexpr int kMaxMachines = 32;
+constexpr int kNegInf = -(1 << 29);         // "minus infinity" of the max-plus maps
+constexpr int kMaxTime = (1 << 22) - 1;     // largest accepted processing time
+constexpr long long kMaxTotal = 1LL << 28;  // largest accepted sum of all times
+constexpr int kMaxTableBytes = 160 * 1024;  // LB2 tables must fit in shared memory
+
+// Instance tables, one contiguous int32 blob in device memory that every CTA
+// copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):
+//   pm   [m][nj]       processing times by machine (nj = n rounded up to 4)
+//   tot  [32]          per-machine totals T_k = sum_j p[j][k]
+//   kl   [S*32]        machine pair of pair slot q: k | l << 8 (dummy: 0)
+//   ptab [S][n][32]    int2 per (slot, position, lane): pair q = slot*32+lane,
+//                      x = (a << 8) | job, y = b, for the job at that position
+//                      of the pair's Johnson order, with a = p[j][l] - p[j][k]
+//                      and b = g_j + p[j][l] (g_j = lag).  Dummy lanes hold
+//                      job 0 with a = 0, b = kNegInf (the identity map).
+struct TableLayout {
+    int n, m, P, S, nj;
+    int off_pm, off_tot, off_kl, off_ptab, words;
+};
+
+TableLayout table_layout(int n, int m);
+
+}  // namespace pfsp
+
+struct pfsp_instance {
+    int n, m;
+    int device;
+    int32_t *p_host;             // n*m job-major copy
+    pfsp::TableLayout lay;
+    int32_t *d_tab;              // device table blob (lay.words int32)
+    bool lb2_ok;                 // LB2 tables fit in shared memory
+    // grow-only device scratch of the host-pointer entry points
+    void *d_scratch;
+    size_t scratch_bytes;
+    pfsp_stats_t stats;
+};
+
+namespace pfsp {
+
+// Kernel launchers (bound_kernel.cu).  Return cudaError_t of the launch.
+cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long num_nodes,
+                               const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
+                               int32_t *lb1, int32_t *lb2, cudaStream_t stream);
+
+// Error reporting shared by the C-ABI translation units.
+int set_error(int code, const char *fmt, ...);
+
+}  // namespace pfsp

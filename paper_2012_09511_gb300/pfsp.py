@@ -1,0 +1,155 @@
+"""Thin Python binding of the C ABI in include/pfsp.h (ctypes; marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: all bounding and searching runs in the CUDA library
+libpfsp_gb300.so.  If that library is missing, importing this module fails
+loudly; there is no CPU fallback.
+
+Host-pointer entry points take numpy arrays; the _dev entry points take device
+addresses (e.g. torch.Tensor.data_ptr()) and a stream handle
+(torch.cuda.Stream.cuda_stream), both as Python ints.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpfsp_gb300.so")
+
+PFSP_OK = 0
+PFSP_ERR_INVALID = -1
+PFSP_ERR_OOM = -2
+PFSP_ERR_CUDA = -3
+PFSP_ERR_UNSUPPORTED = -4
+PFSP_ERR_TIMEOUT = -5
+PFSP_OPTIMAL = 0
+PFSP_PROVEN_NO_BETTER = 1
+PFSP_LIMIT_NODES = 2
+PFSP_LIMIT_TIME = 3
+PFSP_LB1 = 1
+PFSP_LB2 = 2
+PFSP_MINMIN = 0
+PFSP_MINMIN_CAPPED = 1
+INT32_MAX = 2**31 - 1
+
+
+class PfspError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pfsp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class pfsp_stats_t(ctypes.Structure):
+    _fields_ = [("decomposed", ctypes.c_uint64), ("bounded_children", ctypes.c_uint64),
+                ("leaves", ctypes.c_uint64), ("pruned", ctypes.c_uint64), ("steals", ctypes.c_uint64),
+                ("iterations", ctypes.c_uint64), ("seconds", ctypes.c_double),
+                ("kernel_seconds", ctypes.c_double), ("final_ub", ctypes.c_int32),
+                ("explorers", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpfsp_gb300.so is not built (run __graft_entry__.build()); "
+                      "the library has no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_lib.pfsp_last_error.restype = ctypes.c_char_p
+_lib.pfsp_last_error.argtypes = []
+_lib.pfsp_load_instance.restype = ctypes.c_int
+_lib.pfsp_load_instance.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.pfsp_free_instance.restype = None
+_lib.pfsp_free_instance.argtypes = [_vp]
+_lib.pfsp_bound_batch.restype = ctypes.c_int
+_lib.pfsp_bound_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+_lib.pfsp_bound_batch_dev.restype = ctypes.c_int
+_lib.pfsp_bound_batch_dev.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pfsp_stats.restype = ctypes.c_int
+_lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
+
+
+def lib():
+    """The loaded ctypes library (for symbol checks and extensions)."""
+    return _lib
+
+
+def pfsp_last_error() -> str:
+    return _lib.pfsp_last_error().decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise PfspError(rc, pfsp_last_error())
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_vp) if a is not None else None
+
+
+class Instance:
+    """Owner of a pfsp_instance handle; frees it on close or garbage collection."""
+
+    def __init__(self, handle, n, m):
+        self.handle = handle
+        self.n = n
+        self.m = m
+
+    def close(self):
+        if self.handle:
+            _lib.pfsp_free_instance(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pfsp_load_instance(p) -> Instance:
+    """p: int array [n, m] (job-major)."""
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    n, m = p.shape
+    h = _vp()
+    _check(_lib.pfsp_load_instance(n, m, _ptr(p), ctypes.byref(h)))
+    return Instance(h, n, m)
+
+
+def pfsp_free_instance(inst: Instance) -> None:
+    inst.close()
+
+
+def pfsp_bound_batch(inst: Instance, kind, perm, d1, d2, lb1_out=None, lb2_out=None):
+    """Host buffers: perm uint8 [N, n], d1/d2 uint8 [N].  Returns (lb1, lb2), each int32
+    [N, 2, n] or None when not requested."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+    d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+    N = len(d1)
+    n = inst.n
+    if kind & PFSP_LB1 and lb1_out is None:
+        lb1_out = np.empty((N, 2, n), dtype=np.int32)
+    if kind & PFSP_LB2 and lb2_out is None:
+        lb2_out = np.empty((N, 2, n), dtype=np.int32)
+    _check(_lib.pfsp_bound_batch(inst.handle, kind, N, _ptr(perm), _ptr(d1), _ptr(d2),
+                                 _ptr(lb1_out) if kind & PFSP_LB1 else None,
+                                 _ptr(lb2_out) if kind & PFSP_LB2 else None))
+    return (lb1_out if kind & PFSP_LB1 else None), (lb2_out if kind & PFSP_LB2 else None)
+
+
+def pfsp_bound_batch_dev(inst: Instance, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out, stream=0):
+    """Device addresses as ints (0 = NULL); enqueues on `stream` and returns."""
+    _check(_lib.pfsp_bound_batch_dev(inst.handle, kind, int(num_nodes), perm or None, d1 or None,
+                                     d2 or None, lb1_out or None, lb2_out or None, stream or None))
+
+
+def pfsp_stats(inst: Instance) -> dict:
+    s = pfsp_stats_t()
+    _check(_lib.pfsp_stats(inst.handle, ctypes.byref(s)))
+    return s.as_dict()

@@ -1,0 +1,135 @@
+"""Parity of the CUDA batched bounding kernel with the CPU oracle.
+
+Every child bound (LB1 and LB2, forward and backward) must be bit-identical
+to the oracle's from-scratch value; scheduled jobs must read -1.  Cases span
+several warps and CTAs, ragged tails, both job-mask widths (n <= 32 and
+n > 32), every m from 1 to 32, exhaustive node sets of tiny instances, the
+degenerate depths, and sampled nodes of the full 4,194,304-node batch of the
+20 x 20 bounding benchmark in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2012_09511_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    from paper_2012_09511_gb300 import build
+    build.build()
+    from paper_2012_09511_gb300 import pfsp
+    return pfsp
+
+
+def _compare(pf, p, perm, d1, d2, threads=8):
+    inst = pf.pfsp_load_instance(p)
+    g1, g2 = pf.pfsp_bound_batch(inst, pf.PFSP_LB1 | pf.PFSP_LB2, perm, d1, d2)
+    o1, o2 = orc.children_bounds_batch(p, perm, d1, d2, threads=threads)
+    bad1 = np.argwhere(g1 != o1)
+    bad2 = np.argwhere(g2 != o2)
+    assert len(bad1) == 0, ("LB1 mismatch", bad1[:5], g1[tuple(bad1[0])], o1[tuple(bad1[0])])
+    assert len(bad2) == 0, ("LB2 mismatch", bad2[:5], g2[tuple(bad2[0])], o2[tuple(bad2[0])])
+    return g1, g2
+
+
+@pytest.mark.parametrize("n,m,count", [
+    (20, 20, 6000), (20, 10, 5000), (10, 5, 5000), (12, 20, 3000), (50, 5, 1500), (30, 10, 2000),
+    (33, 7, 1500), (64, 4, 800), (32, 32, 600), (17, 3, 3001), (7, 2, 2000), (9, 1, 1000),
+    (2, 3, 300), (1, 4, 50),
+])
+def test_random_nodes_bit_exact(pf, n, m, count):
+    p = inputs.make_instance(n, m, 1000 + n * 64 + m)
+    perm, d1, d2 = inputs.random_nodes(n, count, seed=n + m, dmax=min(10, n))
+    _compare(pf, p, perm, d1, d2)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 8])
+def test_every_node_of_tiny_instances(pf, m):
+    n = 5
+    p = inputs.make_instance(n, m, 77 + m)
+    perm, d1, d2 = inputs.all_nodes_small(n)
+    _compare(pf, p, perm, d1, d2)
+
+
+def test_degenerate_depths(pf):
+    n, m = 20, 20
+    p = inputs.make_instance(n, m, 5)
+    rng = np.random.default_rng(0)
+    perm = np.stack([rng.permutation(n) for _ in range(64)]).astype(np.uint8)
+    # root, no children (d1 + d2 = n), leaf children (d1 + d2 = n - 1), one side empty
+    d1 = np.array([0, 20, 10, 19, 0, 0, 18, 1] * 8, dtype=np.uint8)
+    d2 = np.array([0, 0, 10, 0, 19, 20, 1, 0] * 8, dtype=np.uint8)
+    g1, g2 = _compare(pf, p, perm, d1, d2)
+    assert (g1[1] == -1).all() and (g2[5] == -1).all()
+    # leaves: the bound of a complete schedule is its makespan
+    full = np.concatenate([perm[3, :19], [perm[3, 19]]])
+    assert g1[3, 0, perm[3, 19]] == g2[3, 0, perm[3, 19]] == orc.makespan(p, full)
+
+
+def test_empty_batch_and_invalid_depths(pf):
+    p = inputs.make_instance(8, 4, 1)
+    inst = pf.pfsp_load_instance(p)
+    g1, g2 = pf.pfsp_bound_batch(inst, 3, np.zeros((0, 8)), np.zeros(0), np.zeros(0))
+    assert g1.shape == (0, 2, 8)
+    with pytest.raises(pf.PfspError) as e:
+        pf.pfsp_bound_batch(inst, 3, np.zeros((1, 8)) + np.arange(8), [5], [4])
+    assert e.value.code == pf.PFSP_ERR_INVALID
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_bound_batch(inst, 0, np.arange(8)[None], [1], [1])
+
+
+def test_lb1_only_and_lb2_only(pf):
+    n, m = 20, 20
+    p = inputs.make_instance(n, m, 9)
+    perm, d1, d2 = inputs.random_nodes(n, 3000, 4)
+    inst = pf.pfsp_load_instance(p)
+    a1, _ = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
+    _, b2 = pf.pfsp_bound_batch(inst, pf.PFSP_LB2, perm, d1, d2)
+    o1, o2 = orc.children_bounds_batch(p, perm, d1, d2, threads=8)
+    assert (a1 == o1).all() and (b2 == o2).all()
+
+
+def test_device_entry_point_with_torch_buffers(pf):
+    import torch
+    n, m = 20, 20
+    p = inputs.make_instance(n, m, 21)
+    perm, d1, d2 = inputs.random_nodes(n, 4099, 8)
+    inst = pf.pfsp_load_instance(p)
+    dev = torch.device("cuda:0")
+    tp = torch.from_numpy(perm).to(dev)
+    t1 = torch.from_numpy(d1).to(dev)
+    t2 = torch.from_numpy(d2).to(dev)
+    o1 = torch.empty((4099, 2, n), dtype=torch.int32, device=dev)
+    o2 = torch.empty_like(o1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pf.pfsp_bound_batch_dev(inst, 3, 4099, tp.data_ptr(), t1.data_ptr(), t2.data_ptr(), o1.data_ptr(),
+                                o2.data_ptr(), s.cuda_stream)
+    s.synchronize()
+    r1, r2 = orc.children_bounds_batch(p, perm, d1, d2, threads=8)
+    assert (o1.cpu().numpy() == r1).all() and (o2.cpu().numpy() == r2).all()
+
+
+def test_full_benchmark_batch_sampled(pf):
+    # the 20 x 20 bounding benchmark: 4,194,304 nodes, depths uniform in 0..10;
+    # every output is checked for structure, a sample against the oracle.
+    n, m, N = 20, 20, 4194304
+    p = inputs.make_instance(n, m, 2020)
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=2020)
+    inst = pf.pfsp_load_instance(p)
+    g1, g2 = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([rng.integers(0, N, 3000), np.arange(64), np.arange(N - 64, N)])
+    o1, o2 = orc.children_bounds_batch(p, perm[idx], d1[idx], d2[idx], threads=8)
+    assert (g1[idx] == o1).all() and (g2[idx] == o2).all()
+    # properties at every node: -1 exactly on scheduled jobs, LB1 <= LB2
+    u = n - d1.astype(np.int64) - d2.astype(np.int64)
+    assert ((g1 >= 0).sum(axis=2) == u[:, None]).all()
+    assert (g2 >= g1).all()
+    st = pf.pfsp_stats(inst)
+    assert st["bounded_children"] == int(2 * u.sum())
