@@ -1,0 +1,331 @@
+"""Benchmark of the PFSP branch-and-bound hot path on GB300.
+
+Workload (one step): the 20 x 20 bounding batch -- n = 20 jobs, m = 20
+machines, processing times uniform in [1, 99], 4,194,304 random partial
+schedules with prefix and suffix depths uniform in {0..10}; both children sets
+of every node bounded with LB1 and full-pair LB2 (190 machine pairs).  The
+metric is bounded children per second (every child gets both bounds).
+
+Native arm (default): the batch is resident in HBM; each step is one launch of
+the bounding kernel through pfsp_bound_batch_dev; L2 is flushed (a 256 MiB
+write) before every step, outside the timed events.  `e2e` repeats the
+measurement through the host-pointer entry point pfsp_bound_batch with pinned
+host buffers (host-to-device copy of the nodes and device-to-host copy of both
+bound arrays inside the timed region).
+
+Reference arm (--impl reference): the CPU oracle (oracle/) on the host cores,
+each step a bounded sample of the same batch.
+
+Multi-GPU (torchrun, one rank per GPU): every rank bounds its own batch (weak
+scaling); the only collectives are a barrier and a max of the timings.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_JOBS, M_MACH, N_NODES, SEED, DMAX = 20, 20, 4194304, 2020, 10
+WORKLOAD = "pfsp-bound-20x20-4M"
+METRIC = "bounded children/s (LB1 + full-pair LB2)"
+UNIT = "children/s"
+L2_FLUSH_BYTES = 256 << 20
+# INT32 ALU lanes per SM per clock on sm_103a (add, min/max, logic: measured
+# with the microbenchmark whose result is in profiles/int32_alu_peak.md)
+INT32_LANES_PER_SM_CLK = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nodes", type=int, default=N_NODES)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1000000, help="nodes in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_ops(n, m, d1, d2):
+    """Integer operations the bounding method needs per batch:
+    front/back wavefronts 2 per cell; per child and machine 6 (recurrence
+    max+add, term add+add, max into the bound, remaining-work subtraction);
+    LB2 per (pair, unscheduled job) 13: prefix map 2, suffix map 3, C 2 and
+    the pair term of both children 2 x 3."""
+    d = d1.astype(np.int64) + d2.astype(np.int64)
+    u = n - d
+    P = m * (m - 1) // 2
+    lb1 = 2 * m * d + 2 * u * m * 6
+    lb2 = P * u * 13
+    return int((lb1 + lb2).sum())
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2012_09511_gb300", "csrc")
+    for f in ("bound_device.cuh", "bound_kernel.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "bound_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return t.get("dram_bytes_per_launch_full")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(p, perm, d1, d2, sample):
+    """The oracle as it stands, on the host cores, over a bounded sample of the batch."""
+    import oracle as orc
+    cores = os.cpu_count() or 1
+    k = min(sample, len(d1))
+    t = time.perf_counter()
+    orc.children_bounds_batch(p, perm[:k], d1[:k], d2[:k], threads=cores)
+    dt = time.perf_counter() - t
+    children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
+    return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (k, len(d1), dt)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2012_09511_gb300 import inputs
+    p = inputs.make_instance(N_JOBS, M_MACH, SEED)
+    sample = min(args.cpu_sample, args.nodes)
+    perm, d1, d2 = inputs.random_nodes(N_JOBS, sample, seed=SEED)
+    for _ in range(args.warmup):
+        cpu_baseline(p, perm, d1, d2, min(2000, sample))
+    times, children = [], 0
+    for _ in range(args.steps):
+        r = cpu_baseline(p, perm, d1, d2, sample)
+        times.append(r)
+    value = statistics.median([t["value"] for t in times])
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_MACH, "nodes": args.nodes,
+                      "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": times[0]["cores"], "kind": "oracle",
+                            "sample": times[0]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2012_09511_gb300 import build
+    build.build()
+    from paper_2012_09511_gb300 import inputs, pfsp
+
+    n, m, N = N_JOBS, M_MACH, args.nodes
+    p = inputs.make_instance(n, m, SEED)
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=SEED + rank, dmax=DMAX)
+    children = int(2 * (n - d1.astype(np.int64) - d2.astype(np.int64)).sum())
+    ops = algorithmic_ops(n, m, d1, d2)
+    inst = pfsp.pfsp_load_instance(p)
+    tp = torch.from_numpy(perm).to(dev)
+    t1 = torch.from_numpy(d1).to(dev)
+    t2 = torch.from_numpy(d2).to(dev)
+    o1 = torch.empty((N, 2, n), dtype=torch.int32, device=dev)
+    o2 = torch.empty_like(o1)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step():
+        pfsp.pfsp_bound_batch_dev(inst, pfsp.PFSP_LB1 | pfsp.PFSP_LB2, N, tp.data_ptr(), t1.data_ptr(),
+                                  t2.data_ptr(), o1.data_ptr(), o2.data_ptr(), sh)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local].strip() if vis else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launch_ms = ms / args.steps
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    tot_children = torch.tensor([children * args.steps], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_children, op=dist.ReduceOp.SUM)
+    value = tot_children.item() / (t_max.item() * 1e-3)
+
+    # end to end through the host-pointer entry point, pinned host buffers
+    hp = torch.from_numpy(perm).pin_memory()
+    hd1 = torch.from_numpy(d1).pin_memory()
+    hd2 = torch.from_numpy(d2).pin_memory()
+    h1 = torch.empty((N, 2, n), dtype=torch.int32).pin_memory()
+    h2 = torch.empty((N, 2, n), dtype=torch.int32).pin_memory()
+    args_np = (hp.numpy(), hd1.numpy(), hd2.numpy())
+    if args.e2e_steps > 0:
+        pfsp.pfsp_bound_batch(inst, 3, *args_np, lb1_out=h1.numpy(), lb2_out=h2.numpy())  # warm (scratch)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pfsp.pfsp_bound_batch(inst, 3, *args_np, lb1_out=h1.numpy(), lb2_out=h2.numpy())
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = children * args.e2e_steps * ws / e2e_t.item()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = nsm * INT32_LANES_PER_SM_CLK * sm_max * 1e6
+    achieved = ops / (launch_ms * 1e-3)
+    traffic = ncu_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max.item() / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "nodes_per_gpu": N, "seed": SEED,
+                   "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)",
+                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                   "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
+                         nsm, INT32_LANES_PER_SM_CLK, sm_max),
+                     "ops_per_launch": ops, "kernel_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
+                "d2h_bytes_per_step": int(2 * N * 2 * n * 4)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -51,48 +51,52 @@ __device__ __forceinline__ int popcnt(umask_t<NW> x) {
 
 // Shared-memory views of one CTA's instance tables.
 struct SmemTables {
-    const int *pm;    // [m][nj]
-    const int *tot;   // [32]
-    const int *kl;    // [S*32]
-    const int2 *ptab; // [S][n][32]
+    const int *pm;        // [m][nj]
+    const int *tot;       // [32]
+    const int *kl;        // [S*32]
+    const uint8_t *rank;  // [S][n][32] position of job j in the lane's pair order
+    const int2 *ptab;     // [S][n][32]
 };
 
-// Per-warp scratch layout (int32 words); see warp_words().
-struct WarpScratch {
-    int *F, *R, *B;   // [32] each: parent front, remaining work, back
-    int *ul;          // [64] compact list of unscheduled jobs
-    int *Gf;          // [n][mp] forward child: F'_k + R_k - p_jk
-    int *Gb;          // [n][mp] backward child: F_k + R_k - p_jk
-    int *Bb;          // [n][mp] backward child back B'_k
-    int *PB;          // [n][32] prefix map constants by position (per lane)
-    int *Cb;          // [n][32] C_j per job (per lane); PB..Cb doubles as int2 [n][32]
-    int *Acc;         // [n][32] int2 accumulators (only when not kept in registers)
-};
-
-// Every region starts on a multiple of 4 words (16 bytes) so that the int2
-// views of PB..Cb and Acc are aligned whatever n and m are.
 __host__ __device__ inline int round4(int w) { return (w + 3) & ~3; }
 
-// LB1 alone uses only F, R, B and the compact list (the first 160 words).
+// Per-warp scratch.  Every region starts on a multiple of 4 words (16 bytes);
+// child-indexed tables have round4(n) rows so that the evaluation loop, which
+// walks children in groups of four, stays inside them.
+struct WarpScratch {
+    int *F, *R, *B;   // [32] each: parent front, remaining work, back
+    int *ul;          // [64] compact list: ul[c] = c-th unscheduled job
+    int *cidx;        // [64] cidx[j] = compact index of job j
+    int *Gf;          // [nr][mp] forward child: F'_k + R_k - p_jk
+    int *Gb;          // [nr][mp] backward child: F_k + R_k - p_jk
+    int *Bb;          // [nr][mp] backward child back B'_k
+    int2 *E;          // [nr][32] prefix pass records {PB, t | c << 8} (per lane)
+    int *Cb;          // [nr][32] C of child c (per lane); E..Cb doubles as int2 [u][33]
+    int2 *Acc;        // [nr][32] accumulators (only when not kept in registers)
+};
+
 __host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2) {
-    if (!lb2) return 160;
-    int g = round4(n * (m | 1));
-    return 160 + 3 * g + 2 * n * 32 + (smem_acc ? 2 * n * 32 : 0);
+    if (!lb2) return 224;
+    int nr = round4(n);
+    int g = round4(nr * (m | 1));
+    return 224 + 3 * g + 96 * nr + (smem_acc ? 64 * nr : 0);
 }
 
 __device__ inline WarpScratch carve_warp(int *base, int n, int m) {
-    int g = round4(n * (m | 1));
+    int nr = round4(n);
+    int g = round4(nr * (m | 1));
     WarpScratch w;
     w.F = base;
     w.R = base + 32;
     w.B = base + 64;
     w.ul = base + 96;
-    w.Gf = base + 160;
+    w.cidx = base + 160;
+    w.Gf = base + 224;
     w.Gb = w.Gf + g;
     w.Bb = w.Gb + g;
-    w.PB = w.Bb + g;
-    w.Cb = w.PB + n * 32;
-    w.Acc = w.Cb + n * 32;
+    w.E = reinterpret_cast<int2 *>(w.Bb + g);
+    w.Cb = w.Bb + g + 64 * nr;
+    w.Acc = reinterpret_cast<int2 *>(w.Cb + 32 * nr);
     return w;
 }
 
@@ -107,19 +111,35 @@ struct ChildBounds {
     int lb2f[NW], lb2b[NW];
 };
 
+template <int NW>
+__device__ __forceinline__ int lowest_bit(umask_t<NW> x) {
+    if constexpr (NW == 1) return __ffs(x) - 1;
+    else return __ffsll((long long)x) - 1;
+}
+
+template <int NW>
+__device__ __forceinline__ int highest_bit(umask_t<NW> x) {
+    if constexpr (NW == 1) return 31 - __clz(x);
+    else return 63 - __clzll((long long)x);
+}
+
 // Decompose the node whose permutation entries are held one per lane
 // (job0 = position lane, job1 = position lane + 32) with depths d1, d2.
-// kind: bit 0 = LB1 wanted, bit 1 = LB2 wanted.  All 32 lanes must call.
-template <int NW, bool REGACC>
-__device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m,
-                                               int S, int kind, int job0, int job1, int d1, int d2,
+// kind: bit 0 = LB1 wanted, bit 1 = LB2 wanted.  MT is the machine count
+// when known at compile time (0: take m_rt).  All 32 lanes must call.
+template <int NW, int MT>
+__device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m_rt,
+                                               int S_rt, int kind, int job0, int job1, int d1, int d2,
                                                ChildBounds<NW> &out) {
     using mask_t = umask_t<NW>;
+    constexpr bool REGACC = (NW == 1);
+    const int m = MT ? MT : m_rt;
+    const int S = MT ? (MT * (MT - 1) / 2 + 31) / 32 : S_rt;
     const int lane = threadIdx.x & 31;
     const int mp = m | 1;
     const int nj = (n + 3) & ~3;
 
-    // ---- unscheduled set and its compact list --------------------------------
+    // ---- unscheduled set, its compact list and the compact index of each job --
     bool un0 = lane < n && lane >= d1 && lane < n - d2;
     bool un1 = (NW == 2) && (lane + 32 < n) && (lane + 32 >= d1) && (lane + 32 < n - d2);
     mask_t mine = (un0 ? (mask_t(1) << job0) : mask_t(0));
@@ -136,7 +156,11 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
 #pragma unroll
     for (int h = 0; h < NW; ++h) {
         int j = lane + 32 * h;
-        if (j < n && has_job<NW>(U, j)) W.ul[popcnt<NW>(U & low_bits<NW>(j))] = j;
+        if (j < n) {
+            int c = popcnt<NW>(U & low_bits<NW>(j));
+            W.cidx[j] = c;
+            if (has_job<NW>(U, j)) W.ul[c] = j;
+        }
     }
 
     // ---- step 1: front (Eq. 1 over sigma1) as a wavefront over machines -------
@@ -201,6 +225,7 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
         if (c < u) {
             int j = W.ul[c];
             int f = 0, lf = kNegInf;
+#pragma unroll
             for (int k = 0; k < m; ++k) {
                 int pk = T.pm[k * nj + j];
                 f = max(f, W.F[k]) + pk;
@@ -209,6 +234,7 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
                 if (want2) W.Gf[c * mp + k] = g;
             }
             int b = 0, lb = kNegInf;
+#pragma unroll
             for (int k = m - 1; k >= 0; --k) {
                 int pk = T.pm[k * nj + j];
                 b = max(b, W.B[k]) + pk;
@@ -237,86 +263,108 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
 #pragma unroll
         for (int c = 0; c < 32; ++c) { accf[c] = kNegInf; accb[c] = kNegInf; }
     } else {
-        int2 *A = reinterpret_cast<int2 *>(W.Acc);
-        for (int c = 0; c < u; ++c) A[c * 32 + lane] = make_int2(kNegInf, kNegInf);
+        for (int c = 0; c < u; ++c) W.Acc[c * 32 + lane] = make_int2(kNegInf, kNegInf);
     }
+    const int u4 = (u + 3) & ~3;
+    int2 *E = W.E + lane;
+    // (reversed) positions of the unscheduled jobs in each pair's Johnson
+    // order, one bit mask per slot; with a compile-time slot count all masks
+    // are built in a single walk over the unscheduled jobs
+    constexpr int SC = MT ? (MT * (MT - 1) / 2 + 31) / 32 : 1;
+    mask_t UposAll[SC];
+    if constexpr (MT > 0) {
+#pragma unroll
+        for (int s = 0; s < SC; ++s) UposAll[s] = 0;
+        for (mask_t um = U; um; um &= um - 1) {
+            const uint8_t *rj = T.rank + (size_t)lowest_bit<NW>(um) * SC * 32 + lane;
+#pragma unroll
+            for (int s = 0; s < SC; ++s) UposAll[s] |= mask_t(1) << rj[s * 32];
+        }
+    }
+#pragma unroll 1
     for (int s = 0; s < S; ++s) {
         const int klw = T.kl[s * 32 + lane];
         const int k = klw & 0xff, l = klw >> 8;
-        const bool real = l > 0;  // lanes past the last pair of the last slot hold no pair
         const int Bl = W.B[l];
         const int2 *pt = T.ptab + (size_t)s * n * 32 + lane;
-        // pass 1: prefix constants PB before each position of the order
-        int PB = kNegInf;
-#pragma unroll 4
-        for (int t = 0; t < n; ++t) {
-            int2 e = pt[t * 32];
-            int j = e.x & 0xff;
-            W.PB[t * 32 + lane] = PB;
-            int nb = max(PB + (e.x >> 8), e.y);
-            PB = has_job<NW>(U, j) ? nb : PB;
+        mask_t Upos;
+        if constexpr (MT > 0) {
+            Upos = UposAll[0];
+#pragma unroll
+            for (int q = 0; q + 1 < SC; ++q) UposAll[q] = UposAll[q + 1];
+        } else {
+            Upos = 0;
+            for (mask_t um = U; um; um &= um - 1)
+                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];
         }
-        // pass 2: suffix maps (SA, SB) and C_j of every unscheduled job j
-        int SA = 0, SB = kNegInf;
-#pragma unroll 4
-        for (int t = n - 1; t >= 0; --t) {
+        // prefix pass, ascending Johnson order (descending stored index):
+        // record PB before each job
+        int PB = kNegInf;
+        for (int i = 0; i < u; ++i) {
+            int t = highest_bit<NW>(Upos);
+            Upos ^= mask_t(1) << t;
             int2 e = pt[t * 32];
-            int j = e.x & 0xff;
-            if (has_job<NW>(U, j)) {
-                int C = max(W.PB[t * 32 + lane] + SA, SB);
-                W.Cb[j * 32 + lane] = C;
-                SB = max(e.y + SA, SB);
-                SA += e.x >> 8;
-            }
+            int c = W.cidx[e.x & 0xff];
+            E[i * 32] = make_int2(PB, t | (c << 8));
+            PB = max(PB + (e.x >> 8), e.y);
+        }
+        // suffix pass, descending positions: C = max(PB + SA, SB), then extend
+        int SA = 0, SB = kNegInf;
+        for (int i = u - 1; i >= 0; --i) {
+            int2 q = E[i * 32];
+            int2 e = pt[(q.y & 0xff) * 32];
+            W.Cb[(q.y >> 8) * 32 + lane] = max(q.x + SA, SB);
+            SB = max(e.y + SA, SB);
+            SA += e.x >> 8;
         }
         // evaluation: the third pair term of every child of this parent
+        const int *gf = W.Gf + k;
+        const int *gb = W.Gb + k;
+        const int *bb = W.Bb + l;
+        const int *cb = W.Cb + lane;
         if constexpr (REGACC) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                if (c >= u) break;
-                int j = W.ul[c];
-                int C = real ? W.Cb[j * 32 + lane] : kNegInf;
-                int ef = W.Gf[c * mp + k] + C + Bl;
-                int eb = W.Gb[c * mp + k] + C + W.Bb[c * mp + l];
-                accf[c] = max(accf[c], ef);
-                accb[c] = max(accb[c], eb);
+            for (int c0 = 0; c0 < 32; c0 += 4) {
+                if (c0 >= u4) break;
+#pragma unroll
+                for (int c = c0; c < c0 + 4; ++c) {
+                    int C = cb[c * 32];
+                    accf[c] = max(accf[c], gf[c * mp] + C + Bl);
+                    accb[c] = max(accb[c], gb[c * mp] + C + bb[c * mp]);
+                }
             }
         } else {
-            int2 *A = reinterpret_cast<int2 *>(W.Acc);
             for (int c = 0; c < u; ++c) {
-                int j = W.ul[c];
-                int C = real ? W.Cb[j * 32 + lane] : kNegInf;
-                int ef = W.Gf[c * mp + k] + C + Bl;
-                int eb = W.Gb[c * mp + k] + C + W.Bb[c * mp + l];
-                int2 v = A[c * 32 + lane];
-                v.x = max(v.x, ef);
-                v.y = max(v.y, eb);
-                A[c * 32 + lane] = v;
+                int C = cb[c * 32];
+                int2 v = W.Acc[c * 32 + lane];
+                v.x = max(v.x, gf[c * mp] + C + Bl);
+                v.y = max(v.y, gb[c * mp] + C + bb[c * mp]);
+                W.Acc[c * 32 + lane] = v;
             }
         }
     }
-    // ---- max over lanes (pairs) per child: skewed transpose through smem ------
+    // ---- max over lanes (pairs) per child: transpose through padded rows ------
     __syncwarp();
-    int2 *X = reinterpret_cast<int2 *>(W.PB);  // [n][32], aliases PB and Cb
+    int2 *X = W.E;  // [u][33], aliases E and Cb
     if constexpr (REGACC) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
             if (c >= u) break;
-            X[c * 32 + ((lane + c) & 31)] = make_int2(accf[c], accb[c]);
+            X[c * 33 + lane] = make_int2(accf[c], accb[c]);
         }
     } else {
-        const int2 *A = reinterpret_cast<const int2 *>(W.Acc);
-        for (int c = 0; c < u; ++c) X[c * 32 + ((lane + c) & 31)] = A[c * 32 + lane];
+        for (int c = 0; c < u; ++c) X[c * 33 + lane] = W.Acc[c * 32 + lane];
     }
     __syncwarp();
 #pragma unroll
     for (int h = 0; h < NW; ++h) {
         int c = lane + 32 * h;
         if (c < u) {
+            const int2 *row = X + c * 33;
             int mf = kNegInf, mb = kNegInf;
-#pragma unroll 8
+#pragma unroll
             for (int i = 0; i < 32; ++i) {
-                int2 v = X[c * 32 + ((i + c) & 31)];
+                int2 v = row[i];
                 mf = max(mf, v.x);
                 mb = max(mb, v.y);
             }

@@ -21,7 +21,7 @@ struct BoundArgs {
     const int32_t *tab;
     int tab_words;
     int n, m, S;
-    int off_pm, off_tot, off_kl, off_ptab;
+    int off_pm, off_tot, off_kl, off_rank, off_ptab;
     int warp_words;
     int kind;
 };
@@ -72,8 +72,10 @@ __device__ inline void stage_tables(int *dst, const int32_t *src, int words, uin
     }
 }
 
-template <int NW, bool REGACC>
-__global__ void __launch_bounds__(256) bound_batch_kernel(BoundArgs a) {
+constexpr int kWarpsPerCta = 14;
+
+template <int NW, int MT>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(BoundArgs a) {
     extern __shared__ __align__(16) int smem[];
     __shared__ uint64_t bar;
     stage_tables(smem, a.tab, a.tab_words, &bar);
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(256) bound_batch_kernel(BoundArgs a) {
     T.pm = smem + a.off_pm;
     T.tot = smem + a.off_tot;
     T.kl = smem + a.off_kl;
+    T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
     T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
 
     const int lane = threadIdx.x & 31;
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(256) bound_batch_kernel(BoundArgs a) {
             continue;
         }
         ChildBounds<NW> cb;
-        decompose_node<NW, REGACC>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
+        decompose_node<NW, MT>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
             int j = lane + 32 * h;
@@ -161,12 +164,12 @@ static int fit_warps(const BoundArgs &a, int want) {
     return (int)std::max<long long>(0, std::min<long long>(want, w));
 }
 
-template <int NW, bool REGACC>
+template <int NW, int MT>
 static cudaError_t launch_t(const BoundArgs &a, int want_warps, cudaStream_t stream) {
     const int warps = fit_warps(a, want_warps);
     if (warps < 1) return cudaErrorInvalidConfiguration;
     size_t smem = (size_t)(a.tab_words + warps * a.warp_words) * 4;
-    auto kern = bound_batch_kernel<NW, REGACC>;
+    auto kern = bound_batch_kernel<NW, MT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -194,23 +197,34 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
     a.num_nodes = num_nodes;
     a.tab = inst->d_tab;
     // LB1 alone needs only the processing times, totals and pair indexes
-    a.tab_words = (kind & PFSP_LB2) ? L.words : L.off_ptab;
+    a.tab_words = (kind & PFSP_LB2) ? L.words : L.off_rank;
     a.n = L.n;
     a.m = L.m;
     a.S = (kind & PFSP_LB2) ? L.S : 0;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
     a.off_kl = L.off_kl;
+    a.off_rank = L.off_rank;
     a.off_ptab = L.off_ptab;
     a.kind = kind;
-    const int warps = 8;
+    const int warps = kWarpsPerCta;
     const bool want2 = (kind & PFSP_LB2) && L.m >= 2;
-    if (L.n <= 32) {
-        a.warp_words = warp_words(L.n, L.m, false, want2);
-        return launch_t<1, true>(a, warps, stream);
+    const int nw = L.n <= 32 ? 1 : 2;
+    a.warp_words = warp_words(L.n, L.m, nw == 2, want2);
+    if (nw == 1) {
+        switch (L.m) {
+            case 5: return launch_t<1, 5>(a, warps, stream);
+            case 10: return launch_t<1, 10>(a, warps, stream);
+            case 20: return launch_t<1, 20>(a, warps, stream);
+            default: return launch_t<1, 0>(a, warps, stream);
+        }
     }
-    a.warp_words = warp_words(L.n, L.m, true, want2);
-    return launch_t<2, false>(a, warps, stream);
+    switch (L.m) {
+        case 5: return launch_t<2, 5>(a, warps, stream);
+        case 10: return launch_t<2, 10>(a, warps, stream);
+        case 20: return launch_t<2, 20>(a, warps, stream);
+        default: return launch_t<2, 0>(a, warps, stream);
+    }
 }
 
 }  // namespace pfsp

@@ -36,7 +36,8 @@ TableLayout table_layout(int n, int m) {
     L.off_pm = 0;
     L.off_tot = L.off_pm + m * L.nj;
     L.off_kl = L.off_tot + 32;
-    L.off_ptab = L.off_kl + L.S * 32;
+    L.off_rank = L.off_kl + L.S * 32;
+    L.off_ptab = L.off_rank + L.S * n * 8;
     L.words = L.off_ptab + 2 * L.S * n * 32;
     return L;
 }
@@ -75,9 +76,13 @@ static void build_tables(const TableLayout &L, const int32_t *p, std::vector<int
         blob[L.off_tot + k] = t;
     }
     int2 *ptab = reinterpret_cast<int2 *>(blob.data() + L.off_ptab);
+    uint8_t *rank = reinterpret_cast<uint8_t *>(blob.data() + L.off_rank);
     for (int s = 0; s < L.S; ++s)
         for (int t = 0; t < n; ++t)
-            for (int lane = 0; lane < 32; ++lane) ptab[(s * n + t) * 32 + lane] = make_int2(0, kNegInf);
+            for (int lane = 0; lane < 32; ++lane) {
+                ptab[(s * n + t) * 32 + lane] = make_int2(t, kNegInf);
+                rank[(t * L.S + s) * 32 + lane] = (uint8_t)t;
+            }
     int q = 0;
     std::vector<int> lag(n);
     for (int k = 0; k < m; ++k)
@@ -94,7 +99,9 @@ static void build_tables(const TableLayout &L, const int32_t *p, std::vector<int
                 int j = ord[t];
                 int a = p[j * m + l] - p[j * m + k];
                 int b = lag[j] + p[j * m + l];
-                ptab[(s * n + t) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
+                const int r = n - 1 - t;  // reversed: the order runs from the highest index down
+                ptab[(s * n + r) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
+                rank[(j * L.S + s) * 32 + lane] = (uint8_t)r;
             }
         }
 }
