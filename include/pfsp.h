@@ -101,6 +101,56 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
                          const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out,
                          void *stream);
 
+/*
+ * Options of a solve.  Call pfsp_default_options first, then change fields.
+ *   init_ub      exclusive incumbent: only schedules with makespan < init_ub
+ *                are sought (the paper initialises it at the optimum plus one
+ *                or at a known value, Section 5); INT32_MAX (default) starts
+ *                from the NEH schedule's makespan.  With init_ub equal to the
+ *                optimum, the search proves that nothing better exists and
+ *                the decomposed-node count is that of the fixed critical tree.
+ *   node_limit   stop after about this many counted decompositions (checked
+ *                every check_every iterations per explorer); 0 = no limit.
+ *   time_limit_s stop after this many seconds of device time; 0 = no limit.
+ *   bound        PFSP_LB1 or PFSP_LB2 (Section 2.4).
+ *   branching    PFSP_MINMIN (default) or PFSP_MINMIN_CAPPED: the MinMin rule
+ *                on min(bound, c) with c the solve's initial incumbent (a
+ *                constant, so that every node's decision is fixed for the run).
+ *   warps_per_sm explorers per SM; 0 = as many as fit in shared memory.
+ *   check_every  iterations between limit checks and length publications
+ *                (rounded up to a power of two); 0 = default (16).
+ *   min_steal    smallest remaining interval (in leaves) a victim splits;
+ *                0 = default (2, i.e. any splittable interval).
+ */
+typedef struct {
+    int32_t init_ub;
+    int64_t node_limit;
+    double time_limit_s;
+    int bound;
+    int branching;
+    int warps_per_sm;
+    int check_every;
+    double min_steal;
+    int reserved[8];
+} pfsp_options;
+
+void pfsp_default_options(pfsp_options *opt);
+
+/*
+ * Solve an instance with the device-resident pool of depth-first explorers
+ * (Sections 2.2-3.4): dynamic branching with MinMin, pruning of children whose
+ * bound is not below the incumbent, interval work stealing on the device.
+ * Writes the best makespan found (or init_ub when nothing better exists) to
+ * *best_cmax, a permutation reaching it to best_perm (n int32 job ids; may be
+ * NULL; untouched when *outcome is PFSP_PROVEN_NO_BETTER), and the outcome
+ * code (PFSP_OPTIMAL, PFSP_PROVEN_NO_BETTER, PFSP_LIMIT_NODES,
+ * PFSP_LIMIT_TIME) to *outcome.  pfsp_stats then reports the counters.
+ * Errors: PFSP_ERR_INVALID, PFSP_ERR_UNSUPPORTED, PFSP_ERR_OOM, PFSP_ERR_CUDA,
+ * PFSP_ERR_TIMEOUT (a bounded device-side wait expired; no result).
+ */
+int pfsp_solve(const pfsp_instance *inst, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
+               int *outcome);
+
 /* Counters of the last pfsp_bound_batch / pfsp_solve call on an instance. */
 typedef struct {
     uint64_t decomposed;       /* parents whose children were bounded (root counts 1) */

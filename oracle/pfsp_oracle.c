@@ -415,7 +415,8 @@ int orc_minmin(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un,
 typedef struct {
     orc_tables T;
     int bound;          /* ORC_LB1 or ORC_LB2 */
-    int capped;         /* MinMin on min(LB, UB) */
+    int capped;         /* MinMin on min(LB, cap) */
+    int32_t cap;        /* the run's initial incumbent */
     int32_t ub;         /* incumbent: only makespans < ub are sought */
     int32_t best_perm[ORC_MAXN];
     int found;
@@ -443,7 +444,7 @@ static void bb_dfs(orc_bb *S, const int32_t *perm, int d1, int d2)
     if (u == 1) S->leaves += 2;
     for (int j = 0; j < n; ++j) un[j] = 0;
     for (int i = d1; i < n - d2; ++i) un[perm[i]] = 1;
-    int dir = orc_minmin(n, lb, lb + n, un, S->capped ? S->ub : INT32_MAX);
+    int dir = orc_minmin(n, lb, lb + n, un, S->capped ? S->cap : INT32_MAX);
     const int32_t *lbd = lb + dir * n;
 
     /* prune at bounding time against the current incumbent */
@@ -497,6 +498,7 @@ int orc_bb_solve(int n, int m, const int32_t *p, int bound, int capped, int32_t 
     } else {
         S->ub = init_ub;
     }
+    S->cap = S->ub;
     int32_t root[ORC_MAXN];
     for (int j = 0; j < n; ++j) root[j] = j;
     bb_dfs(S, root, 0, 0);

@@ -26,54 +26,6 @@ struct BoundArgs {
     int kind;
 };
 
-// Stage `words` int32 (a multiple of 4, 16-byte aligned on both sides) from
-// global into shared memory with the bulk-copy engine, completion tracked by
-// an mbarrier.  The wait is bounded; on expiry the block falls back to plain
-// loads so that no thread can wait forever.
-__device__ inline void stage_tables(int *dst, const int32_t *src, int words, uint64_t *bar) {
-    const unsigned bytes = (unsigned)words * 4u;
-    const unsigned sbar = (unsigned)__cvta_generic_to_shared(bar);
-    bool ok = true;
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(bytes)
-                     : "memory");
-        const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
-        // copies of at most 64 KiB - 16 bytes each
-        unsigned done = 0;
-        while (done < bytes) {
-            unsigned chunk = min(bytes - done, 65536u - 16u);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    sdst + done),
-                "l"(reinterpret_cast<const char *>(src) + done), "r"(chunk), "r"(sbar)
-                : "memory");
-            done += chunk;
-        }
-    }
-    // phase 0 completes when all bytes have landed
-    unsigned ready = 0;
-    for (int it = 0; it < (1 << 22) && !ready; ++it) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ready)
-            : "r"(sbar)
-            : "memory");
-    }
-    ok = ready != 0;
-    if (!__syncthreads_and(ok)) {
-        // bounded wait expired (never expected): copy with plain loads instead
-        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
-    }
-}
-
-constexpr int kWarpsPerCta = 14;
-
 template <int NW, int MT>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(BoundArgs a) {
     extern __shared__ __align__(16) int smem[];

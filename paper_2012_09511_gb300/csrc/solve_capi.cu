@@ -1,0 +1,267 @@
+// solve_capi.cu -- host side of pfsp_solve: initial incumbent (NEH), initial
+// partition of the leaf interval [0, n!) among the explorers, device state,
+// cooperative launch of the explorer pool and collection of the result.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "bound_device.cuh"
+#include "pfsp_internal.h"
+#include "solve_internal.h"
+
+namespace pfsp {
+
+// Completion time of the last job on the last machine of a sequence (Eq. 1).
+static int makespan_of(int m, const int32_t *p, const int *seq, int len, std::vector<int> &C) {
+    std::fill(C.begin(), C.end(), 0);
+    for (int i = 0; i < len; ++i) {
+        const int32_t *pj = p + (size_t)seq[i] * m;
+        int prev = 0;
+        for (int k = 0; k < m; ++k) {
+            C[k] = std::max(C[k], prev) + pj[k];
+            prev = C[k];
+        }
+    }
+    return C[m - 1];
+}
+
+// NEH insertion heuristic (Nawaz, Enscore, Ham 1983) for the initial
+// incumbent: jobs by decreasing total time (ties: lower id first), each
+// inserted where the partial makespan is least (ties: earliest position).
+int neh(int n, int m, const int32_t *p, std::vector<int> &perm) {
+    std::vector<int> order(n), tot(n, 0);
+    for (int j = 0; j < n; ++j) {
+        order[j] = j;
+        for (int k = 0; k < m; ++k) tot[j] += p[j * m + k];
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tot[x] > tot[y]; });
+    std::vector<int> seq, cand;
+    std::vector<int> C(m);
+    for (int j : order) {
+        int best_pos = 0, best = INT_MAX;
+        for (int pos = 0; pos <= (int)seq.size(); ++pos) {
+            cand = seq;
+            cand.insert(cand.begin() + pos, j);
+            int c = makespan_of(m, p, cand.data(), (int)cand.size(), C);
+            if (c < best) {
+                best = c;
+                best_pos = pos;
+            }
+        }
+        seq.insert(seq.begin() + best_pos, j);
+    }
+    perm = seq;
+    return makespan_of(m, p, seq.data(), n, C);
+}
+
+struct DeviceSolveState {
+    void *blob = nullptr;
+    size_t bytes = 0;
+    ~DeviceSolveState() {
+        if (blob) cudaFree(blob);
+    }
+};
+
+}  // namespace pfsp
+
+using namespace pfsp;
+
+extern "C" {
+
+void pfsp_default_options(pfsp_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->init_ub = INT32_MAX;
+    o->bound = PFSP_LB1;
+    o->branching = PFSP_MINMIN;
+}
+
+int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
+               int *outcome) {
+    pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
+    if (!inst || !opt || !best_cmax || !outcome) return set_error(PFSP_ERR_INVALID, "NULL argument");
+    if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
+        return set_error(PFSP_ERR_INVALID, "bound must be PFSP_LB1 or PFSP_LB2");
+    if (opt->branching != PFSP_MINMIN && opt->branching != PFSP_MINMIN_CAPPED)
+        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN or PFSP_MINMIN_CAPPED");
+    if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
+    if (opt->bound == PFSP_LB2 && !inst->lb2_ok)
+        return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = inst->n, m = inst->m;
+    const TableLayout &L = inst->lay;
+
+    // incumbent: exclusive; INT32_MAX means "start from the NEH schedule"
+    std::vector<int> neh_perm;
+    int ub0 = opt->init_ub;
+    bool from_neh = false;
+    if (ub0 == INT32_MAX) {
+        ub0 = neh(n, m, inst->p_host, neh_perm);
+        from_neh = true;
+    }
+
+    // launch shape: explorers per CTA limited by shared memory, one CTA per SM
+    SolveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tab = inst->d_tab;
+    a.tab_words = opt->bound == PFSP_LB2 ? L.words : L.off_rank;
+    a.n = n;
+    a.m = m;
+    a.S = opt->bound == PFSP_LB2 ? L.S : 0;
+    a.off_pm = L.off_pm;
+    a.off_tot = L.off_tot;
+    a.off_kl = L.off_kl;
+    a.off_rank = L.off_rank;
+    a.off_ptab = L.off_ptab;
+    a.bound = opt->bound;
+    a.capped = opt->branching == PFSP_MINMIN_CAPPED;
+    a.cap = ub0;
+    const int per_warp = solve_warp_words(n, m, opt->bound);  // bound scratch + explorer state
+    a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
+    int dev = 0, nsm = 1, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
+    long long fit = ((long long)optin - 64 - (long long)a.tab_words * 4) / ((long long)per_warp * 4);
+    warps = (int)std::min<long long>(warps, fit);
+    if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
+    size_t smem = (size_t)(a.tab_words + warps * per_warp) * 4;
+    int per_sm = solve_occupancy(a, warps, smem);
+    if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "solve kernel cannot be resident (occupancy 0)");
+    const int blocks = nsm * per_sm;
+    const int K = blocks * warps;
+    a.K = K;
+
+    // initial partition of [0, n!): equal chunks of the first L levels
+    int Lv = 0;
+    long long PL = 1;
+    while (Lv < n && PL < K) {
+        PL *= (n - Lv);
+        ++Lv;
+    }
+    const long long Kp = std::min<long long>(K, PL);
+    std::vector<uint8_t> hs((size_t)K * 64, 0), he((size_t)K * 65, 0);
+    auto digits = [&](long long x, uint8_t *d) {
+        for (int lvl = Lv - 1; lvl >= 0; --lvl) {
+            int r = n - lvl;
+            d[lvl] = (uint8_t)(x % r);
+            x /= r;
+        }
+    };
+    for (long long i = 0; i < Kp; ++i) {
+        long long s = (long long)((__int128)i * PL / Kp), e = (long long)((__int128)(i + 1) * PL / Kp);
+        digits(s, &hs[(size_t)i * 64]);
+        if (e == PL) he[(size_t)i * 65] = 1;
+        else digits(e, &he[(size_t)i * 65 + 1]);
+    }
+    const int active0 = (int)Kp;
+
+    // device state, one allocation
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_rj = take((size_t)K * n * n), o_rl = take((size_t)K * n * n * 4);
+    const size_t o_is = take((size_t)K * 64), o_ie = take((size_t)K * 65);
+    const size_t o_mb = take((size_t)K * 4), o_rs = take((size_t)K * 4), o_le = take((size_t)K * 4);
+    const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64);
+    DeviceSolveState D;
+    cudaError_t e = cudaMalloc(&D.blob, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PFSP_ERR_OOM, "cudaMalloc of %zu bytes for the explorer pool failed", off);
+    }
+    char *b = (char *)D.blob;
+    a.rows_job = (uint8_t *)(b + o_rj);
+    a.rows_lb = (int32_t *)(b + o_rl);
+    a.in_start = (uint8_t *)(b + o_is);
+    a.in_end = (uint8_t *)(b + o_ie);
+    a.mailbox = (int *)(b + o_mb);
+    a.response = (int *)(b + o_rs);
+    a.len_est = (float *)(b + o_le);
+    a.best_perm = (uint8_t *)(b + o_bp);
+    a.counters = (unsigned long long *)(b + o_ct);
+    int *sc = (int *)(b + o_sc);  // active, ub, stop, err, best_key (8 bytes at +16)
+    a.active = sc + 0;
+    a.ub = sc + 1;
+    a.stop = sc + 2;
+    a.err = sc + 3;
+    a.best_key = (unsigned long long *)(sc + 4);
+    a.node_limit = opt->node_limit;
+    a.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
+    a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
+    int ce = opt->check_every > 0 ? opt->check_every : 16;
+    int pw = 1;
+    while (pw < ce) pw <<= 1;
+    a.check_every = pw;
+
+    int hsc[6] = {active0, ub0, 0, 0, -1, -1};  // best_key = ~0
+    cudaStream_t st = 0;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_end, he.data(), he.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc, hsc, sizeof(hsc), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) e = launch_solve(a, blocks, warps, smem, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    int rsc[6];
+    unsigned long long cnt[8];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rsc, sc, sizeof(rsc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, a.counters, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "pfsp_solve: %s", cudaGetErrorString(e));
+    if (rsc[3] != 0) return set_error(PFSP_ERR_TIMEOUT, "a bounded device wait expired (detail %d)", rsc[3]);
+
+    unsigned long long key;
+    memcpy(&key, &rsc[4], sizeof(key));
+    const int final_ub = rsc[1];
+    bool found = key != ~0ull;
+    std::vector<uint8_t> bp(64);
+    if (found) {
+        int eid = (int)(key & 0xffffffffu);
+        e = cudaMemcpy(bp.data(), a.best_perm + (size_t)eid * 64, 64, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "pfsp_solve readback: %s", cudaGetErrorString(e));
+    }
+    if (rsc[2] == 1) *outcome = PFSP_LIMIT_NODES;
+    else if (rsc[2] == 2) *outcome = PFSP_LIMIT_TIME;
+    else if (found || from_neh) *outcome = PFSP_OPTIMAL;
+    else *outcome = PFSP_PROVEN_NO_BETTER;
+    *best_cmax = final_ub;
+    if (best_perm) {
+        if (found)
+            for (int j = 0; j < n; ++j) best_perm[j] = bp[j];
+        else if (from_neh)
+            for (int j = 0; j < n; ++j) best_perm[j] = neh_perm[j];
+    }
+    memset(&inst->stats, 0, sizeof(inst->stats));
+    inst->stats.decomposed = cnt[0];
+    inst->stats.bounded_children = cnt[1];
+    inst->stats.leaves = cnt[2];
+    inst->stats.pruned = cnt[3];
+    inst->stats.steals = cnt[4];
+    inst->stats.iterations = cnt[5];
+    inst->stats.kernel_seconds = ms * 1e-3;
+    inst->stats.final_ub = final_ub;
+    inst->stats.explorers = K;
+    inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PFSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// solve_internal.h -- arguments and constants of the explorer-pool kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pfsp {
+
+constexpr int kSolveWarps = 12;          // explorers (warps) per CTA at most
+constexpr int kPrunedLB = 0x7fffffff;     // bound stored for a pruned cell
+constexpr int kWaitLimit = 1 << 21;       // polls of a thief waiting for an answer
+constexpr int kErrStealWait = 1;          // error detail: a steal answer never came
+constexpr int kErrNoProgress = 2;         // error detail: no decomposition for kWatchdogNs
+constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
+#define PFSP_FWD_DIR 0
+
+struct SolveArgs {
+    // instance tables (same layout as the bounding kernel)
+    const int32_t *tab;
+    int tab_words;
+    int n, m, S;
+    int off_pm, off_tot, off_kl, off_rank, off_ptab;
+    int warp_words;  // bound scratch words per warp (excluding explorer words)
+    int bound;       // PFSP_LB1 or PFSP_LB2
+    int capped;      // MinMin on min(bound, cap)
+    int cap;
+    int K;           // explorers = warps in the grid
+    uint8_t *rows_job;    // [K][n][n]
+    int32_t *rows_lb;     // [K][n][n]
+    uint8_t *in_start;    // [K][64] start digits of an incoming interval
+    uint8_t *in_end;      // [K][65] end: [0] = coefficient of n!, [1..n] digits
+    int *mailbox;         // [K] thief id or -1
+    int *response;        // [K] 0 waiting, 1 granted, 2 denied
+    float *len_est;       // [K] log2 of the remaining interval length, -1 if empty
+    int *active;          // explorers holding work
+    int *ub;              // incumbent (exclusive)
+    unsigned long long *best_key;  // (cmax << 32) | explorer
+    uint8_t *best_perm;   // [K][64]
+    unsigned long long *counters;  // decomposed, bounded, leaves, pruned, steals, iters, limit count
+    long long node_limit;
+    unsigned long long time_limit_ns;  // stop after this long on the device clock; 0 = none
+    int *stop;            // 0 run, 1 node limit, 2 time limit, 3 error
+    int *err;
+    float min_steal;      // smallest interval length (leaves) a victim gives away
+    int check_every;      // power of two: iterations between limit checks
+};
+
+int solve_warp_words(int n, int m, int bound);
+int solve_occupancy(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+
+}  // namespace pfsp

@@ -53,6 +53,13 @@ class pfsp_stats_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pfsp_options(ctypes.Structure):
+    _fields_ = [("init_ub", ctypes.c_int32), ("node_limit", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
+                ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double),
+                ("reserved", ctypes.c_int * 8)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpfsp_gb300.so is not built (run __graft_entry__.build()); "
                       "the library has no CPU fallback")
@@ -69,6 +76,11 @@ _lib.pfsp_bound_batch.restype = ctypes.c_int
 _lib.pfsp_bound_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
 _lib.pfsp_bound_batch_dev.restype = ctypes.c_int
 _lib.pfsp_bound_batch_dev.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pfsp_default_options.restype = None
+_lib.pfsp_default_options.argtypes = [ctypes.POINTER(pfsp_options)]
+_lib.pfsp_solve.restype = ctypes.c_int
+_lib.pfsp_solve.argtypes = [_vp, ctypes.POINTER(pfsp_options), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
 
@@ -153,3 +165,25 @@ def pfsp_stats(inst: Instance) -> dict:
     s = pfsp_stats_t()
     _check(_lib.pfsp_stats(inst.handle, ctypes.byref(s)))
     return s.as_dict()
+
+
+def pfsp_default_options(**fields) -> pfsp_options:
+    """Defaults of the library, then the given fields (names as in the C struct)."""
+    o = pfsp_options()
+    _lib.pfsp_default_options(ctypes.byref(o))
+    for k, v in fields.items():
+        setattr(o, k, v)
+    return o
+
+
+def pfsp_solve(inst: Instance, opts: pfsp_options = None, **fields) -> dict:
+    """Solve; returns dict(cmax, perm, outcome, **stats)."""
+    if opts is None:
+        opts = pfsp_default_options(**fields)
+    best = ctypes.c_int32()
+    out = ctypes.c_int()
+    perm = (ctypes.c_int32 * inst.n)(*([-1] * inst.n))
+    _check(_lib.pfsp_solve(inst.handle, ctypes.byref(opts), ctypes.byref(best), perm, ctypes.byref(out)))
+    r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value)
+    r.update(pfsp_stats(inst))
+    return r
