@@ -167,6 +167,31 @@ typedef struct {
 
 int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
 
+/*
+ * pfsp_solve for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment variant).  It solves the instance given
+ * directly by n, m and p (same layout and limits as pfsp_load_instance) with
+ * the same options, outcomes and counters as pfsp_solve, but calls no
+ * cudaMalloc or cudaFree: its device scratch -- the instance tables and the
+ * explorer pool -- is one static 8 MiB array per device, created when the
+ * library loads and kept until the process exits.  Use it where allocating is
+ * not allowed: a service that reserves its memory at start-up, an application
+ * whose device memory belongs to another allocator, or a caller that cannot
+ * afford the device synchronisation an allocation implies.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture begins.
+ *   - Every call shares the array and overwrites what the previous call left;
+ *     calls that overlap on the GPU (other threads or streams) race and must
+ *     be serialised by the caller.
+ *   - When the tables plus even a one-explorer-per-SM pool exceed 8 MiB (large
+ *     n), the call fails with PFSP_ERR_UNSUPPORTED; fewer explorers per SM are
+ *     used automatically when that makes the pool fit.
+ *   - stats may be NULL; otherwise it receives the solve's counters.
+ * Returns the same codes as pfsp_solve.
+ */
+int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_options *opt, int32_t *best_cmax,
+                       int32_t *best_perm, int *outcome, pfsp_stats_t *stats);
+
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);
 

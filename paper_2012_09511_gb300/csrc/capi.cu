@@ -65,7 +65,7 @@ static std::vector<int> johnson_lag_order(int n, int m, const int32_t *p, int k,
     return ord;
 }
 
-static void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob) {
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob) {
     const int n = L.n, m = L.m;
     blob.assign(L.words, 0);
     for (int k = 0; k < m; ++k)

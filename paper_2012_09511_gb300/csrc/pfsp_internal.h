@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/pfsp.h"
@@ -61,5 +63,9 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
 
 // Error reporting shared by the C-ABI translation units.
 int set_error(int code, const char *fmt, ...);
+
+// Host-side builders shared by the entry points (capi.cu, solve_capi.cu).
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob);
+int neh(int n, int m, const int32_t *p, std::vector<int> &perm);
 
 }  // namespace pfsp

@@ -81,6 +81,10 @@ _lib.pfsp_default_options.argtypes = [ctypes.POINTER(pfsp_options)]
 _lib.pfsp_solve.restype = ctypes.c_int
 _lib.pfsp_solve.argtypes = [_vp, ctypes.POINTER(pfsp_options), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]
+_lib.pfsp_solve_noalloc.restype = ctypes.c_int
+_lib.pfsp_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(pfsp_options),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(pfsp_stats_t)]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
 
@@ -186,4 +190,21 @@ def pfsp_solve(inst: Instance, opts: pfsp_options = None, **fields) -> dict:
     _check(_lib.pfsp_solve(inst.handle, ctypes.byref(opts), ctypes.byref(best), perm, ctypes.byref(out)))
     r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value)
     r.update(pfsp_stats(inst))
+    return r
+
+
+def pfsp_solve_noalloc(p, opts: pfsp_options = None, **fields) -> dict:
+    """pfsp_solve without device allocations (static scratch); p is [n, m] job-major."""
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    n, m = p.shape
+    if opts is None:
+        opts = pfsp_default_options(**fields)
+    best = ctypes.c_int32()
+    out = ctypes.c_int()
+    perm = (ctypes.c_int32 * n)(*([-1] * n))
+    st = pfsp_stats_t()
+    _check(_lib.pfsp_solve_noalloc(n, m, _ptr(p), ctypes.byref(opts), ctypes.byref(best), perm,
+                                   ctypes.byref(out), ctypes.byref(st)))
+    r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value)
+    r.update(st.as_dict())
     return r
