@@ -101,6 +101,20 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
                          const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out,
                          void *stream);
 
+/* Counters reported by pfsp_stats, pfsp_solve_batch and pfsp_solve_noalloc. */
+typedef struct {
+    uint64_t decomposed;       /* parents whose children were bounded (root counts 1) */
+    uint64_t bounded_children; /* children bounded: sum of 2(n - d1 - d2) over parents */
+    uint64_t leaves;           /* complete schedules evaluated */
+    uint64_t pruned;           /* children of the chosen direction discarded (bound >= incumbent) */
+    uint64_t steals;           /* successful device work-stealing operations */
+    uint64_t iterations;       /* explorer loop iterations summed over explorers */
+    double seconds;            /* wall time of the call (host clock) */
+    double kernel_seconds;     /* device time of the main kernel (CUDA events) */
+    int32_t final_ub;          /* incumbent at the end of a solve */
+    int32_t explorers;         /* explorers used by a solve */
+} pfsp_stats_t;
+
 /*
  * Options of a solve.  Call pfsp_default_options first, then change fields.
  *   init_ub      exclusive incumbent: only schedules with makespan < init_ub
@@ -151,20 +165,42 @@ void pfsp_default_options(pfsp_options *opt);
 int pfsp_solve(const pfsp_instance *inst, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
                int *outcome);
 
-/* Counters of the last pfsp_bound_batch / pfsp_solve call on an instance. */
-typedef struct {
-    uint64_t decomposed;       /* parents whose children were bounded (root counts 1) */
-    uint64_t bounded_children; /* children bounded: sum of 2(n - d1 - d2) over parents */
-    uint64_t leaves;           /* complete schedules evaluated */
-    uint64_t pruned;           /* children of the chosen direction discarded (bound >= incumbent) */
-    uint64_t steals;           /* successful device work-stealing operations */
-    uint64_t iterations;       /* explorer loop iterations summed over explorers */
-    double seconds;            /* wall time of the call (host clock) */
-    double kernel_seconds;     /* device time of the main kernel (CUDA events) */
-    int32_t final_ub;          /* incumbent at the end of a solve */
-    int32_t explorers;         /* explorers used by a solve */
-} pfsp_stats_t;
+/*
+ * Solve `count` independent instances (any mix of n and m, all loaded on the
+ * current device) in one persistent launch of the explorer pool, recorded in
+ * a CUDA graph and launched from it.  Batching is not in the paper; each
+ * instance is solved exactly as pfsp_solve would (same bounds, MinMin,
+ * pruning, work stealing among the explorers working on that instance).
+ * Every CTA first takes the next unclaimed instance; when none is left, CTAs
+ * that finish join the running instance with the most busy explorers.
+ *   init_ubs    count exclusive incumbents, or NULL (NEH for every instance;
+ *               an entry INT32_MAX also means NEH).
+ *   best_cmax   count outputs; outcomes: count outcome codes.
+ *   best_perms  NULL or count rows of 64 int32: row i holds instance i's best
+ *               permutation in its first n_i entries (-1 elsewhere, and -1
+ *               throughout when the outcome is PFSP_PROVEN_NO_BETTER).
+ *   stats       NULL or the counters summed over the batch.
+ * node_limit applies to each instance; time_limit_s to the whole launch.
+ * Errors: as pfsp_solve; PFSP_ERR_INVALID also for an instance on another
+ * device.
+ */
+int pfsp_solve_batch(const pfsp_instance *const *insts, int count, const pfsp_options *opt,
+                     const int32_t *init_ubs, int32_t *best_cmax, int32_t *best_perms, int *outcomes,
+                     pfsp_stats_t *stats);
 
+/*
+ * Autotuner of the batched pool (not in the paper): runs pfsp_solve_batch on
+ * the first `sample` instances (0 = up to 32) for each point of a small grid
+ * of launch parameters -- explorers per SM {4, 8, 12}, iterations between limit
+ * checks and length publications {8, 32}, smallest interval a victim splits
+ * {2, 720} -- and writes to *best the options (base plus the fastest point by
+ * device time).  The children handled per warp are not a parameter: a warp
+ * always bounds every child of the node it decomposes.
+ */
+int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp_options *base, int sample,
+                        pfsp_options *best);
+
+/* Counters of the last pfsp_bound_batch or pfsp_solve call on `inst`. */
 int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
 
 /*

@@ -418,6 +418,10 @@ __device__ inline void stage_tables(int *dst, const int32_t *src, int words, uin
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
         __syncthreads();
     }
+    // every thread is past the wait: retire the barrier so that a later call
+    // (a CTA that moves to another instance) can initialise it again
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sbar) : "memory");
+    __syncthreads();
 }
 
 constexpr int kWarpsPerCta = 14;

@@ -133,8 +133,8 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
         offs[2] = take((size_t)K * n * n * 4);
         offs[3] = take((size_t)K * 64);
         offs[4] = take((size_t)K * 65);
-        offs[5] = take((size_t)K * 4);
-        offs[6] = take((size_t)K * 4);
+        offs[5] = take((size_t)K * 8);
+        offs[6] = take((size_t)K * 8);
         offs[7] = take((size_t)K * 4);
         offs[8] = take((size_t)K * 64);
         offs[9] = take(8 * 8);
@@ -159,14 +159,20 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
                          "(%zu bytes with one explorer per SM)",
                          n, m, kNoAllocBytes, need);
     a.K = K;
+    a.row_stride = n * n;
+    a.inst_of = nullptr;
+    a.my_inst = 0;
+    a.inst_perm = nullptr;
+    a.perm_lock = nullptr;
+    a.perm_cmax = nullptr;
     char *b = (char *)scratch;
     a.tab = (const int32_t *)(b + offs[0]);
     a.rows_job = (uint8_t *)(b + offs[1]);
     a.rows_lb = (int32_t *)(b + offs[2]);
     a.in_start = (uint8_t *)(b + offs[3]);
     a.in_end = (uint8_t *)(b + offs[4]);
-    a.mailbox = (int *)(b + offs[5]);
-    a.response = (int *)(b + offs[6]);
+    a.mailbox = (unsigned long long *)(b + offs[5]);
+    a.response = (unsigned long long *)(b + offs[6]);
     a.len_est = (float *)(b + offs[7]);
     a.best_perm = (uint8_t *)(b + offs[8]);
     a.counters = (unsigned long long *)(b + offs[9]);
@@ -212,8 +218,8 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     int hsc[6] = {(int)Kp, ub0, 0, 0, -1, -1};
     cudaStream_t st = 0;
     cudaError_t e = cudaMemcpyAsync((void *)a.tab, blob.data(), (size_t)L.words * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);

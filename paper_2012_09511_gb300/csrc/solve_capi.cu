@@ -136,6 +136,12 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     const int blocks = nsm * per_sm;
     const int K = blocks * warps;
     a.K = K;
+    a.row_stride = n * n;
+    a.inst_of = nullptr;
+    a.my_inst = 0;
+    a.inst_perm = nullptr;
+    a.perm_lock = nullptr;
+    a.perm_cmax = nullptr;
 
     // initial partition of [0, n!): equal chunks of the first L levels
     int Lv = 0;
@@ -170,7 +176,7 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     };
     const size_t o_rj = take((size_t)K * n * n), o_rl = take((size_t)K * n * n * 4);
     const size_t o_is = take((size_t)K * 64), o_ie = take((size_t)K * 65);
-    const size_t o_mb = take((size_t)K * 4), o_rs = take((size_t)K * 4), o_le = take((size_t)K * 4);
+    const size_t o_mb = take((size_t)K * 8), o_rs = take((size_t)K * 8), o_le = take((size_t)K * 4);
     const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64);
     DeviceSolveState D;
     cudaError_t e = cudaMalloc(&D.blob, off);
@@ -183,8 +189,8 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     a.rows_lb = (int32_t *)(b + o_rl);
     a.in_start = (uint8_t *)(b + o_is);
     a.in_end = (uint8_t *)(b + o_ie);
-    a.mailbox = (int *)(b + o_mb);
-    a.response = (int *)(b + o_rs);
+    a.mailbox = (unsigned long long *)(b + o_mb);
+    a.response = (unsigned long long *)(b + o_rs);
     a.len_est = (float *)(b + o_le);
     a.best_perm = (uint8_t *)(b + o_bp);
     a.counters = (unsigned long long *)(b + o_ct);
@@ -207,8 +213,8 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
-    e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 4, st);
+    e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);

@@ -11,6 +11,10 @@ constexpr int kPrunedLB = 0x7fffffff;     // bound stored for a pruned cell
 constexpr int kWaitLimit = 1 << 21;       // polls of a thief waiting for an answer
 constexpr int kErrStealWait = 1;          // error detail: a steal answer never came
 constexpr int kErrNoProgress = 2;         // error detail: no decomposition for kWatchdogNs
+constexpr int kErrBadInterval = 3;        // error detail: a received interval was not valid
+constexpr int kErrRecordLock = 4;         // error detail: the best-permutation record stayed locked
+constexpr int kLockLimit = 1 << 20;       // attempts to take that lock
+constexpr unsigned long long kNoRequest = ~0ull;  // empty mailbox
 constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
 #define PFSP_FWD_DIR 0
 
@@ -25,12 +29,18 @@ struct SolveArgs {
     int capped;      // MinMin on min(bound, cap)
     int cap;
     int K;           // explorers = warps in the grid
-    uint8_t *rows_job;    // [K][n][n]
-    int32_t *rows_lb;     // [K][n][n]
+    int row_stride;       // row elements per explorer (n * n, or the batch's largest n squared)
+    uint8_t *rows_job;    // [K][row_stride]
+    int32_t *rows_lb;     // [K][row_stride]
+    const int *inst_of;   // batched solves: [K] instance each explorer works on (NULL otherwise)
+    int my_inst;          // batched solves: this CTA's instance
+    int *perm_lock;       // batched solves: lock of this instance's best-permutation record
+    int *perm_cmax;       // batched solves: makespan of the recorded permutation
+    uint8_t *inst_perm;   // batched solves: [64] recorded permutation (NULL: per-explorer slots)
     uint8_t *in_start;    // [K][64] start digits of an incoming interval
     uint8_t *in_end;      // [K][65] end: [0] = coefficient of n!, [1..n] digits
-    int *mailbox;         // [K] thief id or -1
-    int *response;        // [K] 0 waiting, 1 granted, 2 denied
+    unsigned long long *mailbox;   // [K] request: instance << 40 | sequence << 20 | thief, or kNoRequest
+    unsigned long long *response;  // [K] answer to a thief: sequence << 2 | 1 granted / 2 denied
     float *len_est;       // [K] log2 of the remaining interval length, -1 if empty
     int *active;          // explorers holding work
     int *ub;              // incumbent (exclusive)

@@ -28,455 +28,9 @@
 
 #include <cfloat>
 
-#include "bound_device.cuh"
-#include "pfsp_internal.h"
-#include "solve_internal.h"
+#include "explorer_device.cuh"
 
 namespace pfsp {
-
-__device__ inline unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ inline int ld_volatile(const int *p) { return *(const volatile int *)p; }
-
-// Per-warp explorer scratch in shared memory (int words).
-struct ExplorerSmem {
-    int V[64];      // digit selected at each level
-    int dir[64];    // branching direction of each level (0 fwd, 1 bwd)
-    int E[64];      // end of the interval (digits); etop = coefficient of n!
-    int D[64];      // start of an incoming interval
-    int perm[64];   // staging of the decoded node
-    double w[64];   // (n-1-i)! as double, for length estimates
-    int etop;
-    int pad[3];
-};
-constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 4);
-
-struct Stats {
-    unsigned long long decomposed, bounded, leaves, pruned, steals, iters;
-};
-
-template <int NW, int MT>
-struct Explorer {
-    const SolveArgs &a;
-    const SmemTables &T;
-    const WarpScratch &W;
-    ExplorerSmem &X;
-    int n, m, S, lane, me;
-    uint8_t *rj;
-    int32_t *rl;
-    int I;  // current level (-1: at the root)
-    Stats st;
-    unsigned rng;
-    unsigned long long pending_nodes;
-    unsigned long long deadline;
-
-    __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_)
-        : a(a_), T(T_), W(W_), X(X_), me(me_) {
-        n = a.n;
-        m = a.m;
-        S = a.S;
-        lane = threadIdx.x & 31;
-        rj = a.rows_job + (size_t)me * n * n;
-        rl = a.rows_lb + (size_t)me * n * n;
-        I = -1;
-        st = Stats{0, 0, 0, 0, 0, 0};
-        rng = 0x9e3779b9u * (me + 1) ^ 0x85ebca6bu;
-        pending_nodes = 0;
-        deadline = a.time_limit_ns ? global_ns() + a.time_limit_ns : 0ull;
-        for (int i = lane; i < 64; i += 32) {
-            double w = 1.0;
-            for (int t = 2; t <= n - 1 - i; ++t) w *= t;
-            X.w[i] = w;
-        }
-        __syncwarp();
-    }
-
-    // warp-uniform reads of shared counters (lane 0 loads, all lanes agree)
-    __device__ int ub() const {
-        int v = 0;
-        if (lane == 0) v = ld_volatile(a.ub);
-        return __shfl_sync(PFSP_FULL, v, 0);
-    }
-    __device__ int active_count() const {
-        int v = 0;
-        if (lane == 0) v = ld_volatile(a.active);
-        return __shfl_sync(PFSP_FULL, v, 0);
-    }
-
-    // lo(current position) < end ?  Position digits are V[0..I], zeros below.
-    __device__ bool pos_before_end() const {
-        if (X.etop) return true;
-        for (int h = 0; h < NW; ++h) {
-            int i = lane + 32 * h;
-            int v = (i < n && i <= I) ? X.V[i] : 0;
-            int e = i < n ? X.E[i] : 0;
-            unsigned diff = __ballot_sync(PFSP_FULL, v != e);
-            if (diff) {
-                int f = __ffs(diff) - 1;
-                int vf = __shfl_sync(PFSP_FULL, v, f), ef = __shfl_sync(PFSP_FULL, e, f);
-                return vf < ef;
-            }
-        }
-        return false;  // equal
-    }
-
-    // log2 of (end - pos), or -1 if empty (estimate for victim choice only)
-    __device__ float log2_length() const {
-        double t = 0.0;
-        for (int h = 0; h < NW; ++h) {
-            int i = lane + 32 * h;
-            if (i < n) {
-                int v = i <= I ? X.V[i] : 0;
-                t += (double)(X.E[i] - v) * X.w[i];
-            }
-        }
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(PFSP_FULL, t, o);
-        if (X.etop) t += X.w[0] * n;
-        return t >= 1.0 ? (float)log2(t) : -1.0f;
-    }
-
-    // Find the next node: the first live cell at or after V[I] on level I,
-    // backtracking when a row is exhausted (Section 2.5, selection).
-    __device__ bool select() {
-        while (I >= 0) {
-            const int len = n - I;
-            const int v = X.V[I];
-            const int ubv = ub();
-            unsigned b0 = 0, b1 = 0;
-            {
-                int c = lane;
-                bool ok = c < len && c >= v && rl[I * n + c] < ubv;
-                b0 = __ballot_sync(PFSP_FULL, ok);
-            }
-            if (NW == 2 && !b0) {
-                int c = lane + 32;
-                bool ok = c < len && c >= v && rl[I * n + c] < ubv;
-                b1 = __ballot_sync(PFSP_FULL, ok);
-            }
-            if (b0 | b1) {
-                int c = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
-                if (lane == 0) X.V[I] = c;
-                __syncwarp();
-                return true;
-            }
-            --I;
-            if (I >= 0 && lane == 0) X.V[I] += 1;
-            __syncwarp();
-        }
-        return false;
-    }
-
-    // Decompose the node at level I (I = -1: the root): bound both children
-    // sets, choose the direction by MinMin, write row I+1, handle leaves.
-    __device__ void expand(bool counted) {
-        // ---- decode the node into [sigma1 | unscheduled | sigma2] -------------
-        unsigned long long sched = 0;
-        int d1 = 0, d2 = 0;
-        {
-            unsigned fw[2] = {0, 0}, bw[2] = {0, 0};
-            int jobv[2] = {0, 0}, dv[2] = {0, 0};
-            for (int h = 0; h < NW; ++h) {
-                int i = lane + 32 * h;
-                bool on = i <= I && i < n;
-                if (on) {
-                    jobv[h] = rj[i * n + X.V[i]];
-                    dv[h] = X.dir[i];
-                }
-                fw[h] = __ballot_sync(PFSP_FULL, on && dv[h] == PFSP_FWD_DIR);
-                bw[h] = __ballot_sync(PFSP_FULL, on && dv[h] != PFSP_FWD_DIR);
-                unsigned long long bit = on ? (1ull << jobv[h]) : 0ull;
-                unsigned lo = __reduce_or_sync(PFSP_FULL, (unsigned)(bit & 0xffffffffull));
-                unsigned hi = __reduce_or_sync(PFSP_FULL, (unsigned)(bit >> 32));
-                sched |= ((unsigned long long)hi << 32) | lo;
-            }
-            d1 = __popc(fw[0]) + __popc(fw[1]);
-            d2 = __popc(bw[0]) + __popc(bw[1]);
-            for (int h = 0; h < NW; ++h) {
-                int i = lane + 32 * h;
-                if (i <= I && i < n) {
-                    unsigned below = (1u << lane) - 1;
-                    int pos;
-                    if (dv[h] == PFSP_FWD_DIR) pos = (h ? __popc(fw[0]) : 0) + __popc(fw[h] & below);
-                    else pos = n - 1 - ((h ? __popc(bw[0]) : 0) + __popc(bw[h] & below));
-                    X.perm[pos] = jobv[h];
-                }
-            }
-            for (int h = 0; h < NW; ++h) {
-                int j = lane + 32 * h;
-                if (j < n && !((sched >> j) & 1ull)) {
-                    unsigned long long free_below = ~sched & ((1ull << j) - 1);
-                    X.perm[d1 + __popcll(free_below)] = j;
-                }
-            }
-            __syncwarp();
-        }
-        const int job0 = lane < n ? X.perm[lane] : 0;
-        const int job1 = (NW == 2 && lane + 32 < n) ? X.perm[lane + 32] : 0;
-        ChildBounds<NW> cb;
-        const int kind = a.bound == PFSP_LB2 ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
-        decompose_node<NW, MT>(T, W, n, m, S, kind, job0, job1, d1, d2, cb);
-        const int u = cb.u;
-
-        // ---- MinMin (Section 2.3) ----------------------------------------------
-        int vf[NW], vb[NW];
-        int mn = INT_MAX;
-        for (int h = 0; h < NW; ++h) {
-            int c = lane + 32 * h;
-            vf[h] = a.bound == PFSP_LB2 ? cb.lb2f[h] : cb.lb1f[h];
-            vb[h] = a.bound == PFSP_LB2 ? cb.lb2b[h] : cb.lb1b[h];
-            if (c < u) {
-                int xf = a.capped ? min(vf[h], a.cap) : vf[h];
-                int xb = a.capped ? min(vb[h], a.cap) : vb[h];
-                mn = min(mn, min(xf, xb));
-            }
-        }
-        mn = __reduce_min_sync(PFSP_FULL, mn);
-        int cf = 0, cbk = 0;
-        long long sf = 0, sb = 0;
-        for (int h = 0; h < NW; ++h) {
-            int c = lane + 32 * h;
-            bool on = c < u;
-            int xf = a.capped ? min(vf[h], a.cap) : vf[h];
-            int xb = a.capped ? min(vb[h], a.cap) : vb[h];
-            cf += __popc(__ballot_sync(PFSP_FULL, on && xf == mn));
-            cbk += __popc(__ballot_sync(PFSP_FULL, on && xb == mn));
-            sf += on ? xf : 0;
-            sb += on ? xb : 0;
-        }
-        for (int o = 16; o; o >>= 1) {
-            sf += __shfl_xor_sync(PFSP_FULL, sf, o);
-            sb += __shfl_xor_sync(PFSP_FULL, sb, o);
-        }
-        int dir;
-        if (cf != cbk) dir = cf < cbk ? 0 : 1;
-        else if (sf != sb) dir = sf > sb ? 0 : 1;
-        else dir = 0;
-
-        // ---- new row: children of the chosen direction, pruned against UB ------
-        const int row = I + 1;
-        int ubv = ub();
-        int npruned = 0;
-        for (int h = 0; h < NW; ++h) {
-            int c = lane + 32 * h;
-            int lb = dir ? vb[h] : vf[h];
-            bool on = c < u;
-            bool leaf = on && u == 1;
-            if (leaf && lb < ubv) {
-                // a complete schedule better than the incumbent (its bound is
-                // its makespan): record it, then lower the incumbent
-                int j = W.ul[c];
-                int prev = atomicMin(a.ub, lb);
-                if (lb < prev) {
-                    uint8_t *bp = a.best_perm + (size_t)me * 64;
-                    for (int q = 0; q < n; ++q) bp[q] = (uint8_t)(q == d1 ? j : X.perm[q]);
-                    __threadfence();
-                    atomicMin(a.best_key, ((unsigned long long)(unsigned)lb << 32) | (unsigned)me);
-                }
-            }
-            bool keep = on && !leaf && lb < ubv;
-            npruned += __popc(__ballot_sync(PFSP_FULL, on && !keep && !(leaf && lb < ubv)));
-            if (on) {
-                rj[row * n + c] = (uint8_t)W.ul[c];
-                rl[row * n + c] = keep ? lb : kPrunedLB;
-            }
-        }
-        if (lane == 0) {
-            X.dir[row] = dir;
-            X.V[row] = 0;
-        }
-        I = row;
-        __syncwarp();
-        if (counted) {
-            st.decomposed += 1;
-            st.bounded += 2 * u;
-            if (u == 1) st.leaves += 2;
-            st.pruned += npruned;
-            pending_nodes += 1;
-        }
-    }
-
-    // Rebuild the rows along the path to the start digits D and position the
-    // explorer on the first live node at or after start.  Returns false when
-    // no such node exists.
-    __device__ bool init_at_start() {
-        I = -1;
-        bool zero = true;
-        for (int h = 0; h < NW; ++h) {
-            int i = lane + 32 * h;
-            zero &= __all_sync(PFSP_FULL, i >= n || X.D[i] == 0);
-        }
-        expand(zero);  // the root; counted only by the explorer starting at 0
-        while (true) {
-            // I is the level whose row has just been built; follow the digit D[I]
-            const int d = X.D[I];
-            if (lane == 0) X.V[I] = d;
-            __syncwarp();
-            bool alive = rl[I * n + d] < ub();
-            if (!alive) {
-                if (lane == 0) X.V[I] = d + 1;
-                __syncwarp();
-                return select();
-            }
-            bool rest_zero = true;
-            for (int h = 0; h < NW; ++h) {
-                int i = lane + 32 * h;
-                rest_zero &= __all_sync(PFSP_FULL, i >= n || i <= I || X.D[i] == 0);
-            }
-            if (rest_zero || I >= n - 2) return true;  // this node starts the interval
-            expand(false);
-        }
-    }
-
-    // Answer a steal request if one is waiting (victim side).
-    __device__ void service(bool active) {
-        int t = 0;
-        if (lane == 0) t = ld_volatile(a.mailbox + me);
-        t = __shfl_sync(PFSP_FULL, t, 0);
-        if (t < 0) return;
-        int granted = 0;
-        if (active && lane == 0) {
-            // remaining territory [pos, end): pos = V[0..I], zeros below
-            int s[64], q[64];
-            int carry = 0;
-            for (int i = n - 1; i >= 0; --i) {
-                int p = i <= I ? X.V[i] : 0;
-                int v = p + X.E[i] + carry;
-                int r = n - i;
-                carry = v >= r;
-                s[i] = v - (carry ? r : 0);
-            }
-            int top = X.etop + carry;
-            int rem = top & 1;
-            for (int i = 0; i < n; ++i) {
-                int cur = rem * (n - i) + s[i];
-                q[i] = cur >> 1;
-                rem = cur & 1;
-            }
-            // mid > pos ?
-            int cmp = 0;
-            for (int i = 0; i < n && cmp == 0; ++i) {
-                int p = i <= I ? X.V[i] : 0;
-                cmp = q[i] > p ? 1 : (q[i] < p ? -1 : 0);
-            }
-            // length estimate for the minimum steal size
-            double len = X.etop ? X.w[0] * n : 0.0;
-            for (int i = 0; i < n; ++i) len += (double)(X.E[i] - (i <= I ? X.V[i] : 0)) * X.w[i];
-            if (cmp > 0 && len >= (double)a.min_steal) {
-                uint8_t *ds = a.in_start + (size_t)t * 64;
-                uint8_t *de = a.in_end + (size_t)t * 65;
-                for (int i = 0; i < n; ++i) {
-                    ds[i] = (uint8_t)q[i];
-                    de[1 + i] = (uint8_t)X.E[i];
-                }
-                de[0] = (uint8_t)X.etop;
-                for (int i = 0; i < n; ++i) X.E[i] = q[i];
-                X.etop = 0;
-                atomicAdd(a.active, 1);
-                granted = 1;
-            }
-            __threadfence();
-            atomicExch(a.response + t, granted ? 1 : 2);
-            atomicExch(a.mailbox + me, -1);
-        }
-        __syncwarp();
-    }
-
-    __device__ void publish_length(bool active) {
-        float l = active ? log2_length() : -1.0f;
-        if (lane == 0) a.len_est[me] = l;
-    }
-
-    __device__ bool stopped() const {
-        int s = 0;
-        if (lane == 0) s = ld_volatile(a.stop);
-        return __shfl_sync(PFSP_FULL, s, 0) != 0;
-    }
-
-    __device__ void flush_limits() {
-        if (lane == 0 && pending_nodes) {
-            unsigned long long tot = atomicAdd(a.counters + 6, pending_nodes) + pending_nodes;
-            pending_nodes = 0;
-            if (a.node_limit > 0 && tot >= (unsigned long long)a.node_limit) atomicCAS(a.stop, 0, 1);
-        }
-        if (lane == 0 && deadline && global_ns() > deadline) atomicCAS(a.stop, 0, 2);
-        __syncwarp();
-    }
-
-    // Thief side: pick a victim, post a request, wait (bounded) for the answer.
-    // Returns 1 = got an interval (in D / E), 0 = nothing now, -1 = give up.
-    __device__ int try_steal() {
-        const float min_log = log2f(fmaxf(a.min_steal, 1.0f));
-        // scan a random window first, then everything
-        int best = -1;
-        float bestv = min_log;
-        const int K = a.K;
-        for (int pass = 0; pass < 2 && best < 0; ++pass) {
-            int start = 0, count = K;
-            if (pass == 0) {
-                rng = rng * 1664525u + 1013904223u;
-                start = (int)(rng % (unsigned)K);
-                count = min(K, 64);
-            }
-            for (int o = lane; o < count; o += 32) {
-                int e = (start + o) % K;
-                float l = e == me ? -1.0f : *(volatile float *)(a.len_est + e);
-                if (l > bestv) {
-                    bestv = l;
-                    best = e;
-                }
-            }
-            for (int o = 16; o; o >>= 1) {
-                float ov = __shfl_xor_sync(PFSP_FULL, bestv, o);
-                int oe = __shfl_xor_sync(PFSP_FULL, best, o);
-                if (ov > bestv || (ov == bestv && oe > best)) {
-                    bestv = ov;
-                    best = oe;
-                }
-            }
-        }
-        if (best < 0) return 0;
-        int posted = 0;
-        if (lane == 0) {
-            atomicExch(a.response + me, 0);
-            __threadfence();
-            posted = atomicCAS(a.mailbox + best, -1, me) == -1;
-        }
-        posted = __shfl_sync(PFSP_FULL, posted, 0);
-        if (!posted) return 0;
-        int r = 0;
-        for (int it = 0; it < kWaitLimit; ++it) {
-            if (lane == 0) r = ld_volatile(a.response + me);
-            r = __shfl_sync(PFSP_FULL, r, 0);
-            if (r) break;
-            service(false);  // deny requests addressed to this idle explorer
-            if (stopped() || active_count() == 0) return -1;
-            __nanosleep(200);
-        }
-        if (r == 0) {
-            if (lane == 0) {
-                atomicExch(a.err, kErrStealWait);
-                atomicCAS(a.stop, 0, 3);
-            }
-            return -1;
-        }
-        if (r == 2) return 0;
-        __threadfence();
-        const uint8_t *ds = a.in_start + (size_t)me * 64;
-        const uint8_t *de = a.in_end + (size_t)me * 65;
-        for (int i = lane; i < n; i += 32) {
-            X.D[i] = ((volatile const uint8_t *)ds)[i];
-            X.E[i] = ((volatile const uint8_t *)de)[1 + i];
-        }
-        if (lane == 0) X.etop = ((volatile const uint8_t *)de)[0];
-        __syncwarp();
-        st.steals += 1;
-        return 1;
-    }
-};
 
 template <int NW, int MT>
 __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a) {
@@ -498,102 +52,16 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
     const int me = blockIdx.x * warps + wib;
     if (me >= a.K) return;
 
-    Explorer<NW, MT> ex(a, T, W, X, me);
-    // initial interval
     for (int i = lane; i < a.n; i += 32) {
         X.D[i] = a.in_start[(size_t)me * 64 + i];
         X.E[i] = a.in_end[(size_t)me * 65 + 1 + i];
     }
-    if (lane == 0) X.etop = a.in_end[(size_t)me * 65];
-    __syncwarp();
-    bool nonempty = false;
-    {
-        // start < end ?
-        if (X.etop) nonempty = true;
-        else {
-            int f = -1;
-            for (int h = 0; h < NW && f < 0; ++h) {
-                int i = lane + 32 * h;
-                unsigned diff = __ballot_sync(PFSP_FULL, i < a.n && X.D[i] != X.E[i]);
-                if (diff) {
-                    int b = __ffs(diff) - 1;
-                    int di = __shfl_sync(PFSP_FULL, i < a.n ? X.D[i] : 0, b);
-                    int ei = __shfl_sync(PFSP_FULL, i < a.n ? X.E[i] : 0, b);
-                    nonempty = di < ei;
-                    f = b;
-                }
-            }
-        }
-    }
-    int state = nonempty ? 1 : 0;  // 0 empty, 1 needs init, 2 active
-    bool have_node = false;
-    unsigned iter = 0;
-    // watchdog of idle explorers: the global decomposition count must keep
-    // moving while some explorer holds work
-    unsigned long long seen = ~0ull, seen_at = global_ns();
-    while (true) {
-        ++iter;
-        if ((iter & (a.check_every - 1)) == 0) {
-            ex.flush_limits();
-            ex.publish_length(state == 2);
-        }
-        if (ex.stopped()) break;
-        ex.service(state == 2);
-        if (state == 1) {
-            have_node = ex.init_at_start();
-            state = 2;
-            ex.publish_length(true);
-        }
-        if (state == 2) {
-            ex.st.iters += 1;
-            if (!have_node) have_node = ex.select();
-            if (have_node && ex.pos_before_end()) {
-                ex.expand(true);
-                have_node = false;
-                continue;
-            }
-            // interval exhausted
-            state = 0;
-            have_node = false;
-            ex.publish_length(false);
-            if (lane == 0) atomicSub(a.active, 1);
-            __syncwarp();
-        }
-        // idle
-        if (ex.active_count() == 0) break;
-        {
-            int trip = 0;
-            if (lane == 0) {
-                unsigned long long now_cnt = *(volatile unsigned long long *)(a.counters + 6);
-                unsigned long long now = global_ns();
-                if (now_cnt != seen) {
-                    seen = now_cnt;
-                    seen_at = now;
-                } else if (now - seen_at > kWatchdogNs) {
-                    atomicExch(a.err, kErrNoProgress);
-                    atomicCAS(a.stop, 0, 3);
-                    trip = 1;
-                }
-            }
-            if (__shfl_sync(PFSP_FULL, trip, 0)) break;
-        }
-        int r = ex.try_steal();
-        if (r < 0) break;
-        if (r == 1) {
-            state = 1;
-            continue;
-        }
-        __nanosleep(500);
-    }
-    ex.flush_limits();
     if (lane == 0) {
-        atomicAdd(a.counters + 0, ex.st.decomposed);
-        atomicAdd(a.counters + 1, ex.st.bounded);
-        atomicAdd(a.counters + 2, ex.st.leaves);
-        atomicAdd(a.counters + 3, ex.st.pruned);
-        atomicAdd(a.counters + 4, ex.st.steals);
-        atomicAdd(a.counters + 5, ex.st.iters);
+        X.etop = a.in_end[(size_t)me * 65];
+        X.seq = 0;
     }
+    __syncwarp();
+    run_explorer<NW, MT>(a, T, W, X, me);
 }
 
 int solve_warp_words(int n, int m, int bound) {

@@ -85,6 +85,12 @@ _lib.pfsp_solve_noalloc.restype = ctypes.c_int
 _lib.pfsp_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(pfsp_options),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(pfsp_stats_t)]
+_lib.pfsp_solve_batch.restype = ctypes.c_int
+_lib.pfsp_solve_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options), _vp,
+                                  _vp, _vp, _vp, ctypes.POINTER(pfsp_stats_t)]
+_lib.pfsp_autotune_batch.restype = ctypes.c_int
+_lib.pfsp_autotune_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options),
+                                     ctypes.c_int, ctypes.POINTER(pfsp_options)]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
 
@@ -208,3 +214,33 @@ def pfsp_solve_noalloc(p, opts: pfsp_options = None, **fields) -> dict:
     r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value)
     r.update(st.as_dict())
     return r
+
+
+def _handles(insts):
+    arr = (_vp * len(insts))(*[i.handle for i in insts])
+    return arr
+
+
+def pfsp_solve_batch(insts, opts: pfsp_options = None, init_ubs=None, **fields) -> dict:
+    """Solve a list of Instances in one launch.  Returns dict(cmax [count], perms [count, 64],
+    outcomes [count], stats)."""
+    if opts is None:
+        opts = pfsp_default_options(**fields)
+    k = len(insts)
+    cm = np.zeros(k, dtype=np.int32)
+    out = np.zeros(k, dtype=np.int32)
+    perms = np.zeros((k, 64), dtype=np.int32)
+    ubs = None if init_ubs is None else np.ascontiguousarray(init_ubs, dtype=np.int32)
+    st = pfsp_stats_t()
+    _check(_lib.pfsp_solve_batch(_handles(insts), k, ctypes.byref(opts), _ptr(ubs), _ptr(cm), _ptr(perms),
+                                 _ptr(out), ctypes.byref(st)))
+    return dict(cmax=cm, perms=perms, outcomes=out, stats=st.as_dict())
+
+
+def pfsp_autotune_batch(insts, base: pfsp_options = None, sample=0) -> pfsp_options:
+    if base is None:
+        base = pfsp_default_options()
+    best = pfsp_options()
+    _check(_lib.pfsp_autotune_batch(_handles(insts), len(insts), ctypes.byref(base), int(sample),
+                                    ctypes.byref(best)))
+    return best
