@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1000000, help="nodes in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-proof leg")
     return ap.parse_args()
 
 
@@ -170,6 +171,36 @@ def cpu_baseline(p, perm, d1, d2, sample):
     children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
     return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (k, len(d1), dt)}
+
+
+def solve_leg(pfsp, seeds=range(1, 11)):
+    """Time-to-proof of the exact-solve workload (n = 20, m = 10, LB2): each seed
+    solved in proof mode with the incumbent at the oracle's optimum (fixed tree;
+    counts checked against the oracle's), and from its NEH schedule."""
+    from paper_2012_09511_gb300 import inputs
+    path = os.path.join(ROOT, "tests", "golden", "solve_20x10_lb2.json")
+    with open(path) as f:
+        gold = {r["seed"]: r for r in json.load(f)["results"]}
+    per, tot_proof, tot_find, tot_nodes, exact = [], 0.0, 0.0, 0, True
+    for seed in seeds:
+        g = gold[seed]
+        inst = pfsp.pfsp_load_instance(inputs.make_instance(20, 10, seed))
+        pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, init_ub=g["optimum"])  # warm
+        r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, init_ub=g["optimum"])
+        f = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2)
+        ok = (r["decomposed"] == g["proof_decomposed"] and f["cmax"] == g["optimum"]
+              and r["outcome"] == pfsp.PFSP_PROVEN_NO_BETTER)
+        exact &= ok
+        per.append({"seed": seed, "proof_s": r["kernel_seconds"], "nodes": r["decomposed"],
+                    "find_s": f["kernel_seconds"], "optimum": f["cmax"], "exact": ok})
+        tot_proof += r["kernel_seconds"]
+        tot_find += f["kernel_seconds"]
+        tot_nodes += r["decomposed"]
+    return {"workload": "n=20 m=10 uniform[1,99] seeds 1-10, LB2 + MinMin, proof mode at the optimum",
+            "time_to_proof_s": tot_proof, "time_to_optimum_from_neh_s": tot_find,
+            "decomposed_nodes": tot_nodes, "decomposed_nodes_per_s": tot_nodes / max(tot_proof, 1e-9),
+            "counts_and_optima_match_oracle": bool(exact), "per_seed": per,
+            "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds)}
 
 
 def run_reference(args):
@@ -314,6 +345,8 @@ def run_native(args):
     }
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample)
+    if not args.no_solve and ws == 1:
+        out["solve"] = solve_leg(pfsp)
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
