@@ -228,6 +228,39 @@ int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
 int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_options *opt, int32_t *best_cmax,
                        int32_t *best_perm, int *outcome, pfsp_stats_t *stats);
 
+/*
+ * Ordering network (not in the paper): a two-hidden-layer MLP (128 ReLU
+ * units each, bf16 weights, fp32 accumulation, tensor-core kernels) that
+ * reads a node's per-machine front, back and remaining work, each divided by
+ * the instance's mean machine load (sum of p / m), and outputs one "descend
+ * first" logit (column 0) and one logit per machine pair k < l (columns
+ * 1..m(m-1)/2, in the order k = 0..m-2, l = k+1..m-1).  Inputs are padded to
+ * D0 = 3m rounded up to 16 columns, outputs to O = 1 + m(m-1)/2 rounded up to
+ * 16.  Parameters are one fp32 vector [W1 (D0 x 128) | b1 | W2 (128 x 128) |
+ * b2 | W3 (128 x O) | b3], row-major.  2 <= m <= 20.
+ */
+typedef struct pfsp_mlp pfsp_mlp;
+
+/* New network for m machines, He-uniform weights from a SplitMix64 stream. */
+int pfsp_mlp_create(int m, uint64_t seed, pfsp_mlp **out);
+void pfsp_mlp_free(pfsp_mlp *mlp);
+/* Input width, hidden width, output width, number of pairs, parameter count. */
+int pfsp_mlp_shape(const pfsp_mlp *mlp, int *D0, int *H, int *O, int *P, int64_t *n_params);
+int pfsp_mlp_get_params(const pfsp_mlp *mlp, float *out);
+int pfsp_mlp_set_params(pfsp_mlp *mlp, const float *in);
+/* Logits Y [rows][O] of inputs X [rows][D0] (host buffers). */
+int pfsp_mlp_forward(const pfsp_mlp *mlp, int64_t rows, const float *X, float *Y);
+/* Masked mean binary cross-entropy of logits against targets T with mask M
+ * (both [rows][O]), and its gradient with respect to every parameter (host
+ * buffer of n_params floats, parameter layout); the parameters are unchanged. */
+int pfsp_mlp_loss_grad(const pfsp_mlp *mlp, int64_t rows, const float *X, const float *T, const float *M,
+                       float *loss, float *grad);
+/* Adam training (beta 0.9 / 0.999) on mini-batches of `batch` rows of a
+ * SplitMix64-shuffled order per epoch; epoch_loss (NULL or epochs floats)
+ * receives each epoch's mean batch loss. */
+int pfsp_mlp_train(pfsp_mlp *mlp, int64_t rows, const float *X, const float *T, const float *M, int epochs,
+                   int batch, float lr, uint64_t seed, float *epoch_loss);
+
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);
 

@@ -91,6 +91,24 @@ _lib.pfsp_solve_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POIN
 _lib.pfsp_autotune_batch.restype = ctypes.c_int
 _lib.pfsp_autotune_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options),
                                      ctypes.c_int, ctypes.POINTER(pfsp_options)]
+_fp = ctypes.POINTER(ctypes.c_float)
+_lib.pfsp_mlp_create.restype = ctypes.c_int
+_lib.pfsp_mlp_create.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(_vp)]
+_lib.pfsp_mlp_free.restype = None
+_lib.pfsp_mlp_free.argtypes = [_vp]
+_lib.pfsp_mlp_shape.restype = ctypes.c_int
+_lib.pfsp_mlp_shape.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int)] * 4 + [ctypes.POINTER(ctypes.c_int64)]
+_lib.pfsp_mlp_get_params.restype = ctypes.c_int
+_lib.pfsp_mlp_get_params.argtypes = [_vp, _vp]
+_lib.pfsp_mlp_set_params.restype = ctypes.c_int
+_lib.pfsp_mlp_set_params.argtypes = [_vp, _vp]
+_lib.pfsp_mlp_forward.restype = ctypes.c_int
+_lib.pfsp_mlp_forward.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+_lib.pfsp_mlp_loss_grad.restype = ctypes.c_int
+_lib.pfsp_mlp_loss_grad.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+_lib.pfsp_mlp_train.restype = ctypes.c_int
+_lib.pfsp_mlp_train.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                ctypes.c_uint64, _vp]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
 
@@ -244,3 +262,86 @@ def pfsp_autotune_batch(insts, base: pfsp_options = None, sample=0) -> pfsp_opti
     _check(_lib.pfsp_autotune_batch(_handles(insts), len(insts), ctypes.byref(base), int(sample),
                                     ctypes.byref(best)))
     return best
+
+
+class Mlp:
+    """Owner of a pfsp_mlp handle (the ordering network)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        d0, h, o, p = (ctypes.c_int() for _ in range(4))
+        n = ctypes.c_int64()
+        _check(_lib.pfsp_mlp_shape(handle, ctypes.byref(d0), ctypes.byref(h), ctypes.byref(o), ctypes.byref(p),
+                                   ctypes.byref(n)))
+        self.D0, self.H, self.O, self.P, self.n_params = d0.value, h.value, o.value, p.value, n.value
+
+    def close(self):
+        if self.handle:
+            _lib.pfsp_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, flat):
+        """[W1, b1, W2, b2, W3, b3] views of a flat parameter vector."""
+        D0, H, O = self.D0, self.H, self.O
+        sizes = [D0 * H, H, H * H, H, H * O, O]
+        shapes = [(D0, H), (H,), (H, H), (H,), (H, O), (O,)]
+        out, o = [], 0
+        for sz, sh in zip(sizes, shapes):
+            out.append(flat[o:o + sz].reshape(sh))
+            o += sz
+        return out
+
+
+def pfsp_mlp_create(m, seed=0) -> Mlp:
+    h = _vp()
+    _check(_lib.pfsp_mlp_create(int(m), int(seed), ctypes.byref(h)))
+    return Mlp(h)
+
+
+def pfsp_mlp_free(mlp: Mlp) -> None:
+    mlp.close()
+
+
+def pfsp_mlp_get_params(mlp: Mlp) -> np.ndarray:
+    out = np.empty(mlp.n_params, dtype=np.float32)
+    _check(_lib.pfsp_mlp_get_params(mlp.handle, _ptr(out)))
+    return out
+
+
+def pfsp_mlp_set_params(mlp: Mlp, flat) -> None:
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    assert flat.size == mlp.n_params
+    _check(_lib.pfsp_mlp_set_params(mlp.handle, _ptr(flat)))
+
+
+def pfsp_mlp_forward(mlp: Mlp, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.empty((X.shape[0], mlp.O), dtype=np.float32)
+    _check(_lib.pfsp_mlp_forward(mlp.handle, X.shape[0], _ptr(X), _ptr(Y)))
+    return Y
+
+
+def pfsp_mlp_loss_grad(mlp: Mlp, X, T, M):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    M = np.ascontiguousarray(M, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.empty(mlp.n_params, dtype=np.float32)
+    _check(_lib.pfsp_mlp_loss_grad(mlp.handle, X.shape[0], _ptr(X), _ptr(T), _ptr(M), _ptr(loss), _ptr(grad)))
+    return float(loss[0]), grad
+
+
+def pfsp_mlp_train(mlp: Mlp, X, T, M, epochs=5, batch=4096, lr=1e-3, seed=0) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    M = np.ascontiguousarray(M, dtype=np.float32)
+    losses = np.zeros(epochs, dtype=np.float32)
+    _check(_lib.pfsp_mlp_train(mlp.handle, X.shape[0], _ptr(X), _ptr(T), _ptr(M), int(epochs), int(batch),
+                               float(lr), int(seed), _ptr(losses)))
+    return losses
