@@ -136,6 +136,14 @@ typedef struct {
  *   min_steal    smallest remaining interval (in leaves) a victim splits;
  *                0 = default (2, i.e. any splittable interval).
  */
+typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
+
+/* Learned-ordering flags (pfsp_options.learned; not in the paper). */
+#define PFSP_LEARN_CHILD_ORDER 1  /* order each new row by the network's descend-first logits */
+#define PFSP_LEARN_PAIR_ORDER 2   /* sweep LB2's 32-pair slots in the order of the network's pair logits */
+#define PFSP_EARLY_EXIT 4         /* stop the LB2 sweep once every child's bound reaches the cap
+                                     (requires PFSP_MINMIN_CAPPED; values stay exact once capped) */
+
 typedef struct {
     int32_t init_ub;
     int64_t node_limit;
@@ -145,6 +153,8 @@ typedef struct {
     int warps_per_sm;
     int check_every;
     double min_steal;
+    const pfsp_mlp *mlp;  /* network used by the PFSP_LEARN_* flags (built for the instance's m) */
+    int learned;          /* PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0 = plain solver */
     int reserved[8];
 } pfsp_options;
 
@@ -229,6 +239,16 @@ int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_options *opt, 
                        int32_t *best_perm, int *outcome, pfsp_stats_t *stats);
 
 /*
+ * pfsp_solve that also records every `stride`-th counted decomposition (per
+ * explorer) into caller buffers: perm [capacity][n], d1 [capacity],
+ * d2 [capacity] in the layout of pfsp_bound_batch; *count receives the number
+ * of nodes recorded (at most capacity).  These are the solver's own traces
+ * from which the ordering network's training rows are built.
+ */
+int pfsp_solve_trace(const pfsp_instance *inst, const pfsp_options *opt, int64_t capacity, int stride,
+                     uint8_t *perm, uint8_t *d1, uint8_t *d2, int64_t *count, int32_t *best_cmax, int *outcome);
+
+/*
  * Ordering network (not in the paper): a two-hidden-layer MLP (128 ReLU
  * units each, bf16 weights, fp32 accumulation, tensor-core kernels) that
  * reads a node's per-machine front, back and remaining work, each divided by
@@ -239,8 +259,6 @@ int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_options *opt, 
  * 16.  Parameters are one fp32 vector [W1 (D0 x 128) | b1 | W2 (128 x 128) |
  * b2 | W3 (128 x O) | b3], row-major.  2 <= m <= 20.
  */
-typedef struct pfsp_mlp pfsp_mlp;
-
 /* New network for m machines, He-uniform weights from a SplitMix64 stream. */
 int pfsp_mlp_create(int m, uint64_t seed, pfsp_mlp **out);
 void pfsp_mlp_free(pfsp_mlp *mlp);
@@ -260,6 +278,19 @@ int pfsp_mlp_loss_grad(const pfsp_mlp *mlp, int64_t rows, const float *X, const 
  * receives each epoch's mean batch loss. */
 int pfsp_mlp_train(pfsp_mlp *mlp, int64_t rows, const float *X, const float *T, const float *M, int epochs,
                    int batch, float lr, uint64_t seed, float *epoch_loss);
+
+/*
+ * Training rows of the network from num_nodes nodes of `inst` (layout of
+ * pfsp_bound_batch), computed on the GPU: per node 1 + 2n rows -- the parent
+ * (features: front, back, remaining work per machine over the mean machine
+ * load; targets on columns 1..P: the pair's two-machine term equals the LB2
+ * of some child and exceeds its LB1), then the forward child of each job j
+ * (row 1 + j) and the backward child (row 1 + n + j), whose column-0 target
+ * is 1 for the child of least LB2 of its direction (ties: lowest job id).
+ * X [rows][D0], T and M [rows][O] (host buffers, M = loss mask).
+ */
+int pfsp_mlp_rows(const pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
+                  const uint8_t *d1, const uint8_t *d2, float *X, float *T, float *M);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);

@@ -21,6 +21,7 @@
 // recurrence job by job, at O(P u) work per parent instead of O(P u^2).
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -128,13 +129,10 @@ __device__ __forceinline__ int highest_bit(umask_t<NW> x) {
 // kind: bit 0 = LB1 wanted, bit 1 = LB2 wanted.  MT is the machine count
 // when known at compile time (0: take m_rt).  All 32 lanes must call.
 template <int NW, int MT>
-__device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m_rt,
-                                               int S_rt, int kind, int job0, int job1, int d1, int d2,
-                                               ChildBounds<NW> &out) {
+__device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int kind,
+                                              int job0, int job1, int d1, int d2, ChildBounds<NW> &out) {
     using mask_t = umask_t<NW>;
-    constexpr bool REGACC = (NW == 1);
     const int m = MT ? MT : m_rt;
-    const int S = MT ? (MT * (MT - 1) / 2 + 31) / 32 : S_rt;
     const int lane = threadIdx.x & 31;
     const int mp = m | 1;
     const int nj = (n + 3) & ~3;
@@ -253,11 +251,66 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
     }
     out.U = U;
     out.u = u;
+}
 
-    if (!want2 || u == 0) return;
+// One slot of the LB2 sweep for this lane's pair: walk the unscheduled jobs
+// (bit mask Upos of their reversed positions) in ascending Johnson order
+// recording the prefix constant PB before each job, then backwards composing
+// the suffix maps, leaving C of every child (compact index c) in W.Cb[c][lane].
+template <int NW>
+__device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, int2 *E, umask_t<NW> Upos, int u,
+                                          int lane) {
+    using mask_t = umask_t<NW>;
+    int PB = kNegInf;
+    for (int i = 0; i < u; ++i) {
+        int t = highest_bit<NW>(Upos);
+        Upos ^= mask_t(1) << t;
+        int2 e = pt[t * 32];
+        int c = W.cidx[e.x & 0xff];
+        E[i * 32] = make_int2(PB, t | (c << 8));
+        PB = max(PB + (e.x >> 8), e.y);
+    }
+    int SA = 0, SB = kNegInf;
+    for (int i = u - 1; i >= 0; --i) {
+        int2 q = E[i * 32];
+        int2 e = pt[(q.y & 0xff) * 32];
+        W.Cb[(q.y >> 8) * 32 + lane] = max(q.x + SA, SB);
+        SB = max(e.y + SA, SB);
+        SA += e.x >> 8;
+    }
+}
+
+// LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
+// written by decompose_lb1.  `order` (may be NULL) gives the order in which
+// the slots are swept; with cap < INT_MAX the sweep stops after the first
+// slot at which every child's bound is known to be >= cap (its LB1 or one of
+// the pair terms already seen reaches cap): the children's values are then
+// lower bounds >= cap, exact once capped at cap.
+template <int NW, int MT>
+__device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
+                                              ChildBounds<NW> &out, int cap, const int *order) {
+    using mask_t = umask_t<NW>;
+    constexpr bool REGACC = (NW == 1);
+    const int m = MT ? MT : m_rt;
+    const int S = MT ? (MT * (MT - 1) / 2 + 31) / 32 : S_rt;
+    const int lane = threadIdx.x & 31;
+    const int mp = m | 1;
+    const mask_t U = out.U;
+    const int u = out.u;
+    if (u == 0 || m < 2) return;
     __syncwarp();
-
-    // ---- LB2: lanes = machine pairs, S slots of 32 pairs ----------------------
+    // children already decided by LB1 (only used with a cap)
+    mask_t done_f = 0, done_b = 0;
+    if (cap != INT_MAX) {
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+            unsigned bf = __ballot_sync(PFSP_FULL, lane + 32 * h < u && out.lb1f[h] >= cap);
+            unsigned bb = __ballot_sync(PFSP_FULL, lane + 32 * h < u && out.lb1b[h] >= cap);
+            done_f |= (mask_t)bf << (32 * h);
+            done_b |= (mask_t)bb << (32 * h);
+        }
+    }
+    const mask_t all = (u >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << u) - 1);
     int accf[REGACC ? 32 : 1], accb[REGACC ? 32 : 1];
     if constexpr (REGACC) {
 #pragma unroll
@@ -282,41 +335,29 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
         }
     }
 #pragma unroll 1
-    for (int s = 0; s < S; ++s) {
+    for (int si = 0; si < S; ++si) {
+        const int s = order ? order[si] : si;
         const int klw = T.kl[s * 32 + lane];
         const int k = klw & 0xff, l = klw >> 8;
         const int Bl = W.B[l];
         const int2 *pt = T.ptab + (size_t)s * n * 32 + lane;
         mask_t Upos;
         if constexpr (MT > 0) {
-            Upos = UposAll[0];
+            if (order) {
+                Upos = 0;
 #pragma unroll
-            for (int q = 0; q + 1 < SC; ++q) UposAll[q] = UposAll[q + 1];
+                for (int q = 0; q < SC; ++q) Upos = q == s ? UposAll[q] : Upos;
+            } else {
+                Upos = UposAll[0];
+#pragma unroll
+                for (int q = 0; q + 1 < SC; ++q) UposAll[q] = UposAll[q + 1];
+            }
         } else {
             Upos = 0;
             for (mask_t um = U; um; um &= um - 1)
                 Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];
         }
-        // prefix pass, ascending Johnson order (descending stored index):
-        // record PB before each job
-        int PB = kNegInf;
-        for (int i = 0; i < u; ++i) {
-            int t = highest_bit<NW>(Upos);
-            Upos ^= mask_t(1) << t;
-            int2 e = pt[t * 32];
-            int c = W.cidx[e.x & 0xff];
-            E[i * 32] = make_int2(PB, t | (c << 8));
-            PB = max(PB + (e.x >> 8), e.y);
-        }
-        // suffix pass, descending positions: C = max(PB + SA, SB), then extend
-        int SA = 0, SB = kNegInf;
-        for (int i = u - 1; i >= 0; --i) {
-            int2 q = E[i * 32];
-            int2 e = pt[(q.y & 0xff) * 32];
-            W.Cb[(q.y >> 8) * 32 + lane] = max(q.x + SA, SB);
-            SB = max(e.y + SA, SB);
-            SA += e.x >> 8;
-        }
+        scan_slot<NW>(W, pt, E, Upos, u, lane);
         // evaluation: the third pair term of every child of this parent
         const int *gf = W.Gf + k;
         const int *gb = W.Gb + k;
@@ -341,6 +382,38 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
                 v.y = max(v.y, gb[c * mp] + C + bb[c * mp]);
                 W.Acc[c * 32 + lane] = v;
             }
+        }
+        if (cap != INT_MAX && si + 1 < S) {
+            // every child decided? (some pair term or its LB1 already >= cap)
+            mask_t mf = 0, mb = 0;
+            if constexpr (REGACC) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c >= u) break;
+                    mf |= (mask_t)(accf[c] >= cap) << c;
+                    mb |= (mask_t)(accb[c] >= cap) << c;
+                }
+            } else {
+                for (int c = 0; c < u; ++c) {
+                    int2 v = W.Acc[c * 32 + lane];
+                    mf |= (mask_t)(v.x >= cap) << c;
+                    mb |= (mask_t)(v.y >= cap) << c;
+                }
+            }
+            if constexpr (NW == 1) {
+                mf = __reduce_or_sync(PFSP_FULL, (unsigned)mf);
+                mb = __reduce_or_sync(PFSP_FULL, (unsigned)mb);
+            } else {
+                unsigned fl = __reduce_or_sync(PFSP_FULL, (unsigned)(mf & 0xffffffffull));
+                unsigned fh = __reduce_or_sync(PFSP_FULL, (unsigned)(mf >> 32));
+                unsigned bl = __reduce_or_sync(PFSP_FULL, (unsigned)(mb & 0xffffffffull));
+                unsigned bh = __reduce_or_sync(PFSP_FULL, (unsigned)(mb >> 32));
+                mf = ((mask_t)fh << 32) | fl;
+                mb = ((mask_t)bh << 32) | bl;
+            }
+            done_f |= mf;
+            done_b |= mb;
+            if ((done_f & all) == all && (done_b & all) == all) break;
         }
     }
     // ---- max over lanes (pairs) per child: transpose through padded rows ------
@@ -372,6 +445,15 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
             out.lb2b[h] = max(out.lb1b[h], mb);
         }
     }
+}
+
+// Both phases: the bounds of all 2u children of the node.
+template <int NW, int MT>
+__device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m_rt,
+                                               int S_rt, int kind, int job0, int job1, int d1, int d2,
+                                               ChildBounds<NW> &out) {
+    decompose_lb1<NW, MT>(T, W, n, m_rt, kind, job0, job1, d1, d2, out);
+    if ((kind & PFSP_LB2) && (MT ? MT : m_rt) >= 2) decompose_lb2<NW, MT>(T, W, n, m_rt, S_rt, out, INT_MAX, nullptr);
 }
 
 // Stage `words` int32 (a multiple of 4, 16-byte aligned on both sides) from

@@ -31,9 +31,12 @@ struct ExplorerSmem {
     double w[64];   // (n-1-i)! as double, for length estimates
     int etop;
     unsigned seq;   // sequence number of this explorer's last steal request
-    int pad[2];
+    int pad[6];
+    float score[64];   // descend-first logits of the children being ordered
+    float sscore[16];  // summed pair probabilities per LB2 slot
+    int sorder[16];    // LB2 slot order of the current node
 };
-constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 4);
+constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 8 + 64 + 16 + 16);  // a multiple of 8 words
 
 struct Stats {
     unsigned long long decomposed, bounded, leaves, pruned, steals, iters;
@@ -150,6 +153,112 @@ struct Explorer {
         return false;
     }
 
+    // Network scratch of this warp (32-byte aligned).
+    __device__ unsigned char *mlp_scratch() const { return (unsigned char *)(W.F + a.mlp_off); }
+
+    // Order of the LB2 slots for the node whose front, back and remaining
+    // work sit in W.F / W.B / W.R: by decreasing sum over the slot's pairs of
+    // the network's probability that the pair attains a child's LB2.
+    __device__ void slot_order() {
+        const MlpDev &P = a.mlp;
+        unsigned char *ms = mlp_scratch();
+        __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
+        for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
+        __syncwarp();
+        if (lane < m) {
+            Xs[lane] = __float2bfloat16_rn(W.F[lane] * a.inv_scale);
+            Xs[m + lane] = __float2bfloat16_rn(W.B[lane] * a.inv_scale);
+            Xs[2 * m + lane] = __float2bfloat16_rn(W.R[lane] * a.inv_scale);
+        }
+        if (lane < 16) X.sscore[lane] = 0.0f;
+        __syncwarp();
+        mlp_tile_hidden(P, ms);
+        const int npairs = m * (m - 1) / 2;
+        for (int j = 0; j < P.O; j += 16) {
+            const float *stt = mlp_tile_logits(P, ms, j);
+            if (lane < 16) {
+                const int col = j + lane;
+                if (col >= 1 && col <= npairs) {
+                    const float z = stt[lane] + P.b3[col];
+                    atomicAdd(&X.sscore[(col - 1) >> 5], 1.0f / (1.0f + expf(-z)));
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            for (int s = 0; s < S; ++s) X.sorder[s] = s;
+            for (int a1 = 1; a1 < S; ++a1) {
+                int v = X.sorder[a1], b1 = a1 - 1;
+                while (b1 >= 0 && X.sscore[X.sorder[b1]] < X.sscore[v]) {
+                    X.sorder[b1 + 1] = X.sorder[b1];
+                    --b1;
+                }
+                X.sorder[b1 + 1] = v;
+            }
+        }
+        __syncwarp();
+    }
+
+    // Row positions of the u children of direction `dir` (compact index c held
+    // by lane c and c + 32): decreasing descend-first logit, ties by job id.
+    // Depends on the node alone (never on the incumbent), so every explorer
+    // that rebuilds this row orders it the same way.
+    __device__ void child_order(int dir, int u, int (&pos)[NW]) {
+        const MlpDev &P = a.mlp;
+        unsigned char *ms = mlp_scratch();
+        __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
+        const int nj = (n + 3) & ~3;
+        for (int t = 0; t < u; t += 16) {
+            for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
+            __syncwarp();
+            const int c = t + lane;
+            if (lane < 16 && c < u) {
+                const int j = W.ul[c];
+                __nv_bfloat16 *xr = Xs + lane * P.D0;
+                if (dir == 0) {
+                    int f = 0;
+                    for (int k = 0; k < m; ++k) {
+                        const int pk = T.pm[k * nj + j];
+                        f = max(f, W.F[k]) + pk;
+                        xr[k] = __float2bfloat16_rn(f * a.inv_scale);
+                        xr[m + k] = __float2bfloat16_rn(W.B[k] * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((W.R[k] - pk) * a.inv_scale);
+                    }
+                } else {
+                    int b = 0;
+                    for (int k = m - 1; k >= 0; --k) {
+                        const int pk = T.pm[k * nj + j];
+                        b = max(b, W.B[k]) + pk;
+                        xr[k] = __float2bfloat16_rn(W.F[k] * a.inv_scale);
+                        xr[m + k] = __float2bfloat16_rn(b * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((W.R[k] - pk) * a.inv_scale);
+                    }
+                }
+            }
+            __syncwarp();
+            mlp_tile_hidden(P, ms);
+            const float *stt = mlp_tile_logits(P, ms, 0);
+            if (lane < 16 && c < u) {
+                float z = stt[lane * 16] + P.b3[0];
+                X.score[c] = (z == z) ? z : -1e30f;  // a NaN never breaks the ranking
+            }
+            __syncwarp();
+        }
+        for (int h = 0; h < NW; ++h) {
+            const int c = lane + 32 * h;
+            if (c < u) {
+                const float key = X.score[c];
+                int r = 0;
+                for (int c2 = 0; c2 < u; ++c2) {
+                    const float k2 = X.score[c2];
+                    r += (k2 > key) || (k2 == key && c2 < c);
+                }
+                pos[h] = r;
+            }
+        }
+        __syncwarp();
+    }
+
     // Decompose the node at level I (I = -1: the root): bound both children
     // sets, choose the direction by MinMin, write row I+1, handle leaves.
     __device__ void expand(bool counted) {
@@ -196,9 +305,29 @@ struct Explorer {
         }
         const int job0 = lane < n ? X.perm[lane] : 0;
         const int job1 = (NW == 2 && lane + 32 < n) ? X.perm[lane + 32] : 0;
+        if (counted && a.trace_cap > 0 && (st.decomposed % (unsigned long long)a.trace_stride) == 0) {
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(a.trace_count, 1ull);
+            slot = __shfl_sync(PFSP_FULL, slot, 0);
+            if (slot < (unsigned long long)a.trace_cap) {
+                for (int i = lane; i < n; i += 32) a.trace_perm[slot * n + i] = (uint8_t)X.perm[i];
+                if (lane == 0) {
+                    a.trace_d1[slot] = (uint8_t)d1;
+                    a.trace_d2[slot] = (uint8_t)d2;
+                }
+            }
+        }
         ChildBounds<NW> cb;
         const int kind = a.bound == PFSP_LB2 ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
-        decompose_node<NW, MT>(T, W, n, m, S, kind, job0, job1, d1, d2, cb);
+        decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
+        if ((kind & PFSP_LB2) && m >= 2) {
+            const int *order = nullptr;
+            if ((a.learned & PFSP_LEARN_PAIR_ORDER) && S >= 2 && cb.u > 0) {
+                slot_order();
+                order = X.sorder;
+            }
+            decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
+        }
         const int u = cb.u;
 
         // ---- MinMin (Section 2.3) ----------------------------------------------
@@ -240,6 +369,9 @@ struct Explorer {
         const int row = I + 1;
         int ubv = ub();
         int npruned = 0;
+        int pos[NW];
+        for (int h = 0; h < NW; ++h) pos[h] = lane + 32 * h;
+        if ((a.learned & PFSP_LEARN_CHILD_ORDER) && u >= 2) child_order(dir, u, pos);
         for (int h = 0; h < NW; ++h) {
             int c = lane + 32 * h;
             int lb = dir ? vb[h] : vf[h];
@@ -281,8 +413,8 @@ struct Explorer {
             bool keep = on && !leaf && lb < ubv;
             npruned += __popc(__ballot_sync(PFSP_FULL, on && !keep && !(leaf && lb < ubv)));
             if (on) {
-                rj[row * n + c] = (uint8_t)W.ul[c];
-                rl[row * n + c] = keep ? lb : kPrunedLB;
+                rj[row * n + pos[h]] = (uint8_t)W.ul[c];
+                rl[row * n + pos[h]] = keep ? lb : kPrunedLB;
             }
         }
         if (lane == 0) {

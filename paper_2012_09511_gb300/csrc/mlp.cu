@@ -45,6 +45,13 @@ MlpDev mlp_view(const pfsp_mlp *M) {
     return P;
 }
 
+int mlp_dims(const pfsp_mlp *M, int *m, int *D0, int *O) {
+    *m = M->m;
+    *D0 = M->D0;
+    *O = M->O;
+    return PFSP_OK;
+}
+
 __global__ void mlp_refresh_bf16(const float *params, size_t oW1, size_t nW1, size_t oW2, size_t nW2, size_t oW3,
                                  size_t nW3, __nv_bfloat16 *wb) {
     size_t tot = nW1 + nW2 + nW3;

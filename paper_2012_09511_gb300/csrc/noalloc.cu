@@ -23,9 +23,7 @@
 #include <cstring>
 #include <vector>
 
-#include "bound_device.cuh"
-#include "pfsp_internal.h"
-#include "solve_internal.h"
+#include "explorer_device.cuh"
 
 namespace pfsp {
 
@@ -109,14 +107,16 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     a.bound = opt->bound;
     a.capped = opt->branching == PFSP_MINMIN_CAPPED;
     a.cap = ub0;
-    const int per_warp = solve_warp_words(n, m, opt->bound);
-    a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
+    if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs the plain solver only");
+    a.warp_words = (warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2) + 7) & ~7;
+    a.warp_base = (a.tab_words + 7) & ~7;
+    const int per_warp = a.warp_words + kExplorerWords;
     int dev = 0, nsm = 1, optin = 48 * 1024;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int want = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
-    long long fit = ((long long)optin - 64 - (long long)a.tab_words * 4) / ((long long)per_warp * 4);
+    long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
     want = (int)std::min<long long>(want, fit);
 
     // layout inside the static array: tables, then the explorer pool; the
@@ -145,7 +145,7 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     int warps = want, blocks = 0, K = 0;
     size_t smem = 0, need = 0;
     for (; warps >= 1; --warps) {
-        smem = (size_t)(a.tab_words + warps * per_warp) * 4;
+        smem = (size_t)(a.warp_base + warps * per_warp) * 4;
         int per_sm = solve_occupancy(a, warps, smem);
         if (per_sm < 1) continue;
         blocks = nsm * per_sm;

@@ -64,6 +64,11 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
 // Error reporting shared by the C-ABI translation units.
 int set_error(int code, const char *fmt, ...);
 
+struct MlpDev;
+// The network's device view and dimensions (mlp.cu).
+MlpDev mlp_view(const pfsp_mlp *M);
+int mlp_dims(const pfsp_mlp *M, int *m, int *D0, int *O);
+
 // Host-side builders shared by the entry points (capi.cu, solve_capi.cu).
 void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob);
 int neh(int n, int m, const int32_t *p, std::vector<int> &perm);

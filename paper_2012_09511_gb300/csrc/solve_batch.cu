@@ -106,7 +106,7 @@ __device__ inline int opening_count(int n, int W) {
 
 template <int NW>
 __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchArgs b) {
-    extern __shared__ __align__(16) int smem[];
+    extern __shared__ __align__(128) int smem[];
     __shared__ uint64_t bar;
     __shared__ SolveArgs sa;
     __shared__ int s_inst, s_mode;
@@ -304,6 +304,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     if (opt->branching != PFSP_MINMIN && opt->branching != PFSP_MINMIN_CAPPED)
         return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN or PFSP_MINMIN_CAPPED");
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
+    if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs the plain solver only");
     int dev = 0;
     cudaGetDevice(&dev);
     for (int i = 0; i < count; ++i) {

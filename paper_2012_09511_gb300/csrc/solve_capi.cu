@@ -80,8 +80,15 @@ void pfsp_default_options(pfsp_options *o) {
     o->branching = PFSP_MINMIN;
 }
 
-int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
-               int *outcome) {
+struct TraceRequest {
+    int64_t capacity;
+    int stride;
+    uint8_t *perm, *d1, *d2;
+    int64_t *count;
+};
+
+static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, const TraceRequest *tr,
+                      int32_t *best_cmax, int32_t *best_perm, int *outcome) {
     pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
     if (!inst || !opt || !best_cmax || !outcome) return set_error(PFSP_ERR_INVALID, "NULL argument");
     if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
@@ -91,6 +98,18 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->bound == PFSP_LB2 && !inst->lb2_ok)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
+    if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT))
+        return set_error(PFSP_ERR_INVALID, "unknown bits in learned");
+    if ((opt->learned & PFSP_EARLY_EXIT) && opt->branching != PFSP_MINMIN_CAPPED)
+        return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT needs PFSP_MINMIN_CAPPED");
+    const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
+    int net_m = 0, net_D0 = 0, net_O = 0;
+    if (use_net) {
+        if (!opt->mlp) return set_error(PFSP_ERR_INVALID, "learned ordering requested without a network");
+        mlp_dims(opt->mlp, &net_m, &net_D0, &net_O);
+        if (net_m != inst->m)
+            return set_error(PFSP_ERR_INVALID, "network built for m=%d, instance has m=%d", net_m, inst->m);
+    }
     auto t0 = std::chrono::steady_clock::now();
     const int n = inst->n, m = inst->m;
     const TableLayout &L = inst->lay;
@@ -120,17 +139,28 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     a.bound = opt->bound;
     a.capped = opt->branching == PFSP_MINMIN_CAPPED;
     a.cap = ub0;
-    const int per_warp = solve_warp_words(n, m, opt->bound);  // bound scratch + explorer state
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
+    if (use_net) {
+        a.warp_words += mlp_scratch_place(n, m, opt->bound, net_D0, &a.mlp_off);
+        a.mlp = mlp_view(opt->mlp);
+        long long tot = 0;
+        for (int j = 0; j < n * m; ++j) tot += inst->p_host[j];
+        a.inv_scale = tot > 0 ? (float)m / (float)tot : 1.0f;
+    }
+    a.learned = opt->learned;
+    a.warp_words = (a.warp_words + 7) & ~7;  // keeps every warp's scratch 32-byte aligned
+    a.warp_base = (a.tab_words + 7) & ~7;
+    const int per_warp = a.warp_words + (solve_warp_words(n, m, opt->bound) -
+                                         warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2));
     int dev = 0, nsm = 1, optin = 48 * 1024;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
-    long long fit = ((long long)optin - 64 - (long long)a.tab_words * 4) / ((long long)per_warp * 4);
+    long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
-    size_t smem = (size_t)(a.tab_words + warps * per_warp) * 4;
+    size_t smem = (size_t)(a.warp_base + warps * per_warp) * 4;
     int per_sm = solve_occupancy(a, warps, smem);
     if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "solve kernel cannot be resident (occupancy 0)");
     const int blocks = nsm * per_sm;
@@ -178,6 +208,9 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     const size_t o_is = take((size_t)K * 64), o_ie = take((size_t)K * 65);
     const size_t o_mb = take((size_t)K * 8), o_rs = take((size_t)K * 8), o_le = take((size_t)K * 4);
     const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64);
+    const int64_t tcap = tr ? tr->capacity : 0;
+    const size_t o_tp = take((size_t)tcap * n), o_t1 = take((size_t)tcap), o_t2 = take((size_t)tcap),
+                 o_tc = take(8);
     DeviceSolveState D;
     cudaError_t e = cudaMalloc(&D.blob, off);
     if (e != cudaSuccess) {
@@ -203,6 +236,14 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     a.node_limit = opt->node_limit;
     a.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
     a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
+    if (tcap > 0) {
+        a.trace_perm = (uint8_t *)(b + o_tp);
+        a.trace_d1 = (uint8_t *)(b + o_t1);
+        a.trace_d2 = (uint8_t *)(b + o_t2);
+        a.trace_count = (unsigned long long *)(b + o_tc);
+        a.trace_cap = tcap;
+        a.trace_stride = tr->stride > 0 ? tr->stride : 1;
+    }
     int ce = opt->check_every > 0 ? opt->check_every : 16;
     int pw = 1;
     while (pw < ce) pw <<= 1;
@@ -217,6 +258,7 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
+    if (e == cudaSuccess && tcap > 0) e = cudaMemsetAsync(a.trace_count, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_end, he.data(), he.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc, hsc, sizeof(hsc), cudaMemcpyHostToDevice, st);
@@ -256,6 +298,16 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
         else if (from_neh)
             for (int j = 0; j < n; ++j) best_perm[j] = neh_perm[j];
     }
+    if (tcap > 0) {
+        unsigned long long tc = 0;
+        e = cudaMemcpy(&tc, a.trace_count, 8, cudaMemcpyDeviceToHost);
+        const int64_t got = (int64_t)std::min<unsigned long long>(tc, (unsigned long long)tcap);
+        if (e == cudaSuccess && got > 0) e = cudaMemcpy(tr->perm, a.trace_perm, (size_t)got * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && got > 0) e = cudaMemcpy(tr->d1, a.trace_d1, (size_t)got, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && got > 0) e = cudaMemcpy(tr->d2, a.trace_d2, (size_t)got, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "trace readback: %s", cudaGetErrorString(e));
+        *tr->count = got;
+    }
     memset(&inst->stats, 0, sizeof(inst->stats));
     inst->stats.decomposed = cnt[0];
     inst->stats.bounded_children = cnt[1];
@@ -268,6 +320,20 @@ int pfsp_solve(const pfsp_instance *inst_c, const pfsp_options *opt, int32_t *be
     inst->stats.explorers = K;
     inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return PFSP_OK;
+}
+
+int pfsp_solve(const pfsp_instance *inst, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
+               int *outcome) {
+    return solve_impl(inst, opt, nullptr, best_cmax, best_perm, outcome);
+}
+
+int pfsp_solve_trace(const pfsp_instance *inst, const pfsp_options *opt, int64_t capacity, int stride,
+                     uint8_t *perm, uint8_t *d1, uint8_t *d2, int64_t *count, int32_t *best_cmax, int *outcome) {
+    if (capacity < 0 || !count || (capacity > 0 && (!perm || !d1 || !d2)))
+        return set_error(PFSP_ERR_INVALID, "bad trace buffers");
+    TraceRequest tr{capacity, stride, perm, d1, d2, count};
+    *count = 0;
+    return solve_impl(inst, opt, &tr, best_cmax, nullptr, outcome);
 }
 
 }  // extern "C"

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mlp_device.cuh"
+
 namespace pfsp {
 
 constexpr int kSolveWarps = 12;          // explorers (warps) per CTA at most
@@ -53,9 +55,23 @@ struct SolveArgs {
     int *err;
     float min_steal;      // smallest interval length (leaves) a victim gives away
     int check_every;      // power of two: iterations between limit checks
+    int warp_base;        // word offset of the first warp's scratch (32-byte aligned)
+    // recorded decompositions (pfsp_solve_trace); trace_cap = 0: off
+    uint8_t *trace_perm, *trace_d1, *trace_d2;
+    unsigned long long *trace_count;
+    long long trace_cap;
+    int trace_stride;
+    // learned ordering (PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0: off)
+    int learned;
+    MlpDev mlp;
+    float inv_scale;      // 1 / (mean machine load) for the network's features
+    int mlp_off;          // word offset of the network's scratch from the warp's base
 };
 
 int solve_warp_words(int n, int m, int bound);
+// Network scratch placement for a learned solve: sets *off (words from the
+// warp base) and returns the extra words to add to the per-warp stride.
+int mlp_scratch_place(int n, int m, int bound, int D0, int *off);
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 

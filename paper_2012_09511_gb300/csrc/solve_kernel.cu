@@ -34,7 +34,7 @@ namespace pfsp {
 
 template <int NW, int MT>
 __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a) {
-    extern __shared__ __align__(16) int smem[];
+    extern __shared__ __align__(128) int smem[];
     __shared__ uint64_t bar;
     stage_tables(smem, a.tab, a.tab_words, &bar);
     SmemTables T;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
-    int *wbase = smem + a.tab_words + wib * (a.warp_words + kExplorerWords);
+    int *wbase = smem + a.warp_base + wib * (a.warp_words + kExplorerWords);
     WarpScratch W = carve_warp(wbase, a.n, a.m);
     ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
     const int me = blockIdx.x * warps + wib;
@@ -66,6 +66,23 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
 
 int solve_warp_words(int n, int m, int bound) {
     return warp_words(n, m, n > 32, bound == PFSP_LB2 && m >= 2) + kExplorerWords;
+}
+
+int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
+    const int need = (mlp_scratch_bytes(D0) + 3) / 4;
+    const int bw = warp_words(n, m, n > 32, bound == PFSP_LB2 && m >= 2);
+    if (bound == PFSP_LB2 && m >= 2) {
+        // alias the prefix-record / C region, free outside the LB2 sweep
+        const int nr = round4(n);
+        const int e_off = 224 + 3 * round4(nr * (m | 1));
+        const int start = (e_off + 7) & ~7;
+        if (start + need <= bw) {
+            *off = start;
+            return 0;
+        }
+    }
+    *off = (bw + 7) & ~7;
+    return *off + need - bw;
 }
 
 template <int NW, int MT>

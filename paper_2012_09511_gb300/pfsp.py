@@ -53,11 +53,16 @@ class pfsp_stats_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+PFSP_LEARN_CHILD_ORDER = 1
+PFSP_LEARN_PAIR_ORDER = 2
+PFSP_EARLY_EXIT = 4
+
+
 class pfsp_options(ctypes.Structure):
     _fields_ = [("init_ub", ctypes.c_int32), ("node_limit", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
                 ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double),
-                ("reserved", ctypes.c_int * 8)]
+                ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
+                ("learned", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -109,6 +114,12 @@ _lib.pfsp_mlp_loss_grad.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp
 _lib.pfsp_mlp_train.restype = ctypes.c_int
 _lib.pfsp_mlp_train.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                 ctypes.c_uint64, _vp]
+_lib.pfsp_solve_trace.restype = ctypes.c_int
+_lib.pfsp_solve_trace.argtypes = [_vp, ctypes.POINTER(pfsp_options), ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp,
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int)]
+_lib.pfsp_mlp_rows.restype = ctypes.c_int
+_lib.pfsp_mlp_rows.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
 
@@ -196,10 +207,14 @@ def pfsp_stats(inst: Instance) -> dict:
 
 
 def pfsp_default_options(**fields) -> pfsp_options:
-    """Defaults of the library, then the given fields (names as in the C struct)."""
+    """Defaults of the library, then the given fields (names as in the C struct;
+    `mlp` may be an Mlp object)."""
     o = pfsp_options()
     _lib.pfsp_default_options(ctypes.byref(o))
     for k, v in fields.items():
+        if k == "mlp" and v is not None and not isinstance(v, int):
+            o._mlp_owner = v  # keep the network alive with the options
+            v = v.handle.value if hasattr(v.handle, "value") else v.handle
         setattr(o, k, v)
     return o
 
@@ -345,3 +360,37 @@ def pfsp_mlp_train(mlp: Mlp, X, T, M, epochs=5, batch=4096, lr=1e-3, seed=0) -> 
     _check(_lib.pfsp_mlp_train(mlp.handle, X.shape[0], _ptr(X), _ptr(T), _ptr(M), int(epochs), int(batch),
                                float(lr), int(seed), _ptr(losses)))
     return losses
+
+
+def pfsp_solve_trace(inst: Instance, capacity, stride=1, opts: pfsp_options = None, **fields):
+    """Solve while recording every stride-th decomposition: returns (perm [k, n], d1 [k], d2 [k], result)."""
+    if opts is None:
+        opts = pfsp_default_options(**fields)
+    n = inst.n
+    perm = np.zeros((max(capacity, 1), n), dtype=np.uint8)
+    d1 = np.zeros(max(capacity, 1), dtype=np.uint8)
+    d2 = np.zeros(max(capacity, 1), dtype=np.uint8)
+    cnt = ctypes.c_int64()
+    best = ctypes.c_int32()
+    out = ctypes.c_int()
+    _check(_lib.pfsp_solve_trace(inst.handle, ctypes.byref(opts), int(capacity), int(stride), _ptr(perm), _ptr(d1),
+                                 _ptr(d2), ctypes.byref(cnt), ctypes.byref(best), ctypes.byref(out)))
+    k = cnt.value
+    r = dict(cmax=best.value, outcome=out.value)
+    r.update(pfsp_stats(inst))
+    return perm[:k], d1[:k], d2[:k], r
+
+
+def pfsp_mlp_rows(inst: Instance, mlp: Mlp, perm, d1, d2):
+    """Training rows (X, T, M) of the nodes: (1 + 2n) rows per node."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+    d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+    k = len(d1)
+    rows = k * (1 + 2 * inst.n)
+    X = np.empty((rows, mlp.D0), dtype=np.float32)
+    T = np.empty((rows, mlp.O), dtype=np.float32)
+    M = np.empty((rows, mlp.O), dtype=np.float32)
+    _check(_lib.pfsp_mlp_rows(inst.handle, mlp.handle, k, _ptr(perm), _ptr(d1), _ptr(d2), _ptr(X), _ptr(T),
+                              _ptr(M)))
+    return X, T, M

@@ -1,0 +1,149 @@
+"""The learned ordering (network-ordered LB2 slots and rows, early exit).
+
+* Training rows built on the GPU carry the oracle's features (per-machine
+  front, back and remaining work over the mean machine load) and targets
+  (pairs whose two-machine term is a child's LB2 above its LB1; the child of
+  least LB2 per direction).
+* The solver's traced nodes are valid nodes of the instance.
+* Exactness: with any network the optimum is unchanged, and in proof mode
+  capped MinMin with early exit and learned orders explores exactly the tree
+  of plain capped MinMin (the oracle's capped count).
+* Training on the solver's own traces lowers the loss and predicts the pair
+  targets better than the best constant per pair (what the network adds).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2012_09511_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    from paper_2012_09511_gb300 import build
+    build.build()
+    from paper_2012_09511_gb300 import pfsp
+    return pfsp
+
+
+def _pairs(m):
+    return [(k, l) for k in range(m) for l in range(k + 1, m)]
+
+
+def test_training_rows_match_oracle(pf):
+    n, m = 8, 5
+    p = inputs.make_instance(n, m, 12)
+    scale = p.sum() / m
+    perm, d1, d2 = inputs.random_nodes(n, 40, seed=3, dmax=4)
+    inst = pf.pfsp_load_instance(p)
+    mlp = pf.pfsp_mlp_create(m, seed=1)
+    X, T, M = pf.pfsp_mlp_rows(inst, mlp, perm, d1, d2)
+    rows = 1 + 2 * n
+    pairs = _pairs(m)
+    for i in range(len(d1)):
+        s1, s2 = list(perm[i, :d1[i]]), list(perm[i, n - d2[i]:])
+        un = [j for j in range(n) if j not in s1 and j not in s2]
+        base = i * rows
+        want = np.concatenate([orc.front(p, s1), orc.back(p, s2), orc.remain(p, un)]) / scale
+        assert np.allclose(X[base, :3 * m], want, rtol=1e-6)
+        b1, b2 = orc.children_bounds(p, perm[i], d1[i], d2[i])
+        hits = np.zeros(len(pairs))
+        for d in (0, 1):
+            for j in un:
+                c1, c2 = (s1 + [j], s2) if d == 0 else (s1, [j] + s2)
+                r = base + 1 + d * n + j
+                rest = [x for x in un if x != j]
+                wf = np.concatenate([orc.front(p, c1), orc.back(p, c2), orc.remain(p, rest)]) / scale
+                assert np.allclose(X[r, :3 * m], wf, rtol=1e-6)
+                assert M[r, 0] == 1
+                lb1, lb2 = b1[d, j], b2[d, j]
+                if lb2 > lb1:
+                    f, bk = orc.front(p, c1), orc.back(p, c2)
+                    for q, (k, l) in enumerate(pairs):
+                        g = p[:, k + 1:l].sum(axis=1)
+                        order = [x for x in orc.johnson_lag_order(p[:, k], p[:, l], g) if x in rest]
+                        if orc.pair_value(p, k, l, f, bk, order) == lb2:
+                            hits[q] = 1
+            if un:
+                best = min(un, key=lambda j: (b2[d, j], j))
+                tgt = [T[base + 1 + d * n + j, 0] for j in un]
+                assert tgt == [1.0 if j == best else 0.0 for j in un]
+        assert (T[base, 1:1 + len(pairs)] == hits).all(), (i, T[base, 1:1 + len(pairs)], hits)
+        # a node without children has no pair targets: its mask stays zero
+        assert (M[base, 1:1 + len(pairs)] == (1 if un else 0)).all() and M[base, 0] == 0
+        for j in range(n):
+            if j not in un:
+                assert (X[base + 1 + j] == 0).all() and (M[base + 1 + j] == 0).all()
+
+
+def test_traced_nodes_are_valid(pf):
+    n, m = 12, 10
+    p = inputs.make_instance(n, m, 17)
+    inst = pf.pfsp_load_instance(p)
+    perm, d1, d2, r = pf.pfsp_solve_trace(inst, 5000, stride=2, bound=pf.PFSP_LB2)
+    assert 0 < len(d1) <= 5000
+    assert len(d1) <= r["decomposed"] // 2 + r["explorers"] + 1
+    for i in range(len(d1)):
+        assert sorted(perm[i].tolist()) == list(range(n))
+        assert d1[i] + d2[i] <= n - 1
+    assert r["cmax"] == orc.bb_solve(p, bound=orc.LB2)["cmax"]
+
+
+@pytest.mark.parametrize("n,m,seed", [(12, 10, 17), (11, 20, 3), (13, 5, 8)])
+def test_learned_solver_is_exact(pf, n, m, seed):
+    p = inputs.make_instance(n, m, seed)
+    inst = pf.pfsp_load_instance(p)
+    mlp = pf.pfsp_mlp_create(m, seed=seed)  # untrained: exactness must not depend on it
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    capped = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, capped=True)
+    every = pf.PFSP_LEARN_CHILD_ORDER | pf.PFSP_LEARN_PAIR_ORDER | pf.PFSP_EARLY_EXIT
+    r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, branching=pf.PFSP_MINMIN_CAPPED, mlp=mlp,
+                      learned=every)
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+    assert (r["decomposed"], r["bounded_children"]) == (capped["decomposed"], capped["bounded"])
+    f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, branching=pf.PFSP_MINMIN_CAPPED, mlp=mlp, learned=every)
+    assert f["outcome"] == pf.PFSP_OPTIMAL and f["cmax"] == opt
+    assert orc.makespan(p, f["perm"]) == opt
+    g = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, mlp=mlp, learned=pf.PFSP_LEARN_CHILD_ORDER)
+    assert g["cmax"] == opt
+
+
+def test_learned_options_are_validated(pf):
+    p = inputs.make_instance(8, 5, 1)
+    inst = pf.pfsp_load_instance(p)
+    with pytest.raises(pf.PfspError):  # early exit without the capped rule
+        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT)
+    with pytest.raises(pf.PfspError):  # no network
+        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_LEARN_CHILD_ORDER)
+    other = pf.pfsp_mlp_create(10, seed=1)
+    with pytest.raises(pf.PfspError):  # network for another m
+        pf.pfsp_solve(inst, bound=2, mlp=other, learned=pf.PFSP_LEARN_PAIR_ORDER)
+
+
+def test_training_on_solver_traces_beats_constant_predictor(pf):
+    m = 10
+    mlp = pf.pfsp_mlp_create(m, seed=5)
+    Xs, Ts, Ms = [], [], []
+    for seed in range(1, 5):
+        inst = pf.pfsp_load_instance(inputs.make_instance(20, m, seed))
+        perm, d1, d2, _ = pf.pfsp_solve_trace(inst, 1500, stride=3, bound=pf.PFSP_LB2)
+        X, T, M = pf.pfsp_mlp_rows(inst, mlp, perm, d1, d2)
+        keep = M.sum(axis=1) > 0
+        Xs.append(X[keep]); Ts.append(T[keep]); Ms.append(M[keep])
+    X, T, M = np.concatenate(Xs), np.concatenate(Ts), np.concatenate(Ms)
+    rng = np.random.default_rng(0)
+    idx = rng.permutation(len(X))
+    cut = int(0.8 * len(X))
+    tr, te = idx[:cut], idx[cut:]
+    losses = pf.pfsp_mlp_train(mlp, X[tr], T[tr], M[tr], epochs=6, batch=2048, lr=2e-3, seed=2)
+    assert losses[-1] < losses[0]
+    # held-out masked BCE against the best constant per output column
+    loss_net, _ = pf.pfsp_mlp_loss_grad(mlp, X[te], T[te], M[te])
+    pr = (T[tr] * M[tr]).sum(0) / np.maximum(M[tr].sum(0), 1)
+    pr = np.clip(pr, 1e-4, 1 - 1e-4)
+    const = -(M[te] * (T[te] * np.log(pr) + (1 - T[te]) * np.log(1 - pr))).sum() / len(te)
+    assert loss_net < const, (loss_net, const)
