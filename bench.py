@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1000000, help="nodes in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-proof leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-ordering comparison")
     return ap.parse_args()
 
 
@@ -203,6 +204,25 @@ def solve_leg(pfsp, seeds=range(1, 11)):
             "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds)}
 
 
+def learned_leg(pfsp):
+    """Learned ordering vs the plain full-pair LB2 solver on n = 50, m = 5 and
+    n = 30, m = 10 (5 seeds each, from NEH to the proven optimum): networks
+    trained on the GPU on the solver's own traces of 20-job instances with the
+    same m; identical optima required, times and decomposed nodes reported."""
+    from paper_2012_09511_gb300 import learned
+    rep = learned.compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), time_limit_s=20.0,
+                          depth_fracs=(4,))
+    out = {}
+    for shape, v in rep.items():
+        out[shape] = {k: v[k] for k in ("training", "solved_by_both", "time_plain_s", "time_learned_s",
+                                        "speedup", "node_ratio_learned_over_plain")}
+        out[shape]["same_optimum_every_seed"] = all(r["same_optimum"] for r in v["instances"])
+        out[shape]["per_seed"] = [{k: (r[k] if not isinstance(r[k], dict) else
+                                       {kk: r[k][kk] for kk in ("seconds", "decomposed", "cmax")})
+                                   for k in ("seed", "plain", "learned")} for r in v["instances"]]
+    return out
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -347,6 +367,8 @@ def run_native(args):
         out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample)
     if not args.no_solve and ws == 1:
         out["solve"] = solve_leg(pfsp)
+    if not args.no_learned and ws == 1:
+        out["learned"] = learned_leg(pfsp)
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()

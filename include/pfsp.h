@@ -155,6 +155,7 @@ typedef struct {
     double min_steal;
     const pfsp_mlp *mlp;  /* network used by the PFSP_LEARN_* flags (built for the instance's m) */
     int learned;          /* PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0 = plain solver */
+    int learn_depth;      /* the network orders rows of level < learn_depth only (0 = every level) */
     int reserved[8];
 } pfsp_options;
 

@@ -48,6 +48,7 @@ struct Explorer {
     const SmemTables &T;
     const WarpScratch &W;
     ExplorerSmem &X;
+    const MlpDev *net;  // the network staged in shared memory (NULL: plain solver)
     int n, m, S, lane, me;
     uint8_t *rj;
     int32_t *rl;
@@ -57,8 +58,9 @@ struct Explorer {
     unsigned long long pending_nodes;
     unsigned long long deadline;
 
-    __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_)
-        : a(a_), T(T_), W(W_), X(X_), me(me_) {
+    __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
+                        const MlpDev *net_)
+        : a(a_), T(T_), W(W_), X(X_), net(net_), me(me_) {
         n = a.n;
         m = a.m;
         S = a.S;
@@ -160,7 +162,7 @@ struct Explorer {
     // work sit in W.F / W.B / W.R: by decreasing sum over the slot's pairs of
     // the network's probability that the pair attains a child's LB2.
     __device__ void slot_order() {
-        const MlpDev &P = a.mlp;
+        const MlpDev &P = *net;
         unsigned char *ms = mlp_scratch();
         __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
         for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
@@ -204,7 +206,7 @@ struct Explorer {
     // Depends on the node alone (never on the incumbent), so every explorer
     // that rebuilds this row orders it the same way.
     __device__ void child_order(int dir, int u, int (&pos)[NW]) {
-        const MlpDev &P = a.mlp;
+        const MlpDev &P = *net;
         unsigned char *ms = mlp_scratch();
         __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
         const int nj = (n + 3) & ~3;
@@ -322,7 +324,7 @@ struct Explorer {
         decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
         if ((kind & PFSP_LB2) && m >= 2) {
             const int *order = nullptr;
-            if ((a.learned & PFSP_LEARN_PAIR_ORDER) && S >= 2 && cb.u > 0) {
+            if ((a.learned & PFSP_LEARN_PAIR_ORDER) && net && S >= 2 && cb.u > 0 && I + 1 < a.learn_depth) {
                 slot_order();
                 order = X.sorder;
             }
@@ -371,7 +373,7 @@ struct Explorer {
         int npruned = 0;
         int pos[NW];
         for (int h = 0; h < NW; ++h) pos[h] = lane + 32 * h;
-        if ((a.learned & PFSP_LEARN_CHILD_ORDER) && u >= 2) child_order(dir, u, pos);
+        if ((a.learned & PFSP_LEARN_CHILD_ORDER) && net && u >= 2 && row < a.learn_depth) child_order(dir, u, pos);
         for (int h = 0; h < NW; ++h) {
             int c = lane + 32 * h;
             int lb = dir ? vb[h] : vf[h];
@@ -647,9 +649,9 @@ struct Explorer {
 // the solve is stopped.  Counters are added to a.counters on return.
 template <int NW, int MT>
 __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const WarpScratch &W, ExplorerSmem &X,
-                             int me) {
+                             int me, const MlpDev *net) {
     const int lane = threadIdx.x & 31;
-    Explorer<NW, MT> ex(a, T, W, X, me);
+    Explorer<NW, MT> ex(a, T, W, X, me, net);
     bool nonempty = false;
     {
         // start < end ?

@@ -148,8 +148,11 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         a.inv_scale = tot > 0 ? (float)m / (float)tot : 1.0f;
     }
     a.learned = opt->learned;
+    a.learn_depth = opt->learn_depth > 0 ? opt->learn_depth : n;
     a.warp_words = (a.warp_words + 7) & ~7;  // keeps every warp's scratch 32-byte aligned
-    a.warp_base = (a.tab_words + 7) & ~7;
+    a.net_base = (a.tab_words + 7) & ~7;
+    a.net_words = 0;
+    a.warp_base = a.net_base;
     const int per_warp = a.warp_words + (solve_warp_words(n, m, opt->bound) -
                                          warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2));
     int dev = 0, nsm = 1, optin = 48 * 1024;
@@ -158,6 +161,20 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
     long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
+    if (use_net) {
+        // stage the network's weights in shared memory when that costs no
+        // explorer, or when the network runs on most levels (every node then
+        // pays the weights' latency); otherwise it is read from L2
+        const int staged = mlp_staged_words(net_D0, net_O);
+        const long long fit_staged =
+            ((long long)optin - 256 - (long long)(a.net_base + staged) * 4) / ((long long)per_warp * 4);
+        const long long want = std::min<long long>(warps, fit);
+        if (fit_staged >= want || a.learn_depth > n / 2) {
+            a.net_words = staged;
+            a.warp_base = a.net_base + staged;
+            fit = fit_staged;
+        }
+    }
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
     size_t smem = (size_t)(a.warp_base + warps * per_warp) * 4;

@@ -63,15 +63,20 @@ struct SolveArgs {
     int trace_stride;
     // learned ordering (PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0: off)
     int learned;
-    MlpDev mlp;
+    MlpDev mlp;           // network in global memory (staged into shared memory by the kernel)
     float inv_scale;      // 1 / (mean machine load) for the network's features
     int mlp_off;          // word offset of the network's scratch from the warp's base
+    int learn_depth;      // rows of level < learn_depth are ordered by the network
+    int net_base;         // word offset of the staged network in shared memory
+    int net_words;        // words of the staged network (0: not staged)
 };
 
 int solve_warp_words(int n, int m, int bound);
 // Network scratch placement for a learned solve: sets *off (words from the
 // warp base) and returns the extra words to add to the per-warp stride.
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off);
+// Words of the network staged in shared memory (bf16 weights + fp32 biases).
+int mlp_staged_words(int D0, int O);
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 

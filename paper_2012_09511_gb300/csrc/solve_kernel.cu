@@ -50,6 +50,32 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
     WarpScratch W = carve_warp(wbase, a.n, a.m);
     ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
     const int me = blockIdx.x * warps + wib;
+    // the ordering network, copied once per CTA into shared memory
+    __shared__ MlpDev net;
+    if (a.net_words) {
+        const MlpDev &G = a.mlp;
+        const int nw = (G.D0 * G.H + G.H * G.H + G.H * G.O) / 2;  // bf16 weights, W1 | W2 | W3 contiguous
+        int *dst = smem + a.net_base;
+        const int *src = reinterpret_cast<const int *>(G.W1);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        float *fb = reinterpret_cast<float *>(dst + nw);
+        for (int i = threadIdx.x; i < G.H; i += blockDim.x) {
+            fb[i] = G.b1[i];
+            fb[G.H + i] = G.b2[i];
+        }
+        for (int i = threadIdx.x; i < G.O; i += blockDim.x) fb[2 * G.H + i] = G.b3[i];
+        if (threadIdx.x == 0) {
+            net = G;
+            const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(dst);
+            net.W1 = wb;
+            net.W2 = wb + G.D0 * G.H;
+            net.W3 = wb + G.D0 * G.H + G.H * G.H;
+            net.b1 = fb;
+            net.b2 = fb + G.H;
+            net.b3 = fb + 2 * G.H;
+        }
+        __syncthreads();
+    }
     if (me >= a.K) return;
 
     for (int i = lane; i < a.n; i += 32) {
@@ -61,11 +87,16 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
         X.seq = 0;
     }
     __syncwarp();
-    run_explorer<NW, MT>(a, T, W, X, me);
+    run_explorer<NW, MT>(a, T, W, X, me, a.net_words ? &net : (a.learned & 3) ? &a.mlp : nullptr);
 }
 
 int solve_warp_words(int n, int m, int bound) {
     return warp_words(n, m, n > 32, bound == PFSP_LB2 && m >= 2) + kExplorerWords;
+}
+
+int mlp_staged_words(int D0, int O) {
+    const int h = kMlpHidden;
+    return ((D0 * h + h * h + h * O) / 2 + 2 * h + O + 7) & ~7;
 }
 
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {

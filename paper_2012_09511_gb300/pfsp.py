@@ -62,7 +62,7 @@ class pfsp_options(ctypes.Structure):
     _fields_ = [("init_ub", ctypes.c_int32), ("node_limit", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
                 ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
-                ("learned", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 if not os.path.exists(LIB_PATH):
