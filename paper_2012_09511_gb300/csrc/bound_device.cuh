@@ -68,22 +68,29 @@ struct WarpScratch {
     int *F, *R, *B;   // [32] each: parent front, remaining work, back
     int *ul;          // [64] compact list: ul[c] = c-th unscheduled job
     int *cidx;        // [64] cidx[j] = compact index of job j
-    int *Gf;          // [nr][mp] forward child: F'_k + R_k - p_jk
-    int *Gb;          // [nr][mp] backward child: F_k + R_k - p_jk
+    int2 *G;          // [nr][mp] {forward child: F'_k + R_k - p_jk, backward child: F_k + R_k - p_jk}
     int *Bb;          // [nr][mp] backward child back B'_k
-    int2 *E;          // [nr][32] prefix pass records {PB, t | c << 8} (per lane)
-    int *Cb;          // [nr][32] C of child c (per lane); E..Cb doubles as int2 [u][33]
+    int2 *E;          // [nr][32] prefix pass records {PB, t | c << 8} (per lane); NULL for register walks
+    int *Cb;          // [nr][32] C of child c (per lane)
+    int2 *X;          // [u][33] transpose buffer, aliasing E and Cb (or Cb and the words after it)
     int2 *Acc;        // [nr][32] accumulators (only when not kept in registers)
 };
 
-__host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2) {
+// Walks of up to kRegWalk jobs keep their records in registers (scan_slot_reg).
+constexpr int kRegWalk = 20;
+
+// reg_walk: the layout of kernels whose LB2 walks keep their records in
+// registers (n <= kRegWalk): no E region.
+__host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2, bool reg_walk = false) {
     if (!lb2) return 224;
     int nr = round4(n);
     int g = round4(nr * (m | 1));
-    return 224 + 3 * g + 96 * nr + (smem_acc ? 64 * nr : 0);
+    // G takes 2g words; then E + Cb (96 nr), or Cb + X (66 nr) without E
+    const int walk = reg_walk ? 66 * nr : 96 * nr;
+    return 224 + 3 * g + walk + (smem_acc ? 64 * nr : 0);
 }
 
-__device__ inline WarpScratch carve_warp(int *base, int n, int m) {
+__device__ inline WarpScratch carve_warp(int *base, int n, int m, bool reg_walk = false) {
     int nr = round4(n);
     int g = round4(nr * (m | 1));
     WarpScratch w;
@@ -92,12 +99,19 @@ __device__ inline WarpScratch carve_warp(int *base, int n, int m) {
     w.B = base + 64;
     w.ul = base + 96;
     w.cidx = base + 160;
-    w.Gf = base + 224;
-    w.Gb = w.Gf + g;
-    w.Bb = w.Gb + g;
-    w.E = reinterpret_cast<int2 *>(w.Bb + g);
-    w.Cb = w.Bb + g + 64 * nr;
-    w.Acc = reinterpret_cast<int2 *>(w.Cb + 32 * nr);
+    w.G = reinterpret_cast<int2 *>(base + 224);
+    w.Bb = base + 224 + 2 * g;
+    if (reg_walk) {
+        w.E = nullptr;
+        w.Cb = w.Bb + g;
+        w.X = reinterpret_cast<int2 *>(w.Cb);
+        w.Acc = reinterpret_cast<int2 *>(w.Cb + 66 * nr);
+    } else {
+        w.E = reinterpret_cast<int2 *>(w.Bb + g);
+        w.Cb = w.Bb + g + 64 * nr;
+        w.X = w.E;
+        w.Acc = reinterpret_cast<int2 *>(w.Cb + 32 * nr);
+    }
     return w;
 }
 
@@ -118,11 +132,9 @@ __device__ __forceinline__ int lowest_bit(umask_t<NW> x) {
     else return __ffsll((long long)x) - 1;
 }
 
-template <int NW>
-__device__ __forceinline__ int highest_bit(umask_t<NW> x) {
-    if constexpr (NW == 1) return 31 - __clz(x);
-    else return 63 - __clzll((long long)x);
-}
+// max(a + b, c): the step of every max-plus recurrence below, one DPX
+// add-max instruction on sm_90 and later.
+__device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
 
 // Decompose the node whose permutation entries are held one per lane
 // (job0 = position lane, job1 = position lane + 32) with depths d1, d2.
@@ -161,45 +173,38 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
         }
     }
 
-    // ---- step 1: front (Eq. 1 over sigma1) as a wavefront over machines -------
-    int Fk = 0, Sk = 0;
+    // ---- steps 1 and 3: front (Eq. 1 over sigma1) and back (Eq. 1 over the
+    // reversed sigma2 on reversed machines) as two wavefronts over machines,
+    // run in the same loop so that their shuffle chains overlap -------------
+    int Fk = 0, Bk = 0, Sk = 0;
     {
-        int steps = d1 > 0 ? d1 + m - 1 : 0;
+        const int stepsF = d1 > 0 ? d1 + m - 1 : 0;
+        const int stepsB = d2 > 0 ? d2 + m - 1 : 0;
+        const int steps = max(stepsF, stepsB);
+        const int r = m - 1 - lane;
         for (int s = 0; s < steps; ++s) {
-            int i = s - lane;
+            const int i = s - lane;  // sigma1 position this machine handles now
+            const int ib = s - r;    // position from the end of sigma2
             int left = __shfl_up_sync(PFSP_FULL, Fk, 1);
+            int right = __shfl_down_sync(PFSP_FULL, Bk, 1);
             if (lane == 0) left = 0;
-            int ja = __shfl_sync(PFSP_FULL, job0, i & 31);
-            int j = ja;
+            if (lane == m - 1) right = 0;
+            const int pos = n - 1 - ib;
+            int jf = __shfl_sync(PFSP_FULL, job0, i & 31);
+            int jb = __shfl_sync(PFSP_FULL, job0, pos & 31);
             if constexpr (NW == 2) {
-                int jb = __shfl_sync(PFSP_FULL, job1, i & 31);
-                j = i >= 32 ? jb : ja;
+                int jf1 = __shfl_sync(PFSP_FULL, job1, i & 31);
+                int jb1 = __shfl_sync(PFSP_FULL, job1, pos & 31);
+                jf = i >= 32 ? jf1 : jf;
+                jb = pos >= 32 ? jb1 : jb;
             }
             if (lane < m && i >= 0 && i < d1) {
-                int pk = T.pm[lane * nj + j];
+                int pk = T.pm[lane * nj + jf];
                 Fk = max(Fk, left) + pk;
                 Sk += pk;
             }
-        }
-    }
-    // ---- step 3: back (reversed sigma2 on reversed machines) ------------------
-    int Bk = 0;
-    {
-        int steps = d2 > 0 ? d2 + m - 1 : 0;
-        int r = m - 1 - lane;
-        for (int s = 0; s < steps; ++s) {
-            int i = s - r;
-            int right = __shfl_down_sync(PFSP_FULL, Bk, 1);
-            if (lane == m - 1) right = 0;
-            int pos = n - 1 - i;
-            int ja = __shfl_sync(PFSP_FULL, job0, pos & 31);
-            int j = ja;
-            if constexpr (NW == 2) {
-                int jb = __shfl_sync(PFSP_FULL, job1, pos & 31);
-                j = pos >= 32 ? jb : ja;
-            }
-            if (lane < m && i >= 0 && i < d2) {
-                int pk = T.pm[lane * nj + j];
+            if (lane < m && ib >= 0 && ib < d2) {
+                int pk = T.pm[lane * nj + jb];
                 Bk = max(Bk, right) + pk;
                 Sk += pk;
             }
@@ -221,26 +226,25 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
         out.lb1b[h] = kNegInf;
         int c = lane + 32 * h;
         if (c < u) {
-            int j = W.ul[c];
-            int f = 0, lf = kNegInf;
+            // forward child: machines upwards from the parent's front;
+            // backward child: machines downwards from its back (two
+            // independent chains in one loop)
+            const int j = W.ul[c];
+            int f = 0, lf = kNegInf, b = 0, lb = kNegInf;
 #pragma unroll
-            for (int k = 0; k < m; ++k) {
-                int pk = T.pm[k * nj + j];
-                f = max(f, W.F[k]) + pk;
-                int g = f + W.R[k] - pk;
-                lf = max(lf, g + W.B[k]);
-                if (want2) W.Gf[c * mp + k] = g;
-            }
-            int b = 0, lb = kNegInf;
-#pragma unroll
-            for (int k = m - 1; k >= 0; --k) {
-                int pk = T.pm[k * nj + j];
-                b = max(b, W.B[k]) + pk;
-                int g = W.F[k] + W.R[k] - pk;
-                lb = max(lb, g + b);
+            for (int i = 0; i < m; ++i) {
+                const int kf = i, kb = m - 1 - i;
+                const int pf = T.pm[kf * nj + j], pb = T.pm[kb * nj + j];
+                f = max(f, W.F[kf]) + pf;
+                b = max(b, W.B[kb]) + pb;
+                const int gf = f + W.R[kf] - pf;
+                const int gb = W.F[kb] + W.R[kb] - pb;
+                lf = addmax(gf, W.B[kf], lf);
+                lb = addmax(gb, b, lb);
                 if (want2) {
-                    W.Gb[c * mp + k] = g;
-                    W.Bb[c * mp + k] = b;
+                    W.G[c * mp + kf].x = gf;
+                    W.G[c * mp + kb].y = gb;
+                    W.Bb[c * mp + kb] = b;
                 }
             }
             out.lb1f[h] = lf;
@@ -254,50 +258,137 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
 }
 
 // One slot of the LB2 sweep for this lane's pair: walk the unscheduled jobs
-// (bit mask Upos of their reversed positions) in ascending Johnson order
-// recording the prefix constant PB before each job, then backwards composing
-// the suffix maps, leaving C of every child (compact index c) in W.Cb[c][lane].
+// (bit mask Upos of their positions in the pair's Johnson order, lowest bit
+// first) recording the prefix constant PB before each job, then backwards
+// composing the suffix maps, leaving C of every child (compact index c) in
+// W.Cb[c][lane].  Both walks take four jobs per round: the next positions
+// come off the mask by clearing its lowest bit (a two-operation chain), so
+// the table loads of the four jobs issue together instead of each waiting
+// for the previous job's.
 template <int NW>
 __device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, int2 *E, umask_t<NW> Upos, int u,
                                           int lane) {
-    using mask_t = umask_t<NW>;
     int PB = kNegInf;
-    for (int i = 0; i < u; ++i) {
-        int t = highest_bit<NW>(Upos);
-        Upos ^= mask_t(1) << t;
-        int2 e = pt[t * 32];
-        int c = W.cidx[e.x & 0xff];
-        E[i * 32] = make_int2(PB, t | (c << 8));
-        PB = max(PB + (e.x >> 8), e.y);
+    for (int i = 0; i < u; i += 4) {
+        int t[4];
+        int2 e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            t[q] = lowest_bit<NW>(Upos);  // -1 once the mask is empty
+            Upos &= Upos - 1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = (i + q < u) ? pt[t[q] * 32] : make_int2(0, kNegInf);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // rows u..round4(u)-1 get a record that the backward walk never reads
+            const int c = W.cidx[e[q].x & 0xff];
+            E[(i + q) * 32] = make_int2(PB, (t[q] & 0xff) | (c << 8));
+            PB = addmax(PB, e[q].x >> 8, e[q].y);  // identity for a padding step
+        }
     }
     int SA = 0, SB = kNegInf;
-    for (int i = u - 1; i >= 0; --i) {
-        int2 q = E[i * 32];
-        int2 e = pt[(q.y & 0xff) * 32];
-        W.Cb[(q.y >> 8) * 32 + lane] = max(q.x + SA, SB);
-        SB = max(e.y + SA, SB);
-        SA += e.x >> 8;
+    for (int i = u - 1; i >= 0; i -= 4) {
+        int2 q[4], e[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) q[r] = (i - r >= 0) ? E[(i - r) * 32] : make_int2(0, 0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) e[r] = (i - r >= 0) ? pt[(q[r].y & 0xff) * 32] : make_int2(0, kNegInf);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (i - r >= 0) {
+                W.Cb[(q[r].y >> 8) * 32 + lane] = addmax(q[r].x, SA, SB);
+                SB = addmax(e[r].y, SA, SB);
+                SA += e[r].x >> 8;
+            }
+        }
     }
 }
 
-// LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
-// written by decompose_lb1.  `order` (may be NULL) gives the order in which
-// the slots are swept; with cap < INT_MAX the sweep stops after the first
-// slot at which every child's bound is known to be >= cap (its LB1 or one of
-// the pair terms already seen reaches cap): the children's values are then
-// lower bounds >= cap, exact once capped at cap.
-template <int NW, int MT>
-__device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                              ChildBounds<NW> &out, int cap, const int *order) {
+// Register walks keep the forward records in registers: the prefix
+// constant of step i in PBr[i] and the position of its job in byte i % 4 of
+// tb[i / 4].  All indices below are compile-time constants.
+
+// Backward steps 4G+3 .. 4G (those below u) of scan_slot_reg.
+template <int G>
+__device__ __forceinline__ void scan_back_group(const WarpScratch &W, const int2 *pt, const int (&PBr)[kRegWalk],
+                                                const unsigned (&tb)[kRegWalk / 4], int u, int lane, int &SA,
+                                                int &SB) {
+    int2 e[4];
+    int c[4];
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+        const int t = (tb[G] >> (8 * r)) & 0xff;
+        e[r] = (4 * G + r < u) ? pt[t * 32] : make_int2(0, kNegInf);
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; --r) c[r] = W.cidx[e[r].x & 0xff];
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+        if (4 * G + r < u) {
+            W.Cb[c[r] * 32 + lane] = addmax(PBr[4 * G + r], SA, SB);
+            SB = addmax(e[r].y, SA, SB);
+            SA += e[r].x >> 8;
+        }
+    }
+}
+
+// scan_slot for u <= kRegWalk without the per-step records in shared memory:
+// the forward walk keeps them in registers, the backward walk re-reads the
+// job's table entry (for a, b and the job) and the compact index.  It is
+// entered at the group holding step u - 1.
+template <int NW>
+__device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *pt, umask_t<NW> Upos, int u,
+                                              int lane) {
+    int PBr[kRegWalk];
+    unsigned tb[kRegWalk / 4];
+    int PB = kNegInf;
+#pragma unroll
+    for (int g = 0; g < kRegWalk / 4; ++g) {
+        if (4 * g >= u) break;
+        int t[4];
+        int2 e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            t[q] = lowest_bit<NW>(Upos);  // -1 once the mask is empty
+            Upos &= Upos - 1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = (4 * g + q < u) ? pt[t[q] * 32] : make_int2(0, kNegInf);
+        tb[g] = (unsigned)(t[0] & 0xff) | ((unsigned)(t[1] & 0xff) << 8) | ((unsigned)(t[2] & 0xff) << 16) |
+                ((unsigned)(t[3] & 0xff) << 24);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            PBr[4 * g + q] = PB;
+            PB = addmax(PB, e[q].x >> 8, e[q].y);  // identity for a padding step
+        }
+    }
+    int SA = 0, SB = kNegInf;
+    static_assert(kRegWalk == 20, "the entry switch below lists kRegWalk / 4 groups");
+    switch ((u + 3) >> 2) {
+        case 5: scan_back_group<4>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
+        case 4: scan_back_group<3>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
+        case 3: scan_back_group<2>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
+        case 2: scan_back_group<1>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
+        case 1: scan_back_group<0>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
+        default: break;
+    }
+}
+
+// LB2 sweep over the slots.  NC > 0: the children's accumulators are NC
+// registers per direction (u <= NC); NC = 0: they live in W.Acc.  RW: the
+// walks keep their records in registers (u <= kRegWalk).
+template <int NW, int MT, int NC, bool RW>
+__device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
+                                          ChildBounds<NW> &out, int cap, const int *order) {
     using mask_t = umask_t<NW>;
-    constexpr bool REGACC = (NW == 1);
+    constexpr bool REGACC = NC > 0;
     const int m = MT ? MT : m_rt;
     const int S = MT ? (MT * (MT - 1) / 2 + 31) / 32 : S_rt;
     const int lane = threadIdx.x & 31;
     const int mp = m | 1;
     const mask_t U = out.U;
     const int u = out.u;
-    if (u == 0 || m < 2) return;
     __syncwarp();
     // children already decided by LB1 (only used with a cap)
     mask_t done_f = 0, done_b = 0;
@@ -311,18 +402,18 @@ __device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScr
         }
     }
     const mask_t all = (u >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << u) - 1);
-    int accf[REGACC ? 32 : 1], accb[REGACC ? 32 : 1];
+    int accf[REGACC ? NC : 1], accb[REGACC ? NC : 1];
     if constexpr (REGACC) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) { accf[c] = kNegInf; accb[c] = kNegInf; }
+        for (int c = 0; c < NC; ++c) { accf[c] = kNegInf; accb[c] = kNegInf; }
     } else {
         for (int c = 0; c < u; ++c) W.Acc[c * 32 + lane] = make_int2(kNegInf, kNegInf);
     }
     const int u4 = (u + 3) & ~3;
-    int2 *E = W.E + lane;
-    // (reversed) positions of the unscheduled jobs in each pair's Johnson
-    // order, one bit mask per slot; with a compile-time slot count all masks
-    // are built in a single walk over the unscheduled jobs
+    int2 *E = RW ? nullptr : W.E + lane;
+    // positions of the unscheduled jobs in each pair's Johnson order, one
+    // bit mask per slot; with a compile-time slot count all masks are built
+    // in a single walk over the unscheduled jobs
     constexpr int SC = MT ? (MT * (MT - 1) / 2 + 31) / 32 : 1;
     mask_t UposAll[SC];
     if constexpr (MT > 0) {
@@ -357,29 +448,31 @@ __device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScr
             for (mask_t um = U; um; um &= um - 1)
                 Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];
         }
-        scan_slot<NW>(W, pt, E, Upos, u, lane);
+        if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane);
+        else scan_slot<NW>(W, pt, E, Upos, u, lane);
         // evaluation: the third pair term of every child of this parent
-        const int *gf = W.Gf + k;
-        const int *gb = W.Gb + k;
+        const int2 *gk = W.G + k;
         const int *bb = W.Bb + l;
         const int *cb = W.Cb + lane;
         if constexpr (REGACC) {
 #pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 4) {
+            for (int c0 = 0; c0 < NC; c0 += 4) {
                 if (c0 >= u4) break;
 #pragma unroll
                 for (int c = c0; c < c0 + 4; ++c) {
-                    int C = cb[c * 32];
-                    accf[c] = max(accf[c], gf[c * mp] + C + Bl);
-                    accb[c] = max(accb[c], gb[c * mp] + C + bb[c * mp]);
+                    const int C = cb[c * 32];
+                    const int2 g = gk[c * mp];
+                    accf[c] = max(accf[c], g.x + C + Bl);
+                    accb[c] = max(accb[c], g.y + C + bb[c * mp]);
                 }
             }
         } else {
             for (int c = 0; c < u; ++c) {
-                int C = cb[c * 32];
+                const int C = cb[c * 32];
+                const int2 g = gk[c * mp];
                 int2 v = W.Acc[c * 32 + lane];
-                v.x = max(v.x, gf[c * mp] + C + Bl);
-                v.y = max(v.y, gb[c * mp] + C + bb[c * mp]);
+                v.x = max(v.x, g.x + C + Bl);
+                v.y = max(v.y, g.y + C + bb[c * mp]);
                 W.Acc[c * 32 + lane] = v;
             }
         }
@@ -388,7 +481,7 @@ __device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScr
             mask_t mf = 0, mb = 0;
             if constexpr (REGACC) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     if (c >= u) break;
                     mf |= (mask_t)(accf[c] >= cap) << c;
                     mb |= (mask_t)(accb[c] >= cap) << c;
@@ -418,10 +511,10 @@ __device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScr
     }
     // ---- max over lanes (pairs) per child: transpose through padded rows ------
     __syncwarp();
-    int2 *X = W.E;  // [u][33], aliases E and Cb
+    int2 *X = W.X;  // [u][33], aliases the walk records and Cb
     if constexpr (REGACC) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
+        for (int c = 0; c < NC; ++c) {
             if (c >= u) break;
             X[c * 33 + lane] = make_int2(accf[c], accb[c]);
         }
@@ -447,13 +540,32 @@ __device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScr
     }
 }
 
+// LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
+// written by decompose_lb1.  `order` (may be NULL) gives the order in which
+// the slots are swept; with cap < INT_MAX the sweep stops after the first
+// slot at which every child's bound is known to be >= cap (its LB1 or one of
+// the pair terms already seen reaches cap): the children's values are then
+// lower bounds >= cap, exact once capped at cap.
+// WALK = 1: register walks (n <= kRegWalk, scratch carved with reg_walk);
+// WALK = 0: walks through shared memory (any n).  Fixed per kernel, so that
+// a kernel carries the register demand of one path only.
+template <int NW, int MT, int WALK = 0>
+__device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
+                                              ChildBounds<NW> &out, int cap, const int *order) {
+    if (out.u == 0 || (MT ? MT : m_rt) < 2) return;
+    static_assert(WALK == 0 || NW == 1, "register walks need n <= 32");
+    if constexpr (WALK == 1) lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, order);
+    else lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, order);
+}
+
 // Both phases: the bounds of all 2u children of the node.
-template <int NW, int MT>
+template <int NW, int MT, int WALK = 0>
 __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m_rt,
                                                int S_rt, int kind, int job0, int job1, int d1, int d2,
                                                ChildBounds<NW> &out) {
     decompose_lb1<NW, MT>(T, W, n, m_rt, kind, job0, job1, d1, d2, out);
-    if ((kind & PFSP_LB2) && (MT ? MT : m_rt) >= 2) decompose_lb2<NW, MT>(T, W, n, m_rt, S_rt, out, INT_MAX, nullptr);
+    if ((kind & PFSP_LB2) && (MT ? MT : m_rt) >= 2)
+        decompose_lb2<NW, MT, WALK>(T, W, n, m_rt, S_rt, out, INT_MAX, nullptr);
 }
 
 // Stage `words` int32 (a multiple of 4, 16-byte aligned on both sides) from
@@ -506,7 +618,7 @@ __device__ inline void stage_tables(int *dst, const int32_t *src, int words, uin
     __syncthreads();
 }
 
-constexpr int kWarpsPerCta = 14;
+constexpr int kWarpsPerCta = 16;
 
 // Value of child compact index c held by lanes (c & 31) of register h = c >> 5.
 template <int NW>

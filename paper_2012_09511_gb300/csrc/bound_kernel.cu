@@ -26,11 +26,19 @@ struct BoundArgs {
     int kind;
 };
 
-template <int NW, int MT>
+// Each CTA owns a contiguous range of nodes; its warps claim them one at a
+// time from a shared counter, so that warps on less busy schedulers of the
+// SM take more nodes.
+template <int NW, int MT, int WALK>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(BoundArgs a) {
     extern __shared__ __align__(16) int smem[];
     __shared__ uint64_t bar;
-    stage_tables(smem, a.tab, a.tab_words, &bar);
+    __shared__ unsigned long long next_node;
+    const long long per_cta = (a.num_nodes + gridDim.x - 1) / gridDim.x;
+    const long long first = (long long)blockIdx.x * per_cta;
+    const long long end = min(a.num_nodes, first + per_cta);
+    if (threadIdx.x == 0) next_node = (unsigned long long)first;
+    stage_tables(smem, a.tab, a.tab_words, &bar);  // its first barrier publishes next_node
 
     SmemTables T;
     T.pm = smem + a.off_pm;
@@ -42,16 +50,35 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int n = a.n, m = a.m;
-    WarpScratch W = carve_warp(smem + a.tab_words + wib * a.warp_words, n, m);
+    WarpScratch W = carve_warp(smem + a.tab_words + wib * a.warp_words, n, m, WALK == 1);
 
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long node = (long long)blockIdx.x * (blockDim.x >> 5) + wib; node < a.num_nodes; node += nwarps) {
-        int d1 = a.d1[node], d2 = a.d2[node];
-        const uint8_t *pr = a.perm + node * n;
-        int job0 = lane < n ? pr[lane] : 0;
-        int job1 = (NW == 2 && lane + 32 < n) ? pr[lane + 32] : 0;
-        job0 = job0 < n ? job0 : 0;  // keep indexes in range on malformed rows
-        job1 = job1 < n ? job1 : 0;
+    // the next node's depths and permutation entries are loaded while the
+    // current node is decomposed
+    auto claim = [&]() -> long long {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&next_node, 1ull);
+        return (long long)__shfl_sync(PFSP_FULL, c, 0);
+    };
+    int nd1 = 0, nd2 = 0, nj0 = 0, nj1 = 0;
+    auto fetch = [&](long long v) {
+        if (v < end) {
+            nd1 = a.d1[v];
+            nd2 = a.d2[v];
+            const uint8_t *pr = a.perm + v * n;
+            nj0 = lane < n ? pr[lane] : 0;
+            nj1 = (NW == 2 && lane + 32 < n) ? pr[lane + 32] : 0;
+        }
+    };
+    long long next = claim();
+    fetch(next);
+    for (;;) {
+        const long long node = next;
+        if (node >= end) break;
+        const int d1 = nd1, d2 = nd2;
+        int job0 = nj0 < n ? nj0 : 0;  // keep indexes in range on malformed rows
+        int job1 = nj1 < n ? nj1 : 0;
+        next = claim();
+        fetch(next);
         int32_t *o1 = a.lb1 ? a.lb1 + node * 2 * n : nullptr;
         int32_t *o2 = a.lb2 ? a.lb2 + node * 2 * n : nullptr;
         if (d1 + d2 > n) {
@@ -62,7 +89,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
             continue;
         }
         ChildBounds<NW> cb;
-        decompose_node<NW, MT>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
+        decompose_node<NW, MT, WALK>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
             int j = lane + 32 * h;
@@ -116,12 +143,12 @@ static int fit_warps(const BoundArgs &a, int want) {
     return (int)std::max<long long>(0, std::min<long long>(want, w));
 }
 
-template <int NW, int MT>
+template <int NW, int MT, int WALK>
 static cudaError_t launch_t(const BoundArgs &a, int want_warps, cudaStream_t stream) {
     const int warps = fit_warps(a, want_warps);
     if (warps < 1) return cudaErrorInvalidConfiguration;
     size_t smem = (size_t)(a.tab_words + warps * a.warp_words) * 4;
-    auto kern = bound_batch_kernel<NW, MT>;
+    auto kern = bound_batch_kernel<NW, MT, WALK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -162,20 +189,29 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
     const int warps = kWarpsPerCta;
     const bool want2 = (kind & PFSP_LB2) && L.m >= 2;
     const int nw = L.n <= 32 ? 1 : 2;
-    a.warp_words = warp_words(L.n, L.m, nw == 2, want2);
+    const bool reg_walk = nw == 1 && L.n <= kRegWalk;
+    a.warp_words = warp_words(L.n, L.m, nw == 2, want2, reg_walk);
+    if (reg_walk) {
+        switch (L.m) {
+            case 5: return launch_t<1, 5, 1>(a, warps, stream);
+            case 10: return launch_t<1, 10, 1>(a, warps, stream);
+            case 20: return launch_t<1, 20, 1>(a, warps, stream);
+            default: return launch_t<1, 0, 1>(a, warps, stream);
+        }
+    }
     if (nw == 1) {
         switch (L.m) {
-            case 5: return launch_t<1, 5>(a, warps, stream);
-            case 10: return launch_t<1, 10>(a, warps, stream);
-            case 20: return launch_t<1, 20>(a, warps, stream);
-            default: return launch_t<1, 0>(a, warps, stream);
+            case 5: return launch_t<1, 5, 0>(a, warps, stream);
+            case 10: return launch_t<1, 10, 0>(a, warps, stream);
+            case 20: return launch_t<1, 20, 0>(a, warps, stream);
+            default: return launch_t<1, 0, 0>(a, warps, stream);
         }
     }
     switch (L.m) {
-        case 5: return launch_t<2, 5>(a, warps, stream);
-        case 10: return launch_t<2, 10>(a, warps, stream);
-        case 20: return launch_t<2, 20>(a, warps, stream);
-        default: return launch_t<2, 0>(a, warps, stream);
+        case 5: return launch_t<2, 5, 0>(a, warps, stream);
+        case 10: return launch_t<2, 10, 0>(a, warps, stream);
+        case 20: return launch_t<2, 20, 0>(a, warps, stream);
+        default: return launch_t<2, 0, 0>(a, warps, stream);
     }
 }
 

@@ -99,9 +99,8 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
                 int j = ord[t];
                 int a = p[j * m + l] - p[j * m + k];
                 int b = lag[j] + p[j * m + l];
-                const int r = n - 1 - t;  // reversed: the order runs from the highest index down
-                ptab[(s * n + r) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
-                rank[(j * L.S + s) * 32 + lane] = (uint8_t)r;
+                ptab[(s * n + t) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
+                rank[(j * L.S + s) * 32 + lane] = (uint8_t)t;
             }
         }
 }

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
                 for (int k = 0; k < m; ++k) {
                     const int pk = T.pm[k * nj + j];
                     const int rc = W.R[k] - pk;
-                    xf[k] = (W.Gf[c * mp + k] - rc) * a.inv_scale;  // front after j
+                    xf[k] = (W.G[c * mp + k].x - rc) * a.inv_scale;  // front after j
                     xf[m + k] = W.B[k] * a.inv_scale;
                     xf[2 * m + k] = rc * a.inv_scale;
                     xb[k] = W.F[k] * a.inv_scale;
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
             bool hit = false;
             for (int c = 0; c < u; ++c) {
                 const int C = W.Cb[c * 32 + lane];
-                const int ef = W.Gf[c * mp + k] + C + Bl;
-                const int eb = W.Gb[c * mp + k] + C + W.Bb[c * mp + l];
+                const int ef = W.G[c * mp + k].x + C + Bl;
+                const int eb = W.G[c * mp + k].y + C + W.Bb[c * mp + l];
                 hit |= (ef == lb[128 + c] && lb[128 + c] > lb[c]) || (eb == lb[192 + c] && lb[192 + c] > lb[64 + c]);
             }
             const int q = s * 32 + lane;

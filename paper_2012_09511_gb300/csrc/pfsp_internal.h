@@ -23,14 +23,13 @@ constexpr int kMaxTableBytes = 160 * 1024;  // LB2 tables must fit in shared mem
 //   pm   [m][nj]       processing times by machine (nj = n rounded up to 4)
 //   tot  [32]          per-machine totals T_k = sum_j p[j][k]
 //   kl   [S*32]        machine pair of pair slot q: k | l << 8 (dummy: 0)
-//   rank [n][S][32]    uint8: reversed position n-1-t of job j in the
-//                      Johnson order of the lane's pair (dummy lanes: j)
-//   ptab [S][n][32]    int2 per (slot, reversed position, lane): pair
-//                      q = slot*32+lane, x = (a << 8) | job, y = b, for the job
-//                      at position t of the pair's Johnson order stored at
-//                      index n-1-t, with a = p[j][l] - p[j][k] and
-//                      b = g_j + p[j][l] (g_j = lag).  Dummy lanes (pairs past
-//                      the last one) hold job i at index i with a = 0,
+//   rank [n][S][32]    uint8: position t of job j in the Johnson order of
+//                      the lane's pair (dummy lanes: j)
+//   ptab [S][n][32]    int2 per (slot, position, lane): pair q = slot*32+lane,
+//                      x = (a << 8) | job, y = b, for the job at position t of
+//                      the pair's Johnson order, with a = p[j][l] - p[j][k]
+//                      and b = g_j + p[j][l] (g_j = lag).  Dummy lanes (pairs
+//                      past the last one) hold job i at position i with a = 0,
 //                      b = kNegInf: the identity map.
 struct TableLayout {
     int n, m, P, S, nj;
