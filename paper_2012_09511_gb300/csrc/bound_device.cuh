@@ -65,7 +65,7 @@ __host__ __device__ inline int round4(int w) { return (w + 3) & ~3; }
 // child-indexed tables have round4(n) rows so that the evaluation loop, which
 // walks children in groups of four, stays inside them.
 struct WarpScratch {
-    int *F, *R, *B;   // [32] each: parent front, remaining work, back
+    int4 *FRB;        // [32] per machine k: {front F_k, remaining work R_k, back B_k, F_k + R_k} of the parent
     int *ul;          // [64] compact list: ul[c] = c-th unscheduled job
     int *cidx;        // [64] cidx[j] = compact index of job j
     int2 *G;          // [nr][mp] {forward child: F'_k + R_k - p_jk, backward child: F_k + R_k - p_jk}
@@ -76,31 +76,32 @@ struct WarpScratch {
     int2 *Acc;        // [nr][32] accumulators (only when not kept in registers)
 };
 
+// Words before the child tables: FRB, ul, cidx.
+constexpr int kWarpHead = 256;
+
 // Walks of up to kRegWalk jobs keep their records in registers (scan_slot_reg).
 constexpr int kRegWalk = 20;
 
 // reg_walk: the layout of kernels whose LB2 walks keep their records in
 // registers (n <= kRegWalk): no E region.
 __host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2, bool reg_walk = false) {
-    if (!lb2) return 224;
+    if (!lb2) return kWarpHead;
     int nr = round4(n);
     int g = round4(nr * (m | 1));
     // G takes 2g words; then E + Cb (96 nr), or Cb + X (66 nr) without E
     const int walk = reg_walk ? 66 * nr : 96 * nr;
-    return 224 + 3 * g + walk + (smem_acc ? 64 * nr : 0);
+    return kWarpHead + 3 * g + walk + (smem_acc ? 64 * nr : 0);
 }
 
 __device__ inline WarpScratch carve_warp(int *base, int n, int m, bool reg_walk = false) {
     int nr = round4(n);
     int g = round4(nr * (m | 1));
     WarpScratch w;
-    w.F = base;
-    w.R = base + 32;
-    w.B = base + 64;
-    w.ul = base + 96;
-    w.cidx = base + 160;
-    w.G = reinterpret_cast<int2 *>(base + 224);
-    w.Bb = base + 224 + 2 * g;
+    w.FRB = reinterpret_cast<int4 *>(base);
+    w.ul = base + 128;
+    w.cidx = base + 192;
+    w.G = reinterpret_cast<int2 *>(base + kWarpHead);
+    w.Bb = base + kWarpHead + 2 * g;
     if (reg_walk) {
         w.E = nullptr;
         w.Cb = w.Bb + g;
@@ -182,29 +183,33 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
         const int stepsB = d2 > 0 ? d2 + m - 1 : 0;
         const int steps = max(stepsF, stepsB);
         const int r = m - 1 - lane;
+        // lanes past the last machine take no part (their depths are zero);
+        // lane 0 receives its own F from shfl_up and the lane after the last
+        // machine holds B = 0, both of which leave the recurrence unchanged
+        const unsigned ud1 = lane < m ? d1 : 0, ud2 = lane < m ? d2 : 0;
+        const int *pmrow = T.pm + lane * nj;
         for (int s = 0; s < steps; ++s) {
             const int i = s - lane;  // sigma1 position this machine handles now
             const int ib = s - r;    // position from the end of sigma2
-            int left = __shfl_up_sync(PFSP_FULL, Fk, 1);
-            int right = __shfl_down_sync(PFSP_FULL, Bk, 1);
-            if (lane == 0) left = 0;
-            if (lane == m - 1) right = 0;
+            const int left = __shfl_up_sync(PFSP_FULL, Fk, 1);
+            const int right = __shfl_down_sync(PFSP_FULL, Bk, 1);
             const int pos = n - 1 - ib;
-            int jf = __shfl_sync(PFSP_FULL, job0, i & 31);
-            int jb = __shfl_sync(PFSP_FULL, job0, pos & 31);
+            // source lanes are taken modulo 32
+            int jf = __shfl_sync(PFSP_FULL, job0, i);
+            int jb = __shfl_sync(PFSP_FULL, job0, pos);
             if constexpr (NW == 2) {
-                int jf1 = __shfl_sync(PFSP_FULL, job1, i & 31);
-                int jb1 = __shfl_sync(PFSP_FULL, job1, pos & 31);
+                int jf1 = __shfl_sync(PFSP_FULL, job1, i);
+                int jb1 = __shfl_sync(PFSP_FULL, job1, pos);
                 jf = i >= 32 ? jf1 : jf;
                 jb = pos >= 32 ? jb1 : jb;
             }
-            if (lane < m && i >= 0 && i < d1) {
-                int pk = T.pm[lane * nj + jf];
+            if ((unsigned)i < ud1) {
+                const int pk = pmrow[jf];
                 Fk = max(Fk, left) + pk;
                 Sk += pk;
             }
-            if (lane < m && ib >= 0 && ib < d2) {
-                int pk = T.pm[lane * nj + jb];
+            if ((unsigned)ib < ud2) {
+                const int pk = pmrow[jb];
                 Bk = max(Bk, right) + pk;
                 Sk += pk;
             }
@@ -212,9 +217,8 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
     }
     // ---- step 2: remaining work = totals minus scheduled work -----------------
     if (lane < m) {
-        W.F[lane] = Fk;
-        W.R[lane] = T.tot[lane] - Sk;
-        W.B[lane] = Bk;
+        const int Rk = T.tot[lane] - Sk;
+        W.FRB[lane] = make_int4(Fk, Rk, Bk, Fk + Rk);
     }
     __syncwarp();
 
@@ -235,11 +239,12 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
             for (int i = 0; i < m; ++i) {
                 const int kf = i, kb = m - 1 - i;
                 const int pf = T.pm[kf * nj + j], pb = T.pm[kb * nj + j];
-                f = max(f, W.F[kf]) + pf;
-                b = max(b, W.B[kb]) + pb;
-                const int gf = f + W.R[kf] - pf;
-                const int gb = W.F[kb] + W.R[kb] - pb;
-                lf = addmax(gf, W.B[kf], lf);
+                const int4 Pf = W.FRB[kf], Pb = W.FRB[kb];  // broadcast loads
+                f = max(f, Pf.x) + pf;
+                b = max(b, Pb.z) + pb;
+                const int gf = f + Pf.y - pf;
+                const int gb = Pb.w - pb;
+                lf = addmax(gf, Pf.z, lf);
                 lb = addmax(gb, b, lb);
                 if (want2) {
                     W.G[c * mp + kf].x = gf;
@@ -430,7 +435,7 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
         const int s = order ? order[si] : si;
         const int klw = T.kl[s * 32 + lane];
         const int k = klw & 0xff, l = klw >> 8;
-        const int Bl = W.B[l];
+        const int Bl = W.FRB[l].z;
         const int2 *pt = T.ptab + (size_t)s * n * 32 + lane;
         mask_t Upos;
         if constexpr (MT > 0) {

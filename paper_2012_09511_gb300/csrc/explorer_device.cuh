@@ -156,10 +156,10 @@ struct Explorer {
     }
 
     // Network scratch of this warp (32-byte aligned).
-    __device__ unsigned char *mlp_scratch() const { return (unsigned char *)(W.F + a.mlp_off); }
+    __device__ unsigned char *mlp_scratch() const { return (unsigned char *)((int *)W.FRB + a.mlp_off); }
 
     // Order of the LB2 slots for the node whose front, back and remaining
-    // work sit in W.F / W.B / W.R: by decreasing sum over the slot's pairs of
+    // work sit in W.FRB: by decreasing sum over the slot's pairs of
     // the network's probability that the pair attains a child's LB2.
     __device__ void slot_order() {
         const MlpDev &P = *net;
@@ -168,9 +168,10 @@ struct Explorer {
         for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
         __syncwarp();
         if (lane < m) {
-            Xs[lane] = __float2bfloat16_rn(W.F[lane] * a.inv_scale);
-            Xs[m + lane] = __float2bfloat16_rn(W.B[lane] * a.inv_scale);
-            Xs[2 * m + lane] = __float2bfloat16_rn(W.R[lane] * a.inv_scale);
+            const int4 P = W.FRB[lane];
+            Xs[lane] = __float2bfloat16_rn(P.x * a.inv_scale);
+            Xs[m + lane] = __float2bfloat16_rn(P.z * a.inv_scale);
+            Xs[2 * m + lane] = __float2bfloat16_rn(P.y * a.inv_scale);
         }
         if (lane < 16) X.sscore[lane] = 0.0f;
         __syncwarp();
@@ -221,19 +222,19 @@ struct Explorer {
                     int f = 0;
                     for (int k = 0; k < m; ++k) {
                         const int pk = T.pm[k * nj + j];
-                        f = max(f, W.F[k]) + pk;
+                        f = max(f, W.FRB[k].x) + pk;
                         xr[k] = __float2bfloat16_rn(f * a.inv_scale);
-                        xr[m + k] = __float2bfloat16_rn(W.B[k] * a.inv_scale);
-                        xr[2 * m + k] = __float2bfloat16_rn((W.R[k] - pk) * a.inv_scale);
+                        xr[m + k] = __float2bfloat16_rn(W.FRB[k].z * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((W.FRB[k].y - pk) * a.inv_scale);
                     }
                 } else {
                     int b = 0;
                     for (int k = m - 1; k >= 0; --k) {
                         const int pk = T.pm[k * nj + j];
-                        b = max(b, W.B[k]) + pk;
-                        xr[k] = __float2bfloat16_rn(W.F[k] * a.inv_scale);
+                        b = max(b, W.FRB[k].z) + pk;
+                        xr[k] = __float2bfloat16_rn(W.FRB[k].x * a.inv_scale);
                         xr[m + k] = __float2bfloat16_rn(b * a.inv_scale);
-                        xr[2 * m + k] = __float2bfloat16_rn((W.R[k] - pk) * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((W.FRB[k].y - pk) * a.inv_scale);
                     }
                 }
             }

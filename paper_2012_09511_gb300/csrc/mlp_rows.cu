@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
         __syncwarp();
         // parent features
         if (lane < m) {
-            X[lane] = W.F[lane] * a.inv_scale;
-            X[m + lane] = W.B[lane] * a.inv_scale;
-            X[2 * m + lane] = W.R[lane] * a.inv_scale;
+            const int4 P = W.FRB[lane];
+            X[lane] = P.x * a.inv_scale;
+            X[m + lane] = P.z * a.inv_scale;
+            X[2 * m + lane] = P.y * a.inv_scale;
         }
         // children: features, bounds for the pair pass, descend-first targets
         for (int h = 0; h < NW; ++h) {
@@ -97,11 +98,11 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
                 float *xf = X + (size_t)(1 + j) * a.D0, *xb = X + (size_t)(1 + n + j) * a.D0;
                 for (int k = 0; k < m; ++k) {
                     const int pk = T.pm[k * nj + j];
-                    const int rc = W.R[k] - pk;
+                    const int rc = W.FRB[k].y - pk;
                     xf[k] = (W.G[c * mp + k].x - rc) * a.inv_scale;  // front after j
-                    xf[m + k] = W.B[k] * a.inv_scale;
+                    xf[m + k] = W.FRB[k].z * a.inv_scale;
                     xf[2 * m + k] = rc * a.inv_scale;
-                    xb[k] = W.F[k] * a.inv_scale;
+                    xb[k] = W.FRB[k].x * a.inv_scale;
                     xb[m + k] = W.Bb[c * mp + k] * a.inv_scale;
                     xb[2 * m + k] = rc * a.inv_scale;
                 }
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
         for (int s = 0; s < S && m >= 2 && u > 0; ++s) {
             const int klw = T.kl[s * 32 + lane];
             const int k = klw & 0xff, l = klw >> 8;
-            const int Bl = W.B[l];
+            const int Bl = W.FRB[l].z;
             umask_t<NW> Upos = 0;
             for (umask_t<NW> um = cb.U; um; um &= um - 1)
                 Upos |= umask_t<NW>(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];

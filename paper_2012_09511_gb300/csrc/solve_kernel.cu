@@ -105,7 +105,7 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
     if (bound == PFSP_LB2 && m >= 2) {
         // alias the prefix-record / C region, free outside the LB2 sweep
         const int nr = round4(n);
-        const int e_off = 224 + 3 * round4(nr * (m | 1));
+        const int e_off = kWarpHead + 3 * round4(nr * (m | 1));
         const int start = (e_off + 7) & ~7;
         if (start + need <= bw) {
             *off = start;
