@@ -260,11 +260,11 @@ def run_native(args):
     dev = torch.device("cuda", local)
     from paper_2012_09511_gb300 import build
     build.build()
-    from paper_2012_09511_gb300 import inputs, pfsp
+    from paper_2012_09511_gb300 import inputs, pfsp, shard
 
     n, m, N = N_JOBS, M_MACH, args.nodes
     p = inputs.make_instance(n, m, SEED)
-    perm, d1, d2 = inputs.random_nodes(n, N, seed=SEED + rank, dmax=DMAX)
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=shard.rank_seed(SEED, rank), dmax=DMAX)
     children = int(2 * (n - d1.astype(np.int64) - d2.astype(np.int64)).sum())
     ops = algorithmic_ops(n, m, d1, d2)
     inst = pfsp.pfsp_load_instance(p)
@@ -308,12 +308,7 @@ def run_native(args):
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     launch_ms = ms / args.steps
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    tot_children = torch.tensor([children * args.steps], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot_children, op=dist.ReduceOp.SUM)
-    value = tot_children.item() / (t_max.item() * 1e-3)
+    value, slowest_s, _ = shard.whole_job_rate(ms * 1e-3, children * args.steps, device=dev)
 
     # end to end through the host-pointer entry point, pinned host buffers
     hp = torch.from_numpy(perm).pin_memory()
@@ -330,10 +325,7 @@ def run_native(args):
     for _ in range(args.e2e_steps):
         pfsp.pfsp_bound_batch(inst, 3, *args_np, lb1_out=h1.numpy(), lb2_out=h2.numpy())
     e2e_s = max(time.perf_counter() - t0, 1e-9)
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = children * args.e2e_steps * ws / e2e_t.item()
+    e2e_value, _, _ = shard.whole_job_rate(e2e_s, children * args.e2e_steps, device=dev)
 
     if rank != 0:
         if ws > 1:
@@ -347,7 +339,7 @@ def run_native(args):
     traffic = ncu_traffic()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max.item() / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": slowest_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m": m, "nodes_per_gpu": N, "seed": SEED,
                    "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)",

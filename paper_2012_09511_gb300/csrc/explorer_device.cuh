@@ -22,6 +22,10 @@ __device__ inline unsigned long long global_ns() {
 __device__ inline int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
 // Per-warp explorer scratch in shared memory (int words).
+// LB2 slots of the largest machine count the ordering network supports
+// (m = 20: 190 pairs).
+constexpr int kMaxSlots = 6;
+
 struct ExplorerSmem {
     int V[64];      // digit selected at each level
     int dir[64];    // branching direction of each level (0 fwd, 1 bwd)
@@ -42,13 +46,15 @@ struct Stats {
     unsigned long long decomposed, bounded, leaves, pruned, steals, iters;
 };
 
-template <int NW, int MT>
+// LEARNED: the instantiation that runs the ordering network; the plain
+// solver's kernel carries none of its code (nor its register demand).
+template <int NW, int MT, bool LEARNED>
 struct Explorer {
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
     ExplorerSmem &X;
-    const MlpDev *net;  // the network staged in shared memory (NULL: plain solver)
+    const MlpImage *net;  // the network's image staged in shared memory (NULL: plain solver)
     int n, m, S, lane, me;
     uint8_t *rj;
     int32_t *rl;
@@ -59,7 +65,7 @@ struct Explorer {
     unsigned long long deadline;
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
-                        const MlpDev *net_)
+                        const MlpImage *net_)
         : a(a_), T(T_), W(W_), X(X_), net(net_), me(me_) {
         n = a.n;
         m = a.m;
@@ -158,38 +164,78 @@ struct Explorer {
     // Network scratch of this warp (32-byte aligned).
     __device__ unsigned char *mlp_scratch() const { return (unsigned char *)((int *)W.FRB + a.mlp_off); }
 
+    // Layers 1 and 2 of the network on the tile Xs (fused, in registers),
+    // layer 2's activations handed to sink k-tile by k-tile.
+    template <class Sink>
+    __device__ void net_hidden(const __nv_bfloat16 *Xs, Sink &&sink) const {
+        constexpr int KT = MT ? (3 * MT + 15) / 16 : 0;
+        if constexpr (KT > 0) {
+            mlp_fused_hidden<KT, true>(*net, Xs, sink);
+        } else {
+            switch (net->D0 >> 4) {
+                case 1: mlp_fused_hidden<1, true>(*net, Xs, sink); break;
+                case 2: mlp_fused_hidden<2, true>(*net, Xs, sink); break;
+                case 3: mlp_fused_hidden<3, true>(*net, Xs, sink); break;
+                default: mlp_fused_hidden<4, true>(*net, Xs, sink); break;
+            }
+        }
+    }
+
     // Order of the LB2 slots for the node whose front, back and remaining
     // work sit in W.FRB: by decreasing sum over the slot's pairs of
     // the network's probability that the pair attains a child's LB2.
     __device__ void slot_order() {
-        const MlpDev &P = *net;
-        unsigned char *ms = mlp_scratch();
-        __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
-        for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
+        const MlpImage &P = *net;
+        const int ldx = P.D0 + 8;
+        __nv_bfloat16 *Xs = (__nv_bfloat16 *)mlp_scratch();
+        for (int e = lane; e < 16 * ldx; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
         __syncwarp();
         if (lane < m) {
-            const int4 P = W.FRB[lane];
-            Xs[lane] = __float2bfloat16_rn(P.x * a.inv_scale);
-            Xs[m + lane] = __float2bfloat16_rn(P.z * a.inv_scale);
-            Xs[2 * m + lane] = __float2bfloat16_rn(P.y * a.inv_scale);
+            const int4 F = W.FRB[lane];
+            Xs[lane] = __float2bfloat16_rn(F.x * a.inv_scale);
+            Xs[m + lane] = __float2bfloat16_rn(F.z * a.inv_scale);
+            Xs[2 * m + lane] = __float2bfloat16_rn(F.y * a.inv_scale);
         }
         if (lane < 16) X.sscore[lane] = 0.0f;
         __syncwarp();
-        mlp_tile_hidden(P, ms);
+        __nv_bfloat16 *H2 = Xs + 16 * ldx;
+        net_hidden(Xs, MlpPark{H2});
+        __syncwarp();
+        unsigned A2[kMlpHidden / 16][4];
+        mlp_unpark(H2, A2);
+        // row 0 (the parent) sits in lanes 0..3: columns 16p + 2t (+1) and 16p + 8 + 2t (+1)
         const int npairs = m * (m - 1) / 2;
-        for (int j = 0; j < P.O; j += 16) {
-            const float *stt = mlp_tile_logits(P, ms, j);
-            if (lane < 16) {
-                const int col = j + lane;
-                if (col >= 1 && col <= npairs) {
-                    const float z = stt[lane] + P.b3[col];
-                    atomicAdd(&X.sscore[(col - 1) >> 5], 1.0f / (1.0f + expf(-z)));
+        const int t = lane & 3;
+        float part[kMaxSlots];
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSlots; ++s2) part[s2] = 0.0f;
+        for (int p = 0; p < P.O3 / 16; ++p) {
+            float c0[4], c1[4];
+            mlp_tile_cols<kMlpHidden / 16>(A2, P.W3t, kMlpHidden + 8, p, c0, c1);
+            if (lane < 4) {
+                const int cols[4] = {16 * p + 2 * t, 16 * p + 2 * t + 1, 16 * p + 8 + 2 * t, 16 * p + 9 + 2 * t};
+                const float z[4] = {c0[0], c0[1], c1[0], c1[1]};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int col = cols[i];
+                    if (col >= 1 && col <= npairs) {
+                        const float pr = 1.0f / (1.0f + expf(-(z[i] + P.b3[col])));
+#pragma unroll
+                        for (int s2 = 0; s2 < kMaxSlots; ++s2) part[s2] += ((col - 1) >> 5) == s2 ? pr : 0.0f;
+                    }
                 }
             }
-            __syncwarp();
         }
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSlots; ++s2) {
+            float v = part[s2];
+            v += __shfl_xor_sync(PFSP_FULL, v, 1);
+            v += __shfl_xor_sync(PFSP_FULL, v, 2);
+            if (lane == 0 && s2 < S) X.sscore[s2] = v;
+        }
+        __syncwarp();
         if (lane == 0) {
-            for (int s = 0; s < S; ++s) X.sorder[s] = s;
+            for (int s2 = 0; s2 < S; ++s2) X.sorder[s2] = s2;
             for (int a1 = 1; a1 < S; ++a1) {
                 int v = X.sorder[a1], b1 = a1 - 1;
                 while (b1 >= 0 && X.sscore[X.sorder[b1]] < X.sscore[v]) {
@@ -207,43 +253,48 @@ struct Explorer {
     // Depends on the node alone (never on the incumbent), so every explorer
     // that rebuilds this row orders it the same way.
     __device__ void child_order(int dir, int u, int (&pos)[NW]) {
-        const MlpDev &P = *net;
-        unsigned char *ms = mlp_scratch();
-        __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
+        const MlpImage &P = *net;
+        const int ldx = P.D0 + 8;
+        __nv_bfloat16 *Xs = (__nv_bfloat16 *)mlp_scratch();
         const int nj = (n + 3) & ~3;
-        for (int t = 0; t < u; t += 16) {
-            for (int e = lane; e < 16 * P.D0; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
+        for (int t0 = 0; t0 < u; t0 += 16) {
+            for (int e = lane; e < 16 * ldx; e += 32) Xs[e] = __float2bfloat16_rn(0.0f);
             __syncwarp();
-            const int c = t + lane;
+            const int c = t0 + lane;
             if (lane < 16 && c < u) {
                 const int j = W.ul[c];
-                __nv_bfloat16 *xr = Xs + lane * P.D0;
+                __nv_bfloat16 *xr = Xs + lane * ldx;
                 if (dir == 0) {
                     int f = 0;
                     for (int k = 0; k < m; ++k) {
                         const int pk = T.pm[k * nj + j];
-                        f = max(f, W.FRB[k].x) + pk;
+                        const int4 F = W.FRB[k];
+                        f = max(f, F.x) + pk;
                         xr[k] = __float2bfloat16_rn(f * a.inv_scale);
-                        xr[m + k] = __float2bfloat16_rn(W.FRB[k].z * a.inv_scale);
-                        xr[2 * m + k] = __float2bfloat16_rn((W.FRB[k].y - pk) * a.inv_scale);
+                        xr[m + k] = __float2bfloat16_rn(F.z * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((F.y - pk) * a.inv_scale);
                     }
                 } else {
                     int b = 0;
                     for (int k = m - 1; k >= 0; --k) {
                         const int pk = T.pm[k * nj + j];
-                        b = max(b, W.FRB[k].z) + pk;
-                        xr[k] = __float2bfloat16_rn(W.FRB[k].x * a.inv_scale);
+                        const int4 F = W.FRB[k];
+                        b = max(b, F.z) + pk;
+                        xr[k] = __float2bfloat16_rn(F.x * a.inv_scale);
                         xr[m + k] = __float2bfloat16_rn(b * a.inv_scale);
-                        xr[2 * m + k] = __float2bfloat16_rn((W.FRB[k].y - pk) * a.inv_scale);
+                        xr[2 * m + k] = __float2bfloat16_rn((F.y - pk) * a.inv_scale);
                     }
                 }
             }
             __syncwarp();
-            mlp_tile_hidden(P, ms);
-            const float *stt = mlp_tile_logits(P, ms, 0);
-            if (lane < 16 && c < u) {
-                float z = stt[lane * 16] + P.b3[0];
-                X.score[c] = (z == z) ? z : -1e30f;  // a NaN never breaks the ranking
+            float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            net_hidden(Xs, MlpFirstCols{P.W3t, c0});
+            // column 0 of rows g and g + 8 sits in lane 4g
+            if ((lane & 3) == 0) {
+                const int g = lane >> 2;
+                const float z0 = c0[0] + P.b3[0], z1 = c0[2] + P.b3[0];
+                if (t0 + g < u) X.score[t0 + g] = (z0 == z0) ? z0 : -1e30f;  // a NaN never breaks the ranking
+                if (t0 + g + 8 < u) X.score[t0 + g + 8] = (z1 == z1) ? z1 : -1e30f;
             }
             __syncwarp();
         }
@@ -325,9 +376,11 @@ struct Explorer {
         decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
         if ((kind & PFSP_LB2) && m >= 2) {
             const int *order = nullptr;
-            if ((a.learned & PFSP_LEARN_PAIR_ORDER) && net && S >= 2 && cb.u > 0 && I + 1 < a.learn_depth) {
-                slot_order();
-                order = X.sorder;
+            if constexpr (LEARNED) {
+                if ((a.learned & PFSP_LEARN_PAIR_ORDER) && net && S >= 2 && cb.u > 0 && I + 1 < a.learn_depth) {
+                    slot_order();
+                    order = X.sorder;
+                }
             }
             decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
         }
@@ -374,7 +427,9 @@ struct Explorer {
         int npruned = 0;
         int pos[NW];
         for (int h = 0; h < NW; ++h) pos[h] = lane + 32 * h;
-        if ((a.learned & PFSP_LEARN_CHILD_ORDER) && net && u >= 2 && row < a.learn_depth) child_order(dir, u, pos);
+        if constexpr (LEARNED) {
+            if ((a.learned & PFSP_LEARN_CHILD_ORDER) && net && u >= 2 && row < a.learn_depth) child_order(dir, u, pos);
+        }
         for (int h = 0; h < NW; ++h) {
             int c = lane + 32 * h;
             int lb = dir ? vb[h] : vf[h];
@@ -648,11 +703,11 @@ struct Explorer {
 // X.D / X.E / X.etop (empty if start >= end), then select, decompose, answer
 // steal requests and steal until no explorer of the instance holds work or
 // the solve is stopped.  Counters are added to a.counters on return.
-template <int NW, int MT>
+template <int NW, int MT, bool LEARNED = false>
 __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const WarpScratch &W, ExplorerSmem &X,
-                             int me, const MlpDev *net) {
+                             int me, const MlpImage *net) {
     const int lane = threadIdx.x & 31;
-    Explorer<NW, MT> ex(a, T, W, X, me, net);
+    Explorer<NW, MT, LEARNED> ex(a, T, W, X, me, net);
     bool nonempty = false;
     {
         // start < end ?

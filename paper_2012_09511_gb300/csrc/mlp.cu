@@ -86,25 +86,82 @@ __host__ __device__ inline GradSmem grad_smem(int D0, int H, int O) {
     return g;
 }
 
-__global__ void mlp_forward_kernel(MlpDev P, const float *X, long long rows, float *Y) {
+// The inference image (layout in mlp_device.cuh) of O3 output columns:
+// transposed, row-padded bf16 weights from the bf16 copies, fp32 biases.
+__global__ void mlp_image_kernel(MlpDev P, int O3, unsigned char *img) {
+    const int H = P.H, D0 = P.D0, O = P.O;
+    MlpImage I = mlp_image_view(img, D0, O3);
+    __nv_bfloat16 *W1t = const_cast<__nv_bfloat16 *>(I.W1t), *W2t = const_cast<__nv_bfloat16 *>(I.W2t),
+                  *W3t = const_cast<__nv_bfloat16 *>(I.W3t);
+    float *b1 = const_cast<float *>(I.b1), *b2 = const_cast<float *>(I.b2), *b3 = const_cast<float *>(I.b3);
+    const int n1 = H * (D0 + 8), n2 = H * (H + 8), n3 = O3 * (H + 8);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3 + 2 * H + O3; i += gridDim.x * blockDim.x) {
+        if (i < n1) {
+            const int o = i / (D0 + 8), k = i % (D0 + 8);
+            W1t[i] = k < D0 ? P.W1[k * H + o] : zero;
+        } else if (i < n1 + n2) {
+            const int o = (i - n1) / (H + 8), k = (i - n1) % (H + 8);
+            W2t[i - n1] = k < H ? P.W2[k * H + o] : zero;
+        } else if (i < n1 + n2 + n3) {
+            const int o = (i - n1 - n2) / (H + 8), k = (i - n1 - n2) % (H + 8);
+            W3t[i - n1 - n2] = (k < H && o < O) ? P.W3[k * O + o] : zero;
+        } else {
+            const int j = i - n1 - n2 - n3;
+            if (j < H) b1[j] = P.b1[j];
+            else if (j < 2 * H) b2[j - H] = P.b2[j - H];
+            else b3[j - 2 * H] = (j - 2 * H) < O ? P.b3[j - 2 * H] : 0.0f;
+        }
+    }
+}
+
+cudaError_t mlp_build_image(const pfsp_mlp *M, int O3, void *dst, cudaStream_t st) {
+    const int total = mlp_image_bytes(M->D0, O3) / 2;
+    mlp_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(mlp_view(M), O3, (unsigned char *)dst);
+    return cudaGetLastError();
+}
+
+// Forward pass with the fused inference path that the solver uses: each CTA
+// copies the image into shared memory, each warp runs 16-row tiles.
+template <int KT1>
+__global__ void mlp_forward_kernel(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
+                                   float *Y) {
     extern __shared__ __align__(128) unsigned char sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    GradSmem L = grad_smem(P.D0, P.H, P.O);
-    unsigned char *w = sm + (size_t)wib * L.total;
-    __nv_bfloat16 *Xs = (__nv_bfloat16 *)(w + L.xs), *H1 = (__nv_bfloat16 *)(w + L.h1), *H2 = (__nv_bfloat16 *)(w + L.h2);
-    float *Yf = (float *)(w + L.yf), *st = (float *)(w + L.st);
+    const int D0 = 16 * KT1, ldx = D0 + 8;
+    for (int i = threadIdx.x; i < img_bytes / 16; i += blockDim.x)
+        reinterpret_cast<int4 *>(sm)[i] = reinterpret_cast<const int4 *>(img)[i];
+    __syncthreads();
+    const MlpImage P = mlp_image_view(sm, D0, O);
+    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(sm + img_bytes + wib * mlp_scratch_bytes(D0));
+    const int g = lane >> 2, t = lane & 3;
     const long long tiles = (rows + 15) / 16;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + wib; t < tiles; t += nw) {
-        for (int e = lane; e < 16 * P.D0; e += 32) {
-            long long r = t * 16 + e / P.D0;
-            Xs[e] = __float2bfloat16_rn(r < rows ? X[r * P.D0 + e % P.D0] : 0.0f);
+    for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + wib; tile < tiles; tile += nw) {
+        for (int e = lane; e < 16 * D0; e += 32) {
+            const long long r = tile * 16 + e / D0;
+            Xs[(e / D0) * ldx + e % D0] = __float2bfloat16_rn(r < rows ? X[r * D0 + e % D0] : 0.0f);
         }
         __syncwarp();
-        mlp_tile_forward(P, Xs, H1, H2, st, Yf, P.O);
-        for (int e = lane; e < 16 * P.O; e += 32) {
-            long long r = t * 16 + e / P.O;
-            if (r < rows) Y[r * P.O + e % P.O] = Yf[e];
+        unsigned A2[kMlpHidden / 16][4];
+        mlp_fused_hidden<KT1, false>(P, Xs, MlpKeep{A2});
+        for (int p = 0; p < O / 16; ++p) {
+            float c0[4], c1[4];
+            mlp_tile_cols<kMlpHidden / 16>(A2, P.W3t, kMlpHidden + 8, p, c0, c1);
+            const long long r0 = tile * 16 + g, r1 = r0 + 8;
+            const int ca = 16 * p + 2 * t, cb = ca + 8;
+            if (r0 < rows) {
+                Y[r0 * O + ca] = c0[0] + P.b3[ca];
+                Y[r0 * O + ca + 1] = c0[1] + P.b3[ca + 1];
+                Y[r0 * O + cb] = c1[0] + P.b3[cb];
+                Y[r0 * O + cb + 1] = c1[1] + P.b3[cb + 1];
+            }
+            if (r1 < rows) {
+                Y[r1 * O + ca] = c0[2] + P.b3[ca];
+                Y[r1 * O + ca + 1] = c0[3] + P.b3[ca + 1];
+                Y[r1 * O + cb] = c1[2] + P.b3[cb];
+                Y[r1 * O + cb + 1] = c1[3] + P.b3[cb + 1];
+            }
         }
         __syncwarp();
     }
@@ -290,7 +347,6 @@ static int grad_blocks_and_smem(const pfsp_mlp *M, int warps, size_t *smem) {
     GradSmem L = grad_smem(M->D0, M->H, M->O);
     *smem = (size_t)L.total * warps;
     cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -307,6 +363,25 @@ static uint64_t splitmix(uint64_t &s) {
 }  // namespace pfsp
 
 using namespace pfsp;
+
+namespace pfsp {
+
+template <int KT1>
+static cudaError_t forward_t(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
+                             float *Y) {
+    const int warps = 4;
+    const size_t smem = (size_t)img_bytes + warps * mlp_scratch_bytes(16 * KT1);
+    void (*kern)(const unsigned char *, int, int, const float *, long long, float *) = mlp_forward_kernel<KT1>;
+    cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    kern<<<nsm, warps * 32, smem>>>(img, img_bytes, O, X, rows, Y);
+    return cudaGetLastError();
+}
+
+}  // namespace pfsp
 
 extern "C" {
 
@@ -409,18 +484,25 @@ int pfsp_mlp_forward(const pfsp_mlp *M, int64_t rows, const float *X, float *Y) 
     if (!M || (rows > 0 && (!X || !Y)) || rows < 0) return set_error(PFSP_ERR_INVALID, "bad argument");
     if (rows == 0) return PFSP_OK;
     float *dX = nullptr, *dY = nullptr;
+    unsigned char *img = nullptr;
+    const int img_bytes = mlp_image_bytes(M->D0, M->O);
     cudaError_t e = cudaMalloc(&dX, rows * M->D0 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dY, rows * M->O * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&img, img_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(dX, X, rows * M->D0 * 4, cudaMemcpyHostToDevice);
-    size_t smem = 0;
-    int nsm = grad_blocks_and_smem(M, 4, &smem);
+    if (e == cudaSuccess) e = mlp_build_image(M, M->O, img, 0);
     if (e == cudaSuccess) {
-        mlp_forward_kernel<<<nsm * 2, 128, smem>>>(mlp_view(M), dX, rows, dY);
-        e = cudaGetLastError();
+        switch (M->D0 / 16) {
+            case 1: e = pfsp::forward_t<1>(img, img_bytes, M->O, dX, rows, dY); break;
+            case 2: e = pfsp::forward_t<2>(img, img_bytes, M->O, dX, rows, dY); break;
+            case 3: e = pfsp::forward_t<3>(img, img_bytes, M->O, dX, rows, dY); break;
+            default: e = pfsp::forward_t<4>(img, img_bytes, M->O, dX, rows, dY); break;
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpy(Y, dY, rows * M->O * 4, cudaMemcpyDeviceToHost);
     cudaFree(dX);
     cudaFree(dY);
+    cudaFree(img);
     return e == cudaSuccess ? PFSP_OK : set_error(PFSP_ERR_CUDA, "pfsp_mlp_forward: %s", cudaGetErrorString(e));
 }
 

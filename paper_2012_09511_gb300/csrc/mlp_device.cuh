@@ -60,38 +60,175 @@ __device__ inline void mlp_tile_forward(const MlpDev &P, const __nv_bfloat16 *Xs
     mlp_dense_tile<false>(H2s, P.H, P.W3, P.b3, P.O, nullptr, Y, ldy, st);
 }
 
-// Per-warp scratch of in-solver inference: Xs [16][D0] bf16, H1s and H2s
-// [16][H] bf16, a 16x16 fp32 staging tile (byte offsets, 32-byte aligned).
-__host__ __device__ inline int mlp_scratch_bytes(int D0) { return 32 * D0 + 4 * 16 * kMlpHidden + 1024; }
+// ---- fused inference: the three layers of a 16-row tile in registers --------
+// mma.sync m16n8k16 (bf16 in, fp32 accumulate): the accumulator fragment of
+// output columns 16p..16p+15 (n-tiles 2p and 2p+1) holds, per thread, exactly
+// the elements of the next layer's A fragment for k-tile p (rows g and g + 8,
+// columns 2t, 2t + 1 and 8 + 2t, 9 + 2t, g = lane / 4, t = lane % 4), so bias,
+// ReLU and the bf16 rounding are applied in registers and no activation goes
+// through memory.  B fragments come from the staged image by ldmatrix.
+//
+// The image (one CTA's copy in shared memory, built by mlp_build_image):
+// W1t [H][D0 + 8], W2t [H][H + 8], W3t [O3][H + 8] bf16, transposed ([out][in])
+// with rows padded by 8 elements so that the eight 16-byte rows one ldmatrix
+// matrix reads start on distinct banks; then b1 [H], b2 [H], b3 [O3] fp32.
+// O3 (a multiple of 16) output columns are staged: 16 when only the
+// descend-first logit (column 0) is needed, O for the pair head too.
+struct MlpImage {
+    const __nv_bfloat16 *W1t, *W2t, *W3t;
+    const float *b1, *b2, *b3;
+    int D0, O3;
+};
 
-// Layers 1 and 2 of the 16-row tile in Xs; leaves H2s.
-__device__ inline void mlp_tile_hidden(const MlpDev &P, unsigned char *ms) {
-    __nv_bfloat16 *Xs = (__nv_bfloat16 *)ms;
-    __nv_bfloat16 *H1s = (__nv_bfloat16 *)(ms + 32 * P.D0);
-    __nv_bfloat16 *H2s = H1s + 16 * P.H;
-    float *st = (float *)(H2s + 16 * P.H);
-    mlp_dense_tile<true>(Xs, P.D0, P.W1, P.b1, P.H, H1s, nullptr, P.H, st);
-    mlp_dense_tile<true>(H1s, P.H, P.W2, P.b2, P.H, H2s, nullptr, P.H, st);
+__host__ __device__ inline int mlp_image_bytes(int D0, int O3) {
+    const int H = kMlpHidden;
+    return 2 * (H * (D0 + 8) + H * (H + 8) + O3 * (H + 8)) + 4 * (2 * H + O3);
 }
 
-// Logits of output columns j..j+15 (without bias) for the 16 rows, left in
-// the staging tile (row-major 16 x 16); returns the staging tile.
-__device__ inline float *mlp_tile_logits(const MlpDev &P, unsigned char *ms, int j) {
-    using namespace nvcuda;
-    __nv_bfloat16 *H2s = (__nv_bfloat16 *)(ms + 32 * P.D0) + 16 * P.H;
-    float *st = (float *)(H2s + 16 * P.H);
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
-    wmma::fill_fragment(acc, 0.0f);
-    for (int k = 0; k < P.H; k += 16) {
-        wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> fa;
-        wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> fb;
-        wmma::load_matrix_sync(fa, H2s + k, P.H);
-        wmma::load_matrix_sync(fb, P.W3 + (size_t)k * P.O + j, P.O);
-        wmma::mma_sync(acc, fa, fb, acc);
+__host__ __device__ inline MlpImage mlp_image_view(const void *base, int D0, int O3) {
+    const int H = kMlpHidden;
+    MlpImage P;
+    P.D0 = D0;
+    P.O3 = O3;
+    P.W1t = reinterpret_cast<const __nv_bfloat16 *>(base);
+    P.W2t = P.W1t + H * (D0 + 8);
+    P.W3t = P.W2t + H * (H + 8);
+    P.b1 = reinterpret_cast<const float *>(P.W3t + O3 * (H + 8));
+    P.b2 = P.b1 + H;
+    P.b3 = P.b2 + H;
+    return P;
+}
+
+// Per-warp scratch of fused inference: the input tile Xs [16][D0 + 8] bf16,
+// then the parked layer-2 tile H2 [16][H + 8] bf16 (pair head only).
+__host__ __device__ inline int mlp_scratch_bytes(int D0) { return 32 * (D0 + 8) + 32 * (kMlpHidden + 8); }
+
+__device__ __forceinline__ unsigned mlp_pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+__device__ __forceinline__ void mlp_mma(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mlp_ldsm4(unsigned (&r)[4], const __nv_bfloat16 *row) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// Raw logits (no bias) of output columns 16p..16p+15: c0 holds columns
+// 16p + 2t, +1 and c1 columns 16p + 8 + 2t, +1, of rows g ([0], [1]) and
+// g + 8 ([2], [3]).  Wt: [N][ldw] transposed weights, A: KT k-tiles of input.
+template <int KT>
+__device__ __forceinline__ void mlp_tile_cols(const unsigned (&A)[KT][4], const __nv_bfloat16 *Wt, int ldw, int p,
+                                              float (&c0)[4], float (&c1)[4]) {
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    const __nv_bfloat16 *w = Wt + (16 * p + 8 * (q >> 1) + r) * ldw + 8 * (q & 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c0[i] = c1[i] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < KT; ++kk) {
+        unsigned b[4];
+        mlp_ldsm4(b, w + 16 * kk);
+        mlp_mma(c0, A[kk], b[0], b[1]);
+        mlp_mma(c1, A[kk], b[2], b[3]);
     }
-    wmma::store_matrix_sync(st, acc, 16, wmma::mem_row_major);
-    __syncwarp();
-    return st;
+}
+
+// One hidden layer: relu(A W + b) rounded to bf16.  Output k-tile p (the
+// A fragment of the next layer for its columns 16p..16p+15) is handed to
+// sink(p, frag) as soon as it is computed (p is a compile-time constant after
+// unrolling), so a caller need not hold all of them.  ROLL keeps the loop
+// over p rolled (fewer live registers) for sinks that use p in addresses only.
+template <int KT, bool ROLL, class Sink>
+__device__ __forceinline__ void mlp_layer_relu(const unsigned (&A)[KT][4], const __nv_bfloat16 *Wt, int ldw,
+                                               const float *b, Sink &&sink) {
+    const int t = threadIdx.x & 3;
+#pragma unroll(ROLL ? 1 : kMlpHidden / 16)
+    for (int p = 0; p < kMlpHidden / 16; ++p) {
+        float c0[4], c1[4];
+        mlp_tile_cols<KT>(A, Wt, ldw, p, c0, c1);
+        const float2 e0 = *reinterpret_cast<const float2 *>(b + 16 * p + 2 * t);
+        const float2 e1 = *reinterpret_cast<const float2 *>(b + 16 * p + 8 + 2 * t);
+        unsigned o[4];
+        o[0] = mlp_pack_bf16(fmaxf(c0[0] + e0.x, 0.0f), fmaxf(c0[1] + e0.y, 0.0f));
+        o[1] = mlp_pack_bf16(fmaxf(c0[2] + e0.x, 0.0f), fmaxf(c0[3] + e0.y, 0.0f));
+        o[2] = mlp_pack_bf16(fmaxf(c1[0] + e1.x, 0.0f), fmaxf(c1[1] + e1.y, 0.0f));
+        o[3] = mlp_pack_bf16(fmaxf(c1[2] + e1.x, 0.0f), fmaxf(c1[3] + e1.y, 0.0f));
+        sink(p, o);
+    }
+}
+
+// Layers 1 and 2 of the tile Xs ([16][D0 + 8] bf16, shared memory, KT1 =
+// D0 / 16); layer 2's activations go to sink(p, frag) k-tile by k-tile
+// (ROLL: the sink uses p in addresses only).
+template <int KT1, bool ROLL, class Sink>
+__device__ __forceinline__ void mlp_fused_hidden(const MlpImage &P, const __nv_bfloat16 *Xs, Sink &&sink) {
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    const int ldx = 16 * KT1 + 8;
+    unsigned A0[KT1][4];
+#pragma unroll
+    for (int kk = 0; kk < KT1; ++kk) mlp_ldsm4(A0[kk], Xs + (r + 8 * (q & 1)) * ldx + 16 * kk + 8 * (q >> 1));
+    unsigned A1[kMlpHidden / 16][4];
+    mlp_layer_relu<KT1, false>(A0, P.W1t, ldx, P.b1, [&](int p, const unsigned (&o)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) A1[p][i] = o[i];
+    });
+    mlp_layer_relu<kMlpHidden / 16, ROLL>(A1, P.W2t, kMlpHidden + 8, P.b2, sink);
+}
+
+// A sink that keeps layer 2's activations in registers (A2) for a later
+// full layer 3.
+struct MlpKeep {
+    unsigned (&A2)[kMlpHidden / 16][4];
+    __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) A2[p][i] = o[i];
+    }
+};
+
+// A sink that runs layer 3 for output columns 0..7 on the fly: acc holds the
+// raw logits of column 2t, 2t + 1 of rows g ([0], [1]) and g + 8 ([2], [3]).
+struct MlpFirstCols {
+    const __nv_bfloat16 *W3t;
+    float (&acc)[4];
+    __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
+        const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+        unsigned b[4];
+        mlp_ldsm4(b, W3t + (8 * (q >> 1) + r) * (kMlpHidden + 8) + 16 * p + 8 * (q & 1));
+        mlp_mma(acc, o, b[0], b[1]);
+    }
+};
+
+// A sink that parks layer 2's activations in a shared-memory tile
+// H2 [16][H + 8] bf16 (row-major, the layout ldmatrix reads back).
+struct MlpPark {
+    __nv_bfloat16 *H2;
+    __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
+        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+        const int ld = kMlpHidden + 8;
+        unsigned *r0 = reinterpret_cast<unsigned *>(H2 + g * ld + 16 * p + 2 * t);
+        unsigned *r1 = reinterpret_cast<unsigned *>(H2 + (g + 8) * ld + 16 * p + 2 * t);
+        r0[0] = o[0];
+        r1[0] = o[1];
+        r0[4] = o[2];  // columns + 8
+        r1[4] = o[3];
+    }
+};
+
+// Layer 2's activations back from a parked tile as A fragments.
+__device__ __forceinline__ void mlp_unpark(const __nv_bfloat16 *H2, unsigned (&A2)[kMlpHidden / 16][4]) {
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    const int ld = kMlpHidden + 8;
+#pragma unroll
+    for (int kk = 0; kk < kMlpHidden / 16; ++kk) mlp_ldsm4(A2[kk], H2 + (r + 8 * (q & 1)) * ld + 16 * kk + 8 * (q >> 1));
 }
 
 }  // namespace pfsp

@@ -66,6 +66,9 @@ int set_error(int code, const char *fmt, ...);
 struct MlpDev;
 // The network's device view and dimensions (mlp.cu).
 MlpDev mlp_view(const pfsp_mlp *M);
+// Writes the network's inference image of O3 output columns (layout in
+// mlp_device.cuh) to the device buffer dst, on stream st.
+cudaError_t mlp_build_image(const pfsp_mlp *M, int O3, void *dst, cudaStream_t st);
 int mlp_dims(const pfsp_mlp *M, int *m, int *D0, int *O);
 
 // Host-side builders shared by the entry points (capi.cu, solve_capi.cu).

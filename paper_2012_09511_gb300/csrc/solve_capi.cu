@@ -140,9 +140,14 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.capped = opt->branching == PFSP_MINMIN_CAPPED;
     a.cap = ub0;
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
+    // the network's inference image: every output column when it orders the
+    // LB2 slots, else only the descend-first column (one 16-column tile)
+    const int net_O3 = use_net ? ((opt->learned & PFSP_LEARN_PAIR_ORDER) ? net_O : 16) : 0;
+    const int img_bytes = use_net ? mlp_image_bytes(net_D0, net_O3) : 0;
     if (use_net) {
         a.warp_words += mlp_scratch_place(n, m, opt->bound, net_D0, &a.mlp_off);
-        a.mlp = mlp_view(opt->mlp);
+        a.net_D0 = net_D0;
+        a.net_O3 = net_O3;
         long long tot = 0;
         for (int j = 0; j < n * m; ++j) tot += inst->p_host[j];
         a.inv_scale = tot > 0 ? (float)m / (float)tot : 1.0f;
@@ -159,22 +164,14 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
-    long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
+    const int max_warps = use_net ? kSolveWarpsLearned : kSolveWarps;
+    int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, max_warps) : max_warps;
     if (use_net) {
-        // stage the network's weights in shared memory when that costs no
-        // explorer, or when the network runs on most levels (every node then
-        // pays the weights' latency); otherwise it is read from L2
-        const int staged = mlp_staged_words(net_D0, net_O);
-        const long long fit_staged =
-            ((long long)optin - 256 - (long long)(a.net_base + staged) * 4) / ((long long)per_warp * 4);
-        const long long want = std::min<long long>(warps, fit);
-        if (fit_staged >= want || a.learn_depth > n / 2) {
-            a.net_words = staged;
-            a.warp_base = a.net_base + staged;
-            fit = fit_staged;
-        }
+        // the image is always staged in shared memory (ldmatrix reads it there)
+        a.net_words = img_bytes / 4;
+        a.warp_base = a.net_base + a.net_words;
     }
+    long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
     size_t smem = (size_t)(a.warp_base + warps * per_warp) * 4;
@@ -228,6 +225,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const int64_t tcap = tr ? tr->capacity : 0;
     const size_t o_tp = take((size_t)tcap * n), o_t1 = take((size_t)tcap), o_t2 = take((size_t)tcap),
                  o_tc = take(8);
+    const size_t o_img = take((size_t)img_bytes);
     DeviceSolveState D;
     cudaError_t e = cudaMalloc(&D.blob, off);
     if (e != cudaSuccess) {
@@ -250,6 +248,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.stop = sc + 2;
     a.err = sc + 3;
     a.best_key = (unsigned long long *)(sc + 4);
+    if (use_net) a.net_image = (const unsigned char *)(b + o_img);
     a.node_limit = opt->node_limit;
     a.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
     a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
@@ -272,6 +271,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     e = cudaMemsetAsync(a.mailbox, 0xff, (size_t)K * 8, st);
+    if (e == cudaSuccess && use_net) e = mlp_build_image(opt->mlp, net_O3, (void *)a.net_image, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);

@@ -9,6 +9,7 @@
 namespace pfsp {
 
 constexpr int kSolveWarps = 12;          // explorers (warps) per CTA at most
+constexpr int kSolveWarpsLearned = 8;    // with the ordering network: 2 per scheduler, 255 registers each
 constexpr int kPrunedLB = 0x7fffffff;     // bound stored for a pruned cell
 constexpr int kWaitLimit = 1 << 21;       // polls of a thief waiting for an answer
 constexpr int kErrStealWait = 1;          // error detail: a steal answer never came
@@ -63,20 +64,19 @@ struct SolveArgs {
     int trace_stride;
     // learned ordering (PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0: off)
     int learned;
-    MlpDev mlp;           // network in global memory (staged into shared memory by the kernel)
+    const unsigned char *net_image;  // the network's inference image in global memory (mlp_device.cuh)
+    int net_D0, net_O3;   // its input width and staged output columns
     float inv_scale;      // 1 / (mean machine load) for the network's features
     int mlp_off;          // word offset of the network's scratch from the warp's base
     int learn_depth;      // rows of level < learn_depth are ordered by the network
-    int net_base;         // word offset of the staged network in shared memory
-    int net_words;        // words of the staged network (0: not staged)
+    int net_base;         // word offset of the staged image in shared memory
+    int net_words;        // words of the staged image (0: no network)
 };
 
 int solve_warp_words(int n, int m, int bound);
 // Network scratch placement for a learned solve: sets *off (words from the
 // warp base) and returns the extra words to add to the per-warp stride.
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off);
-// Words of the network staged in shared memory (bf16 weights + fp32 biases).
-int mlp_staged_words(int D0, int O);
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 

@@ -32,8 +32,8 @@
 
 namespace pfsp {
 
-template <int NW, int MT>
-__global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a) {
+template <int NW, int MT, bool LEARNED>
+__global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) * 32, 1) solve_kernel(SolveArgs a) {
     extern __shared__ __align__(128) int smem[];
     __shared__ uint64_t bar;
     stage_tables(smem, a.tab, a.tab_words, &bar);
@@ -50,30 +50,11 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
     WarpScratch W = carve_warp(wbase, a.n, a.m);
     ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
     const int me = blockIdx.x * warps + wib;
-    // the ordering network, copied once per CTA into shared memory
-    __shared__ MlpDev net;
-    if (a.net_words) {
-        const MlpDev &G = a.mlp;
-        const int nw = (G.D0 * G.H + G.H * G.H + G.H * G.O) / 2;  // bf16 weights, W1 | W2 | W3 contiguous
-        int *dst = smem + a.net_base;
-        const int *src = reinterpret_cast<const int *>(G.W1);
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
-        float *fb = reinterpret_cast<float *>(dst + nw);
-        for (int i = threadIdx.x; i < G.H; i += blockDim.x) {
-            fb[i] = G.b1[i];
-            fb[G.H + i] = G.b2[i];
-        }
-        for (int i = threadIdx.x; i < G.O; i += blockDim.x) fb[2 * G.H + i] = G.b3[i];
-        if (threadIdx.x == 0) {
-            net = G;
-            const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(dst);
-            net.W1 = wb;
-            net.W2 = wb + G.D0 * G.H;
-            net.W3 = wb + G.D0 * G.H + G.H * G.H;
-            net.b1 = fb;
-            net.b2 = fb + G.H;
-            net.b3 = fb + 2 * G.H;
-        }
+    // the ordering network's inference image, copied once per CTA
+    __shared__ MlpImage net;
+    if (LEARNED && a.net_words) {
+        stage_tables(smem + a.net_base, reinterpret_cast<const int32_t *>(a.net_image), a.net_words, &bar);
+        if (threadIdx.x == 0) net = mlp_image_view(smem + a.net_base, a.net_D0, a.net_O3);
         __syncthreads();
     }
     if (me >= a.K) return;
@@ -87,17 +68,13 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_kernel(SolveArgs a)
         X.seq = 0;
     }
     __syncwarp();
-    run_explorer<NW, MT>(a, T, W, X, me, a.net_words ? &net : (a.learned & 3) ? &a.mlp : nullptr);
+    run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_words ? &net : nullptr);
 }
 
 int solve_warp_words(int n, int m, int bound) {
     return warp_words(n, m, n > 32, bound == PFSP_LB2 && m >= 2) + kExplorerWords;
 }
 
-int mlp_staged_words(int D0, int O) {
-    const int h = kMlpHidden;
-    return ((D0 * h + h * h + h * O) / 2 + 2 * h + O + 7) & ~7;
-}
 
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
     const int need = (mlp_scratch_bytes(D0) + 3) / 4;
@@ -116,40 +93,46 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
     return *off + need - bw;
 }
 
-template <int NW, int MT>
+template <int NW, int MT, bool LEARNED>
 static cudaError_t launch_solve_t(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    auto kern = solve_kernel<NW, MT>;
+    auto kern = solve_kernel<NW, MT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(warps * 32), args, smem, st);
 }
 
-template <int NW, int MT>
+template <int NW, int MT, bool LEARNED>
 static int occupancy_t(int warps, size_t smem) {
-    auto kern = solve_kernel<NW, MT>;
+    auto kern = solve_kernel<NW, MT, LEARNED>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem) != cudaSuccess) return 0;
     return per_sm;
 }
 
-#define PFSP_DISPATCH(NWV, FN, ...)                                       \
+#define PFSP_DISPATCH(NWV, LV, FN, ...)                                   \
     switch (a.m) {                                                         \
-        case 5: return FN<NWV, 5>(__VA_ARGS__);                            \
-        case 10: return FN<NWV, 10>(__VA_ARGS__);                          \
-        case 20: return FN<NWV, 20>(__VA_ARGS__);                          \
-        default: return FN<NWV, 0>(__VA_ARGS__);                           \
+        case 5: return FN<NWV, 5, LV>(__VA_ARGS__);                        \
+        case 10: return FN<NWV, 10, LV>(__VA_ARGS__);                      \
+        case 20: return FN<NWV, 20, LV>(__VA_ARGS__);                      \
+        default: return FN<NWV, 0, LV>(__VA_ARGS__);                       \
     }
 
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
-    if (a.n <= 32) { PFSP_DISPATCH(1, occupancy_t, warps, smem) }
-    PFSP_DISPATCH(2, occupancy_t, warps, smem)
+    const bool learned = a.net_words > 0;
+    if (a.n <= 32 && learned) { PFSP_DISPATCH(1, true, occupancy_t, warps, smem) }
+    if (a.n <= 32) { PFSP_DISPATCH(1, false, occupancy_t, warps, smem) }
+    if (learned) { PFSP_DISPATCH(2, true, occupancy_t, warps, smem) }
+    PFSP_DISPATCH(2, false, occupancy_t, warps, smem)
 }
 
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    if (a.n <= 32) { PFSP_DISPATCH(1, launch_solve_t, a, blocks, warps, smem, st) }
-    PFSP_DISPATCH(2, launch_solve_t, a, blocks, warps, smem, st)
+    const bool learned = a.net_words > 0;
+    if (a.n <= 32 && learned) { PFSP_DISPATCH(1, true, launch_solve_t, a, blocks, warps, smem, st) }
+    if (a.n <= 32) { PFSP_DISPATCH(1, false, launch_solve_t, a, blocks, warps, smem, st) }
+    if (learned) { PFSP_DISPATCH(2, true, launch_solve_t, a, blocks, warps, smem, st) }
+    PFSP_DISPATCH(2, false, launch_solve_t, a, blocks, warps, smem, st)
 }
 
 }  // namespace pfsp
