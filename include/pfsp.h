@@ -131,8 +131,7 @@ typedef struct {
  *                on min(bound, c) with c the solve's initial incumbent (a
  *                constant, so that every node's decision is fixed for the run).
  *   warps_per_sm explorers per SM; 0 = as many as fit in shared memory (at
- *                most 12; 8 when the ordering network runs, whose kernel
- *                keeps its activations in registers).
+ *                most 12).
  *   check_every  iterations between limit checks and length publications
  *                (rounded up to a power of two); 0 = default (16).
  *   min_steal    smallest remaining interval (in leaves) a victim splits;

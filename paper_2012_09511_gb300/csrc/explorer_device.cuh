@@ -167,16 +167,16 @@ struct Explorer {
     // Layers 1 and 2 of the network on the tile Xs (fused, in registers),
     // layer 2's activations handed to sink k-tile by k-tile.
     template <class Sink>
-    __device__ void net_hidden(const __nv_bfloat16 *Xs, Sink &&sink) const {
+    __device__ void net_hidden(const __nv_bfloat16 *Xs, __nv_bfloat16 *H1, Sink &&sink) const {
         constexpr int KT = MT ? (3 * MT + 15) / 16 : 0;
         if constexpr (KT > 0) {
-            mlp_fused_hidden<KT, true>(*net, Xs, sink);
+            mlp_fused_hidden<KT>(*net, Xs, H1, sink);
         } else {
             switch (net->D0 >> 4) {
-                case 1: mlp_fused_hidden<1, true>(*net, Xs, sink); break;
-                case 2: mlp_fused_hidden<2, true>(*net, Xs, sink); break;
-                case 3: mlp_fused_hidden<3, true>(*net, Xs, sink); break;
-                default: mlp_fused_hidden<4, true>(*net, Xs, sink); break;
+                case 1: mlp_fused_hidden<1>(*net, Xs, H1, sink); break;
+                case 2: mlp_fused_hidden<2>(*net, Xs, H1, sink); break;
+                case 3: mlp_fused_hidden<3>(*net, Xs, H1, sink); break;
+                default: mlp_fused_hidden<4>(*net, Xs, H1, sink); break;
             }
         }
     }
@@ -198,11 +198,8 @@ struct Explorer {
         }
         if (lane < 16) X.sscore[lane] = 0.0f;
         __syncwarp();
-        __nv_bfloat16 *H2 = Xs + 16 * ldx;
-        net_hidden(Xs, MlpPark{H2});
-        __syncwarp();
-        unsigned A2[kMlpHidden / 16][4];
-        mlp_unpark(H2, A2);
+        __nv_bfloat16 *H1 = Xs + 16 * ldx, *H2 = H1 + 16 * (kMlpHidden + 8);
+        net_hidden(Xs, H1, MlpPark{H2});
         // row 0 (the parent) sits in lanes 0..3: columns 16p + 2t (+1) and 16p + 8 + 2t (+1)
         const int npairs = m * (m - 1) / 2;
         const int t = lane & 3;
@@ -211,7 +208,7 @@ struct Explorer {
         for (int s2 = 0; s2 < kMaxSlots; ++s2) part[s2] = 0.0f;
         for (int p = 0; p < P.O3 / 16; ++p) {
             float c0[4], c1[4];
-            mlp_tile_cols<kMlpHidden / 16>(A2, P.W3t, kMlpHidden + 8, p, c0, c1);
+            mlp_tile_cols<kMlpHidden / 16>(H2, kMlpHidden + 8, P.W3t, kMlpHidden + 8, p, c0, c1);
             if (lane < 4) {
                 const int cols[4] = {16 * p + 2 * t, 16 * p + 2 * t + 1, 16 * p + 8 + 2 * t, 16 * p + 9 + 2 * t};
                 const float z[4] = {c0[0], c0[1], c1[0], c1[1]};
@@ -288,7 +285,7 @@ struct Explorer {
             }
             __syncwarp();
             float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            net_hidden(Xs, MlpFirstCols{P.W3t, c0});
+            net_hidden(Xs, Xs + 16 * ldx, MlpFirstCols{P.W3t, c0});
             // column 0 of rows g and g + 8 sits in lane 4g
             if ((lane & 3) == 0) {
                 const int g = lane >> 2;

@@ -143,11 +143,11 @@ __global__ void mlp_forward_kernel(const unsigned char *img, int img_bytes, int 
             Xs[(e / D0) * ldx + e % D0] = __float2bfloat16_rn(r < rows ? X[r * D0 + e % D0] : 0.0f);
         }
         __syncwarp();
-        unsigned A2[kMlpHidden / 16][4];
-        mlp_fused_hidden<KT1, false>(P, Xs, MlpKeep{A2});
+        __nv_bfloat16 *H1 = Xs + 16 * ldx, *H2 = H1 + 16 * (kMlpHidden + 8);
+        mlp_fused_hidden<KT1>(P, Xs, H1, MlpPark{H2});
         for (int p = 0; p < O / 16; ++p) {
             float c0[4], c1[4];
-            mlp_tile_cols<kMlpHidden / 16>(A2, P.W3t, kMlpHidden + 8, p, c0, c1);
+            mlp_tile_cols<kMlpHidden / 16>(H2, kMlpHidden + 8, P.W3t, kMlpHidden + 8, p, c0, c1);
             const long long r0 = tile * 16 + g, r1 = r0 + 8;
             const int ca = 16 * p + 2 * t, cb = ca + 8;
             if (r0 < rows) {

@@ -99,9 +99,10 @@ __host__ __device__ inline MlpImage mlp_image_view(const void *base, int D0, int
     return P;
 }
 
-// Per-warp scratch of fused inference: the input tile Xs [16][D0 + 8] bf16,
-// then the parked layer-2 tile H2 [16][H + 8] bf16 (pair head only).
-__host__ __device__ inline int mlp_scratch_bytes(int D0) { return 32 * (D0 + 8) + 32 * (kMlpHidden + 8); }
+// Per-warp scratch of fused inference, bf16 tiles of 16 rows: the input Xs
+// [16][D0 + 8], layer 1's activations H1 [16][H + 8] and layer 2's H2
+// [16][H + 8] (kept only for the pair head).
+__host__ __device__ inline int mlp_scratch_bytes(int D0) { return 32 * (D0 + 8) + 64 * (kMlpHidden + 8); }
 
 __device__ __forceinline__ unsigned mlp_pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -123,38 +124,41 @@ __device__ __forceinline__ void mlp_ldsm4(unsigned (&r)[4], const __nv_bfloat16 
                  : "r"(addr));
 }
 
-// Raw logits (no bias) of output columns 16p..16p+15: c0 holds columns
-// 16p + 2t, +1 and c1 columns 16p + 8 + 2t, +1, of rows g ([0], [1]) and
-// g + 8 ([2], [3]).  Wt: [N][ldw] transposed weights, A: KT k-tiles of input.
+// Raw products (no bias) for output columns 16p..16p+15 of a 16-row tile
+// whose KT k-tiles of input come from the shared tile As ([16][lda] bf16,
+// one ldmatrix per k-tile): c0 holds columns 16p + 2t, +1 and c1 columns
+// 16p + 8 + 2t, +1, of rows g ([0], [1]) and g + 8 ([2], [3]).
+// Wt: [N][ldw] transposed weights.
 template <int KT>
-__device__ __forceinline__ void mlp_tile_cols(const unsigned (&A)[KT][4], const __nv_bfloat16 *Wt, int ldw, int p,
-                                              float (&c0)[4], float (&c1)[4]) {
+__device__ __forceinline__ void mlp_tile_cols(const __nv_bfloat16 *As, int lda, const __nv_bfloat16 *Wt, int ldw,
+                                              int p, float (&c0)[4], float (&c1)[4]) {
     const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    const __nv_bfloat16 *x = As + (r + 8 * (q & 1)) * lda + 8 * (q >> 1);
     const __nv_bfloat16 *w = Wt + (16 * p + 8 * (q >> 1) + r) * ldw + 8 * (q & 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) c0[i] = c1[i] = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < KT; ++kk) {
-        unsigned b[4];
+        unsigned av[4], b[4];
+        mlp_ldsm4(av, x + 16 * kk);
         mlp_ldsm4(b, w + 16 * kk);
-        mlp_mma(c0, A[kk], b[0], b[1]);
-        mlp_mma(c1, A[kk], b[2], b[3]);
+        mlp_mma(c0, av, b[0], b[1]);
+        mlp_mma(c1, av, b[2], b[3]);
     }
 }
 
-// One hidden layer: relu(A W + b) rounded to bf16.  Output k-tile p (the
-// A fragment of the next layer for its columns 16p..16p+15) is handed to
-// sink(p, frag) as soon as it is computed (p is a compile-time constant after
-// unrolling), so a caller need not hold all of them.  ROLL keeps the loop
-// over p rolled (fewer live registers) for sinks that use p in addresses only.
-template <int KT, bool ROLL, class Sink>
-__device__ __forceinline__ void mlp_layer_relu(const unsigned (&A)[KT][4], const __nv_bfloat16 *Wt, int ldw,
+// One hidden layer on a shared input tile: relu(A W + b) rounded to bf16.
+// Output k-tile p (the next layer's A fragment for columns 16p..16p+15) goes
+// to sink(p, frag) as soon as it is computed; the loop over p stays rolled,
+// so only a few fragments are live at a time.
+template <int KT, class Sink>
+__device__ __forceinline__ void mlp_layer_relu(const __nv_bfloat16 *As, int lda, const __nv_bfloat16 *Wt, int ldw,
                                                const float *b, Sink &&sink) {
     const int t = threadIdx.x & 3;
-#pragma unroll(ROLL ? 1 : kMlpHidden / 16)
+#pragma unroll 1
     for (int p = 0; p < kMlpHidden / 16; ++p) {
         float c0[4], c1[4];
-        mlp_tile_cols<KT>(A, Wt, ldw, p, c0, c1);
+        mlp_tile_cols<KT>(As, lda, Wt, ldw, p, c0, c1);
         const float2 e0 = *reinterpret_cast<const float2 *>(b + 16 * p + 2 * t);
         const float2 e1 = *reinterpret_cast<const float2 *>(b + 16 * p + 8 + 2 * t);
         unsigned o[4];
@@ -166,36 +170,24 @@ __device__ __forceinline__ void mlp_layer_relu(const unsigned (&A)[KT][4], const
     }
 }
 
-// Layers 1 and 2 of the tile Xs ([16][D0 + 8] bf16, shared memory, KT1 =
-// D0 / 16); layer 2's activations go to sink(p, frag) k-tile by k-tile
-// (ROLL: the sink uses p in addresses only).
-template <int KT1, bool ROLL, class Sink>
-__device__ __forceinline__ void mlp_fused_hidden(const MlpImage &P, const __nv_bfloat16 *Xs, Sink &&sink) {
-    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
-    const int ldx = 16 * KT1 + 8;
-    unsigned A0[KT1][4];
-#pragma unroll
-    for (int kk = 0; kk < KT1; ++kk) mlp_ldsm4(A0[kk], Xs + (r + 8 * (q & 1)) * ldx + 16 * kk + 8 * (q >> 1));
-    unsigned A1[kMlpHidden / 16][4];
-    mlp_layer_relu<KT1, false>(A0, P.W1t, ldx, P.b1, [&](int p, const unsigned (&o)[4]) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) A1[p][i] = o[i];
-    });
-    mlp_layer_relu<kMlpHidden / 16, ROLL>(A1, P.W2t, kMlpHidden + 8, P.b2, sink);
-}
-
-// A sink that keeps layer 2's activations in registers (A2) for a later
-// full layer 3.
-struct MlpKeep {
-    unsigned (&A2)[kMlpHidden / 16][4];
+// A sink that parks a layer's activations in a shared tile [16][H + 8] bf16
+// (row-major, the layout ldmatrix reads back as A fragments).
+struct MlpPark {
+    __nv_bfloat16 *Hs;
     __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) A2[p][i] = o[i];
+        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+        const int ld = kMlpHidden + 8;
+        unsigned *r0 = reinterpret_cast<unsigned *>(Hs + g * ld + 16 * p + 2 * t);
+        unsigned *r1 = reinterpret_cast<unsigned *>(Hs + (g + 8) * ld + 16 * p + 2 * t);
+        r0[0] = o[0];
+        r1[0] = o[1];
+        r0[4] = o[2];  // columns + 8
+        r1[4] = o[3];
     }
 };
 
 // A sink that runs layer 3 for output columns 0..7 on the fly: acc holds the
-// raw logits of column 2t, 2t + 1 of rows g ([0], [1]) and g + 8 ([2], [3]).
+// raw logits of columns 2t, 2t + 1 of rows g ([0], [1]) and g + 8 ([2], [3]).
 struct MlpFirstCols {
     const __nv_bfloat16 *W3t;
     float (&acc)[4];
@@ -207,28 +199,15 @@ struct MlpFirstCols {
     }
 };
 
-// A sink that parks layer 2's activations in a shared-memory tile
-// H2 [16][H + 8] bf16 (row-major, the layout ldmatrix reads back).
-struct MlpPark {
-    __nv_bfloat16 *H2;
-    __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
-        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-        const int ld = kMlpHidden + 8;
-        unsigned *r0 = reinterpret_cast<unsigned *>(H2 + g * ld + 16 * p + 2 * t);
-        unsigned *r1 = reinterpret_cast<unsigned *>(H2 + (g + 8) * ld + 16 * p + 2 * t);
-        r0[0] = o[0];
-        r1[0] = o[1];
-        r0[4] = o[2];  // columns + 8
-        r1[4] = o[3];
-    }
-};
-
-// Layer 2's activations back from a parked tile as A fragments.
-__device__ __forceinline__ void mlp_unpark(const __nv_bfloat16 *H2, unsigned (&A2)[kMlpHidden / 16][4]) {
-    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
-    const int ld = kMlpHidden + 8;
-#pragma unroll
-    for (int kk = 0; kk < kMlpHidden / 16; ++kk) mlp_ldsm4(A2[kk], H2 + (r + 8 * (q & 1)) * ld + 16 * kk + 8 * (q >> 1));
+// Layers 1 and 2 of the tile Xs ([16][D0 + 8], KT1 = D0 / 16): layer 1's
+// activations are parked in H1, layer 2's handed to sink(p, frag).
+template <int KT1, class Sink>
+__device__ __forceinline__ void mlp_fused_hidden(const MlpImage &P, const __nv_bfloat16 *Xs, __nv_bfloat16 *H1,
+                                                 Sink &&sink) {
+    mlp_layer_relu<KT1>(Xs, 16 * KT1 + 8, P.W1t, 16 * KT1 + 8, P.b1, MlpPark{H1});
+    __syncwarp();
+    mlp_layer_relu<kMlpHidden / 16>(H1, kMlpHidden + 8, P.W2t, kMlpHidden + 8, P.b2, sink);
+    __syncwarp();
 }
 
 }  // namespace pfsp

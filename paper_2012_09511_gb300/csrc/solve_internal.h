@@ -9,7 +9,7 @@
 namespace pfsp {
 
 constexpr int kSolveWarps = 12;          // explorers (warps) per CTA at most
-constexpr int kSolveWarpsLearned = 8;    // with the ordering network: 2 per scheduler, 255 registers each
+constexpr int kSolveWarpsLearned = 12;   // with the ordering network (same as the plain solver)
 constexpr int kPrunedLB = 0x7fffffff;     // bound stored for a pruned cell
 constexpr int kWaitLimit = 1 << 21;       // polls of a thief waiting for an answer
 constexpr int kErrStealWait = 1;          // error detail: a steal answer never came
@@ -79,5 +79,8 @@ int solve_warp_words(int n, int m, int bound);
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off);
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+// The same for the kernels with the ordering network (solve_learned.cu).
+int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 
 }  // namespace pfsp

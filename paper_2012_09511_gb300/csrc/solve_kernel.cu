@@ -26,55 +26,13 @@
 // wait is bounded; on expiry the kernel records an error and stops.
 #include <cuda_runtime.h>
 
-#include <cfloat>
-
-#include "explorer_device.cuh"
+#include "solve_kernel.cuh"
 
 namespace pfsp {
-
-template <int NW, int MT, bool LEARNED>
-__global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) * 32, 1) solve_kernel(SolveArgs a) {
-    extern __shared__ __align__(128) int smem[];
-    __shared__ uint64_t bar;
-    stage_tables(smem, a.tab, a.tab_words, &bar);
-    SmemTables T;
-    T.pm = smem + a.off_pm;
-    T.tot = smem + a.off_tot;
-    T.kl = smem + a.off_kl;
-    T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
-    T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    int *wbase = smem + a.warp_base + wib * (a.warp_words + kExplorerWords);
-    WarpScratch W = carve_warp(wbase, a.n, a.m);
-    ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
-    const int me = blockIdx.x * warps + wib;
-    // the ordering network's inference image, copied once per CTA
-    __shared__ MlpImage net;
-    if (LEARNED && a.net_words) {
-        stage_tables(smem + a.net_base, reinterpret_cast<const int32_t *>(a.net_image), a.net_words, &bar);
-        if (threadIdx.x == 0) net = mlp_image_view(smem + a.net_base, a.net_D0, a.net_O3);
-        __syncthreads();
-    }
-    if (me >= a.K) return;
-
-    for (int i = lane; i < a.n; i += 32) {
-        X.D[i] = a.in_start[(size_t)me * 64 + i];
-        X.E[i] = a.in_end[(size_t)me * 65 + 1 + i];
-    }
-    if (lane == 0) {
-        X.etop = a.in_end[(size_t)me * 65];
-        X.seq = 0;
-    }
-    __syncwarp();
-    run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_words ? &net : nullptr);
-}
 
 int solve_warp_words(int n, int m, int bound) {
     return warp_words(n, m, n > 32, bound == PFSP_LB2 && m >= 2) + kExplorerWords;
 }
-
 
 int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
     const int need = (mlp_scratch_bytes(D0) + 3) / 4;
@@ -93,45 +51,15 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
     return *off + need - bw;
 }
 
-template <int NW, int MT, bool LEARNED>
-static cudaError_t launch_solve_t(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    auto kern = solve_kernel<NW, MT, LEARNED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&a};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(warps * 32), args, smem, st);
-}
-
-template <int NW, int MT, bool LEARNED>
-static int occupancy_t(int warps, size_t smem) {
-    auto kern = solve_kernel<NW, MT, LEARNED>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem) != cudaSuccess) return 0;
-    return per_sm;
-}
-
-#define PFSP_DISPATCH(NWV, LV, FN, ...)                                   \
-    switch (a.m) {                                                         \
-        case 5: return FN<NWV, 5, LV>(__VA_ARGS__);                        \
-        case 10: return FN<NWV, 10, LV>(__VA_ARGS__);                      \
-        case 20: return FN<NWV, 20, LV>(__VA_ARGS__);                      \
-        default: return FN<NWV, 0, LV>(__VA_ARGS__);                       \
-    }
-
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
-    const bool learned = a.net_words > 0;
-    if (a.n <= 32 && learned) { PFSP_DISPATCH(1, true, occupancy_t, warps, smem) }
+    if (a.net_words > 0) return solve_occupancy_learned(a, warps, smem);
     if (a.n <= 32) { PFSP_DISPATCH(1, false, occupancy_t, warps, smem) }
-    if (learned) { PFSP_DISPATCH(2, true, occupancy_t, warps, smem) }
     PFSP_DISPATCH(2, false, occupancy_t, warps, smem)
 }
 
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    const bool learned = a.net_words > 0;
-    if (a.n <= 32 && learned) { PFSP_DISPATCH(1, true, launch_solve_t, a, blocks, warps, smem, st) }
+    if (a.net_words > 0) return launch_solve_learned(a, blocks, warps, smem, st);
     if (a.n <= 32) { PFSP_DISPATCH(1, false, launch_solve_t, a, blocks, warps, smem, st) }
-    if (learned) { PFSP_DISPATCH(2, true, launch_solve_t, a, blocks, warps, smem, st) }
     PFSP_DISPATCH(2, false, launch_solve_t, a, blocks, warps, smem, st)
 }
 
