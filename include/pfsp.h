@@ -113,6 +113,13 @@ typedef struct {
     double kernel_seconds;     /* device time of the main kernel (CUDA events) */
     int32_t final_ub;          /* incumbent at the end of a solve */
     int32_t explorers;         /* explorers used by a solve */
+    /* pfsp_solve only (zero elsewhere): SM clock cycles spent by the explorers
+     * in each phase of their loop, summed over explorers: [0] limit checks and
+     * answering steal requests, [1] selecting the next node, [2] decoding it,
+     * [3] LB1 (wavefronts and children), [4] the LB2 sweep, [5] MinMin,
+     * pruning and the new row, [6] rebuilding the path to a stolen interval's
+     * start, [7] stealing and waiting without work. */
+    uint64_t phase_cycles[8];
 } pfsp_stats_t;
 
 /*
@@ -142,8 +149,14 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
 /* Learned-ordering flags (pfsp_options.learned; not in the paper). */
 #define PFSP_LEARN_CHILD_ORDER 1  /* order each new row by the network's descend-first logits */
 #define PFSP_LEARN_PAIR_ORDER 2   /* sweep LB2's 32-pair slots in the order of the network's pair logits */
-#define PFSP_EARLY_EXIT 4         /* stop the LB2 sweep once every child's bound reaches the cap
-                                     (requires PFSP_MINMIN_CAPPED; values stay exact once capped) */
+#define PFSP_EARLY_EXIT 4         /* skip or stop the LB2 sweep as soon as every child of one
+                                     direction has a bound (its LB1 or a pair term seen) at least the
+                                     solve's initial incumbent: such a node has no child below the
+                                     incumbent under either MinMin rule (the decided direction holds
+                                     no minimum below it, so MinMin picks it), hence the search tree
+                                     and every counter are those of the full sweep.  Best with the
+                                     pairs most likely to decide a child in the first slot
+                                     (pfsp_learn_pair_order). */
 
 typedef struct {
     int32_t init_ub;
@@ -211,6 +224,23 @@ int pfsp_solve_batch(const pfsp_instance *const *insts, int count, const pfsp_op
  */
 int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp_options *base, int sample,
                         pfsp_options *best);
+
+/*
+ * Order of the machine pairs in the LB2 sweep (not in the paper; LB2 of
+ * Section 2.4 is the maximum over all pairs, so no bound value depends on it).
+ * order[i] (i = 0 .. m(m-1)/2 - 1) is the index of the pair placed at sweep
+ * position i, pairs being indexed k = 0..m-2, l = k+1..m-1 (the network's
+ * column order); positions 0..31 form the first 32-pair slot, and so on.  The
+ * order matters only to PFSP_EARLY_EXIT, which can stop after a slot.  order
+ * NULL restores the index order.  The instance's device tables are rebuilt
+ * (the call synchronises the device first; no call using the instance may
+ * run meanwhile).
+ * Errors: PFSP_ERR_INVALID (NULL instance, order not a permutation),
+ * PFSP_ERR_CUDA.
+ */
+int pfsp_set_pair_order(pfsp_instance *inst, const int32_t *order);
+/* The instance's current pair order (m(m-1)/2 int32). */
+int pfsp_get_pair_order(const pfsp_instance *inst, int32_t *order);
 
 /* Counters of the last pfsp_bound_batch or pfsp_solve call on `inst`. */
 int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
@@ -293,6 +323,27 @@ int pfsp_mlp_train(pfsp_mlp *mlp, int64_t rows, const float *X, const float *T, 
  */
 int pfsp_mlp_rows(const pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
                   const uint8_t *d1, const uint8_t *d2, float *X, float *T, float *M);
+
+/*
+ * Per-pair scores of the ordering network over num_nodes nodes of `inst`
+ * (layout of pfsp_bound_batch), on the GPU: score[q] (q in the network's pair
+ * order, m(m-1)/2 floats) is the mean over the nodes of the network's
+ * probability that pair q gives the LB2 of a child, read from the parent
+ * row's features.  num_nodes >= 1.
+ */
+int pfsp_mlp_pair_scores(const pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
+                         const uint8_t *d1, const uint8_t *d2, float *score);
+
+/*
+ * Learned pair order (not in the paper): pfsp_mlp_pair_scores over the given
+ * nodes, pairs sorted by decreasing score (ties: lower index first), then
+ * pfsp_set_pair_order.  order (NULL or m(m-1)/2 int32) receives the order.
+ * The nodes are typically a short trace of the solver on this instance
+ * (pfsp_solve_trace), so that the first 32-pair slot holds the pairs that
+ * most often decide a child of the nodes the search visits.
+ */
+int pfsp_learn_pair_order(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
+                          const uint8_t *d1, const uint8_t *d2, int32_t *order);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);

@@ -395,7 +395,9 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
     const mask_t U = out.U;
     const int u = out.u;
     __syncwarp();
-    // children already decided by LB1 (only used with a cap)
+    const mask_t all = (u >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << u) - 1);
+    // children already decided by LB1 (only used with a cap); when every
+    // child of one direction is, the node is a dead end and no pair is needed
     mask_t done_f = 0, done_b = 0;
     if (cap != INT_MAX) {
 #pragma unroll
@@ -405,8 +407,8 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             done_f |= (mask_t)bf << (32 * h);
             done_b |= (mask_t)bb << (32 * h);
         }
+        if ((done_f & all) == all || (done_b & all) == all) return;
     }
-    const mask_t all = (u >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << u) - 1);
     int accf[REGACC ? NC : 1], accb[REGACC ? NC : 1];
     if constexpr (REGACC) {
 #pragma unroll
@@ -482,7 +484,8 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             }
         }
         if (cap != INT_MAX && si + 1 < S) {
-            // every child decided? (some pair term or its LB1 already >= cap)
+            // every child of one direction decided? (its LB1 or some pair
+            // term already >= cap)
             mask_t mf = 0, mb = 0;
             if constexpr (REGACC) {
 #pragma unroll
@@ -511,7 +514,7 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             }
             done_f |= mf;
             done_b |= mb;
-            if ((done_f & all) == all && (done_b & all) == all) break;
+            if ((done_f & all) == all || (done_b & all) == all) break;
         }
     }
     // ---- max over lanes (pairs) per child: transpose through padded rows ------
@@ -547,10 +550,13 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
 
 // LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
 // written by decompose_lb1.  `order` (may be NULL) gives the order in which
-// the slots are swept; with cap < INT_MAX the sweep stops after the first
-// slot at which every child's bound is known to be >= cap (its LB1 or one of
-// the pair terms already seen reaches cap): the children's values are then
-// lower bounds >= cap, exact once capped at cap.
+// the slots are swept.  With cap < INT_MAX the sweep stops (or is skipped)
+// as soon as every child of one direction is known to have a bound >= cap
+// (its LB1 or a pair term already seen reaches cap).  The values returned are
+// then lower bounds of the children's LB2 (each is the LB1 or the largest pair
+// term seen).  Such a node has no child below cap in either MinMin rule: the
+// decided direction holds no minimum below cap, so it is chosen whenever the
+// other holds one, and every child of both is >= cap otherwise.
 // WALK = 1: register walks (n <= kRegWalk, scratch carved with reg_walk);
 // WALK = 0: walks through shared memory (any n).  Fixed per kernel, so that
 // a kernel carries the register demand of one path only.

@@ -65,8 +65,11 @@ static std::vector<int> johnson_lag_order(int n, int m, const int32_t *p, int k,
     return ord;
 }
 
-void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob) {
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order) {
     const int n = L.n, m = L.m;
+    // slot position of every pair: pair_order[i] = the pair at position i
+    std::vector<int> where(L.P);
+    for (int i = 0; i < L.P; ++i) where[pair_order ? pair_order[i] : i] = i;
     blob.assign(L.words, 0);
     for (int k = 0; k < m; ++k)
         for (int j = 0; j < n; ++j) blob[L.off_pm + k * L.nj + j] = p[j * m + k];
@@ -87,8 +90,8 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
     std::vector<int> lag(n);
     for (int k = 0; k < m; ++k)
         for (int l = k + 1; l < m; ++l, ++q) {
-            const int s = q / 32, lane = q % 32;
-            blob[L.off_kl + q] = k | (l << 8);
+            const int s = where[q] / 32, lane = where[q] % 32;
+            blob[L.off_kl + where[q]] = k | (l << 8);
             for (int j = 0; j < n; ++j) {
                 int g = 0;
                 for (int r = k + 1; r < l; ++r) g += p[j * m + r];
@@ -175,7 +178,7 @@ int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out) {
     inst->lay = table_layout(n, m);
     inst->lb2_ok = (size_t)inst->lay.words * 4 <= (size_t)kMaxTableBytes;
     std::vector<int32_t> blob;
-    build_tables(inst->lay, p, blob);
+    build_tables(inst->lay, p, blob, nullptr);
     cudaError_t e = cudaMalloc(&inst->d_tab, blob.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -199,7 +202,43 @@ void pfsp_free_instance(pfsp_instance *inst) {
     if (inst->d_tab) cudaFree(inst->d_tab);
     if (inst->d_scratch) cudaFree(inst->d_scratch);
     free(inst->p_host);
+    free(inst->pair_order);
     free(inst);
+}
+
+int pfsp_set_pair_order(pfsp_instance *inst, const int32_t *order) {
+    g_err[0] = 0;
+    if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
+    const int P = inst->lay.P;
+    std::vector<int32_t> ord(P);
+    if (order) {
+        std::vector<char> seen(P, 0);
+        for (int i = 0; i < P; ++i) {
+            if (order[i] < 0 || order[i] >= P || seen[order[i]])
+                return set_error(PFSP_ERR_INVALID, "order is not a permutation of 0..%d (entry %d)", P - 1, i);
+            seen[order[i]] = 1;
+            ord[i] = order[i];
+        }
+    } else {
+        std::iota(ord.begin(), ord.end(), 0);
+    }
+    std::vector<int32_t> blob;
+    build_tables(inst->lay, inst->p_host, blob, ord.data());
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(inst->d_tab, blob.data(), blob.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of reordered instance tables");
+    if (P > 0 && !inst->pair_order) inst->pair_order = (int32_t *)malloc(sizeof(int32_t) * P);
+    if (P > 0 && !inst->pair_order) return set_error(PFSP_ERR_OOM, "host allocation failed");
+    if (P > 0) memcpy(inst->pair_order, ord.data(), sizeof(int32_t) * P);
+    return PFSP_OK;
+}
+
+int pfsp_get_pair_order(const pfsp_instance *inst, int32_t *order) {
+    g_err[0] = 0;
+    if (!inst || !order) return set_error(PFSP_ERR_INVALID, "NULL argument");
+    for (int i = 0; i < inst->lay.P; ++i) order[i] = inst->pair_order ? inst->pair_order[i] : i;
+    return PFSP_OK;
 }
 
 int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,

@@ -39,8 +39,10 @@ struct ExplorerSmem {
     float score[64];   // descend-first logits of the children being ordered
     float sscore[16];  // summed pair probabilities per LB2 slot
     int sorder[16];    // LB2 slot order of the current node
+    unsigned long long ph[kPhases];  // SM clock cycles spent in each phase (lane 0 updates)
 };
-constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 8 + 64 + 16 + 16);  // a multiple of 8 words
+constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 8 + 64 + 16 + 16 + 2 * kPhases);  // a multiple of 8 words
+static_assert(kExplorerWords % 8 == 0, "explorer scratch keeps 32-byte alignment");
 
 struct Stats {
     unsigned long long decomposed, bounded, leaves, pruned, steals, iters;
@@ -63,6 +65,7 @@ struct Explorer {
     unsigned rng;
     unsigned long long pending_nodes;
     unsigned long long deadline;
+    long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
                         const MlpImage *net_)
@@ -83,7 +86,19 @@ struct Explorer {
             for (int t = 2; t <= n - 1 - i; ++t) w *= t;
             X.w[i] = w;
         }
+        if (lane < kPhases) X.ph[lane] = 0ull;
+        t_mark = clock64();
         __syncwarp();
+    }
+
+    // Charge the cycles since the last mark to phase p (a few instructions of
+    // lane 0; the sums are reported per solve).
+    __device__ __forceinline__ void tick(int p) {
+        if (lane == 0) {
+            const long long t = clock64();
+            X.ph[p] += (unsigned long long)(t - t_mark);
+            t_mark = t;
+        }
     }
 
     // warp-uniform reads of shared counters (lane 0 loads, all lanes agree)
@@ -200,12 +215,12 @@ struct Explorer {
         __syncwarp();
         __nv_bfloat16 *H1 = Xs + 16 * ldx, *H2 = H1 + 16 * (kMlpHidden + 8);
         net_hidden(Xs, H1, MlpPark{H2});
-        // row 0 (the parent) sits in lanes 0..3: columns 16p + 2t (+1) and 16p + 8 + 2t (+1)
+        // row 0 (the parent) sits in lanes 0..3: columns 16p + 2t (+1) and
+        // 16p + 8 + 2t (+1).  The pair probabilities go to the input tile,
+        // free once layer 1 has run, one float per pair in column order.
         const int npairs = m * (m - 1) / 2;
         const int t = lane & 3;
-        float part[kMaxSlots];
-#pragma unroll
-        for (int s2 = 0; s2 < kMaxSlots; ++s2) part[s2] = 0.0f;
+        float *prob = reinterpret_cast<float *>(Xs);
         for (int p = 0; p < P.O3 / 16; ++p) {
             float c0[4], c1[4];
             mlp_tile_cols<kMlpHidden / 16>(H2, kMlpHidden + 8, P.W3t, kMlpHidden + 8, p, c0, c1);
@@ -215,20 +230,18 @@ struct Explorer {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int col = cols[i];
-                    if (col >= 1 && col <= npairs) {
-                        const float pr = 1.0f / (1.0f + expf(-(z[i] + P.b3[col])));
-#pragma unroll
-                        for (int s2 = 0; s2 < kMaxSlots; ++s2) part[s2] += ((col - 1) >> 5) == s2 ? pr : 0.0f;
-                    }
+                    if (col >= 1 && col <= npairs) prob[col - 1] = 1.0f / (1.0f + expf(-(z[i] + P.b3[col])));
                 }
             }
         }
-#pragma unroll
-        for (int s2 = 0; s2 < kMaxSlots; ++s2) {
-            float v = part[s2];
-            v += __shfl_xor_sync(PFSP_FULL, v, 1);
-            v += __shfl_xor_sync(PFSP_FULL, v, 2);
-            if (lane == 0 && s2 < S) X.sscore[s2] = v;
+        __syncwarp();
+        // summed over the pairs that each slot holds (the instance's pair order)
+        for (int s2 = 0; s2 < S; ++s2) {
+            const int klw = T.kl[s2 * 32 + lane];
+            const int k = klw & 0xff, l = klw >> 8;
+            float v = l > k ? prob[pair_index(k, l, m)] : 0.0f;
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(PFSP_FULL, v, o);
+            if (lane == 0) X.sscore[s2] = v;
         }
         __syncwarp();
         if (lane == 0) {
@@ -356,6 +369,7 @@ struct Explorer {
         }
         const int job0 = lane < n ? X.perm[lane] : 0;
         const int job1 = (NW == 2 && lane + 32 < n) ? X.perm[lane + 32] : 0;
+        tick(counted ? kPhDecode : kPhInit);
         if (counted && a.trace_cap > 0 && (st.decomposed % (unsigned long long)a.trace_stride) == 0) {
             unsigned long long slot = 0;
             if (lane == 0) slot = atomicAdd(a.trace_count, 1ull);
@@ -371,6 +385,7 @@ struct Explorer {
         ChildBounds<NW> cb;
         const int kind = a.bound == PFSP_LB2 ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
         decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
+        tick(counted ? kPhLB1 : kPhInit);
         if ((kind & PFSP_LB2) && m >= 2) {
             const int *order = nullptr;
             if constexpr (LEARNED) {
@@ -381,6 +396,7 @@ struct Explorer {
             }
             decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
         }
+        tick(counted ? kPhLB2 : kPhInit);
         const int u = cb.u;
 
         // ---- MinMin (Section 2.3) ----------------------------------------------
@@ -485,6 +501,7 @@ struct Explorer {
             st.pruned += npruned;
             pending_nodes += 1;
         }
+        tick(counted ? kPhBranch : kPhInit);
     }
 
     // Rebuild the rows along the path to the start digits D and position the
@@ -738,15 +755,19 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
         }
         if (ex.stopped()) break;
         ex.service(state == 2);
+        ex.tick(kPhService);
         if (state == 1) {
             have_node = ex.init_at_start();
             state = 2;
             ex.publish_length(true);
+            ex.tick(kPhInit);
         }
         if (state == 2) {
             ex.st.iters += 1;
             if (!have_node) have_node = ex.select();
-            if (have_node && ex.pos_before_end()) {
+            const bool go = have_node && ex.pos_before_end();
+            ex.tick(kPhSelect);
+            if (go) {
                 ex.expand(true);
                 have_node = false;
                 continue;
@@ -777,15 +798,21 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
             if (__shfl_sync(PFSP_FULL, trip, 0)) break;
         }
         int r = ex.try_steal();
+        ex.tick(kPhIdle);
         if (r < 0) break;
         if (r == 1) {
             state = 1;
             continue;
         }
         __nanosleep(500);
+        ex.tick(kPhIdle);
     }
     ex.flush_limits();
     ex.publish_length(false);
+    ex.tick(kPhService);
+    if (lane == 0 && a.phase) {
+        for (int p = 0; p < kPhases; ++p) atomicAdd(a.phase + p, X.ph[p]);
+    }
     if (lane == 0) {
         atomicAdd(a.counters + 0, ex.st.decomposed);
         atomicAdd(a.counters + 1, ex.st.bounded);

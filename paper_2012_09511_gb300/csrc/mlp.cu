@@ -480,29 +480,44 @@ int pfsp_mlp_set_params(pfsp_mlp *M, const float *in) {
     return e == cudaSuccess ? PFSP_OK : set_error(PFSP_ERR_CUDA, "%s", cudaGetErrorString(e));
 }
 
+}  // extern "C"
+
+namespace pfsp {
+
+// Logits dY [rows][O] of device inputs dX [rows][D0] (synchronous).
+cudaError_t mlp_forward_dev(const pfsp_mlp *M, const float *dX, long long rows, float *dY) {
+    unsigned char *img = nullptr;
+    const int img_bytes = mlp_image_bytes(M->D0, M->O);
+    cudaError_t e = cudaMalloc(&img, img_bytes);
+    if (e == cudaSuccess) e = mlp_build_image(M, M->O, img, 0);
+    if (e == cudaSuccess) {
+        switch (M->D0 / 16) {
+            case 1: e = forward_t<1>(img, img_bytes, M->O, dX, rows, dY); break;
+            case 2: e = forward_t<2>(img, img_bytes, M->O, dX, rows, dY); break;
+            case 3: e = forward_t<3>(img, img_bytes, M->O, dX, rows, dY); break;
+            default: e = forward_t<4>(img, img_bytes, M->O, dX, rows, dY); break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(img);
+    return e;
+}
+
+}  // namespace pfsp
+
+extern "C" {
+
 int pfsp_mlp_forward(const pfsp_mlp *M, int64_t rows, const float *X, float *Y) {
     if (!M || (rows > 0 && (!X || !Y)) || rows < 0) return set_error(PFSP_ERR_INVALID, "bad argument");
     if (rows == 0) return PFSP_OK;
     float *dX = nullptr, *dY = nullptr;
-    unsigned char *img = nullptr;
-    const int img_bytes = mlp_image_bytes(M->D0, M->O);
     cudaError_t e = cudaMalloc(&dX, rows * M->D0 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dY, rows * M->O * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&img, img_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(dX, X, rows * M->D0 * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = mlp_build_image(M, M->O, img, 0);
-    if (e == cudaSuccess) {
-        switch (M->D0 / 16) {
-            case 1: e = pfsp::forward_t<1>(img, img_bytes, M->O, dX, rows, dY); break;
-            case 2: e = pfsp::forward_t<2>(img, img_bytes, M->O, dX, rows, dY); break;
-            case 3: e = pfsp::forward_t<3>(img, img_bytes, M->O, dX, rows, dY); break;
-            default: e = pfsp::forward_t<4>(img, img_bytes, M->O, dX, rows, dY); break;
-        }
-    }
+    if (e == cudaSuccess) e = pfsp::mlp_forward_dev(M, dX, rows, dY);
     if (e == cudaSuccess) e = cudaMemcpy(Y, dY, rows * M->O * 4, cudaMemcpyDeviceToHost);
     cudaFree(dX);
     cudaFree(dY);
-    cudaFree(img);
     return e == cudaSuccess ? PFSP_OK : set_error(PFSP_ERR_CUDA, "pfsp_mlp_forward: %s", cudaGetErrorString(e));
 }
 

@@ -22,10 +22,12 @@ constexpr int kMaxTableBytes = 160 * 1024;  // LB2 tables must fit in shared mem
 // copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):
 //   pm   [m][nj]       processing times by machine (nj = n rounded up to 4)
 //   tot  [32]          per-machine totals T_k = sum_j p[j][k]
-//   kl   [S*32]        machine pair of pair slot q: k | l << 8 (dummy: 0)
+//   kl   [S*32]        machine pair at slot position i: k | l << 8 (dummy: 0);
+//                      pairs sit in the instance's pair order (default: k = 0..m-2,
+//                      l = k+1..m-1), position i in slot i / 32, lane i % 32
 //   rank [n][S][32]    uint8: position t of job j in the Johnson order of
 //                      the lane's pair (dummy lanes: j)
-//   ptab [S][n][32]    int2 per (slot, position, lane): pair q = slot*32+lane,
+//   ptab [S][n][32]    int2 per (slot, position, lane): the lane's pair,
 //                      x = (a << 8) | job, y = b, for the job at position t of
 //                      the pair's Johnson order, with a = p[j][l] - p[j][k]
 //                      and b = g_j + p[j][l] (g_j = lag).  Dummy lanes (pairs
@@ -51,6 +53,7 @@ struct pfsp_instance {
     void *d_scratch;
     size_t scratch_bytes;
     pfsp_stats_t stats;
+    int32_t *pair_order;         // pair at each slot position (NULL: k < l lexicographic)
 };
 
 namespace pfsp {
@@ -72,7 +75,12 @@ cudaError_t mlp_build_image(const pfsp_mlp *M, int O3, void *dst, cudaStream_t s
 int mlp_dims(const pfsp_mlp *M, int *m, int *D0, int *O);
 
 // Host-side builders shared by the entry points (capi.cu, solve_capi.cu).
-void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob);
+// pair_order: the pair (index in k < l lexicographic order) placed at each
+// slot position, NULL for the lexicographic order itself.
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order);
+
+// Index of machine pair k < l in the lexicographic order of all m(m-1)/2 pairs.
+__host__ __device__ inline int pair_index(int k, int l, int m) { return k * (2 * m - k - 1) / 2 + (l - k - 1); }
 int neh(int n, int m, const int32_t *p, std::vector<int> &perm);
 
 }  // namespace pfsp

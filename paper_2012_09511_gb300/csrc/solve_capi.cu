@@ -100,8 +100,6 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
     if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT))
         return set_error(PFSP_ERR_INVALID, "unknown bits in learned");
-    if ((opt->learned & PFSP_EARLY_EXIT) && opt->branching != PFSP_MINMIN_CAPPED)
-        return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT needs PFSP_MINMIN_CAPPED");
     const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
     int net_m = 0, net_D0 = 0, net_O = 0;
     if (use_net) {
@@ -221,7 +219,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const size_t o_rj = take((size_t)K * n * n), o_rl = take((size_t)K * n * n * 4);
     const size_t o_is = take((size_t)K * 64), o_ie = take((size_t)K * 65);
     const size_t o_mb = take((size_t)K * 8), o_rs = take((size_t)K * 8), o_le = take((size_t)K * 4);
-    const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64);
+    const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64), o_ph = take(8 * kPhases);
     const int64_t tcap = tr ? tr->capacity : 0;
     const size_t o_tp = take((size_t)tcap * n), o_t1 = take((size_t)tcap), o_t2 = take((size_t)tcap),
                  o_tc = take(8);
@@ -242,6 +240,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.len_est = (float *)(b + o_le);
     a.best_perm = (uint8_t *)(b + o_bp);
     a.counters = (unsigned long long *)(b + o_ct);
+    a.phase = (unsigned long long *)(b + o_ph);
     int *sc = (int *)(b + o_sc);  // active, ub, stop, err, best_key (8 bytes at +16)
     a.active = sc + 0;
     a.ub = sc + 1;
@@ -275,6 +274,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.phase, 0, 8 * kPhases, st);
     if (e == cudaSuccess && tcap > 0) e = cudaMemsetAsync(a.trace_count, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_end, he.data(), he.size(), cudaMemcpyHostToDevice, st);
@@ -283,9 +283,10 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (e == cudaSuccess) e = launch_solve(a, blocks, warps, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
     int rsc[6];
-    unsigned long long cnt[8];
+    unsigned long long cnt[8], ph[kPhases];
     if (e == cudaSuccess) e = cudaMemcpyAsync(rsc, sc, sizeof(rsc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, a.counters, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ph, a.phase, sizeof(ph), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
@@ -335,6 +336,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     inst->stats.kernel_seconds = ms * 1e-3;
     inst->stats.final_ub = final_ub;
     inst->stats.explorers = K;
+    for (int p = 0; p < kPhases; ++p) inst->stats.phase_cycles[p] = ph[p];
     inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return PFSP_OK;
 }

@@ -21,6 +21,18 @@ constexpr unsigned long long kNoRequest = ~0ull;  // empty mailbox
 constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
 #define PFSP_FWD_DIR 0
 
+// Phases of an explorer's loop whose SM clock cycles are summed per solve
+// (pfsp_stats_t.phase_cycles).
+constexpr int kPhService = 0;  // limit checks, steal requests answered, length publication
+constexpr int kPhSelect = 1;   // next live cell, backtracking, interval-end check
+constexpr int kPhDecode = 2;   // node decoding into [sigma1 | unscheduled | sigma2]
+constexpr int kPhLB1 = 3;      // front/back wavefronts and LB1 of all children
+constexpr int kPhLB2 = 4;      // LB2 sweep over the machine pairs
+constexpr int kPhBranch = 5;   // MinMin, pruning, the new row, leaves (and the network's row order)
+constexpr int kPhInit = 6;     // rebuilding the path to a new interval's start
+constexpr int kPhIdle = 7;     // stealing and waiting without work
+constexpr int kPhases = 8;
+
 struct SolveArgs {
     // instance tables (same layout as the bounding kernel)
     const int32_t *tab;
@@ -50,6 +62,7 @@ struct SolveArgs {
     unsigned long long *best_key;  // (cmax << 32) | explorer
     uint8_t *best_perm;   // [K][64]
     unsigned long long *counters;  // decomposed, bounded, leaves, pruned, steals, iters, limit count
+    unsigned long long *phase;     // [kPhases] cycles per phase summed over explorers (NULL: not reported)
     long long node_limit;
     unsigned long long time_limit_ns;  // stop after this long on the device clock; 0 = none
     int *stop;            // 0 run, 1 node limit, 2 time limit, 3 error

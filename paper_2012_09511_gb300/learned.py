@@ -3,15 +3,20 @@
 Orchestration only; every step runs in the library's kernels:
 pfsp_solve_trace records nodes the solver decomposes, pfsp_mlp_rows builds
 the training rows on the GPU, pfsp_mlp_train trains the network on the GPU,
-and pfsp_solve runs the plain and the learned solvers.
+pfsp_learn_pair_order ranks the machine pairs with the network, and
+pfsp_solve runs the plain and the learned solvers.
 
-The learned solver uses the capped MinMin rule, sweeps LB2's 32-pair slots in
-the order of the network's pair logits and stops the sweep once every child's
-bound reaches the cap, and orders each new row by the network's descend-first
-logits.  Its optimum is always the plain solver's; the comparison reports the
-time to the proven optimum and the decomposed-node counts of both.
+The learned solver sweeps LB2's machine pairs in the network's order (per
+instance, from a short pilot trace), stops a node's sweep as soon as every
+child of one direction is at or above the incumbent (no such node has a child
+below it, so the tree is unchanged), and orders the rows of the first levels
+by the network's descend-first logits.  Its optimum is always the plain
+solver's; the comparison reports the time to the proven optimum (wall time,
+pilot and ranking included) and the decomposed-node counts of both.
 """
 from __future__ import annotations
+
+import time
 
 import numpy as np
 
@@ -45,59 +50,125 @@ def train_network(pfsp, m, train_instances, seed=0, epochs=8, batch=4096, lr=2e-
     return mlp, {"rows": int(len(X)), "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
 
 
-def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None):
-    """Plain and learned solves of one instance from its NEH schedule (LB2).
+def pilot_nodes(pfsp, inst, nodes=4096, stride=2, bound=2, time_limit_s=2.0):
+    """A short trace of the solver on `inst`: the first `nodes` decompositions,
+    every `stride`-th recorded (the sample the pair ranking is computed on)."""
+    perm, d1, d2, _ = pfsp.pfsp_solve_trace(inst, nodes // stride + 64, stride=stride, bound=bound,
+                                            node_limit=nodes, time_limit_s=time_limit_s)
+    return perm, d1, d2
 
-    `learned` uses every learned option with the network ordering the rows of
-    the first `depth` levels (depth = depths[0], default n / 3); the other
-    entries are ablations: the capped rule and early exit without the network,
-    and the network's row order alone at each depth of `depths`."""
+
+def rank_pairs(pfsp, inst, mlp, **pilot_kw):
+    """Learned pair order of `inst`: the network's mean pair probabilities over a
+    pilot trace, pairs sorted by decreasing score and applied to the instance
+    (so that LB2's first 32-pair slot holds the pairs most likely to decide a
+    child).  Returns the order."""
+    perm, d1, d2 = pilot_nodes(pfsp, inst, **pilot_kw)
+    if len(d1) == 0:
+        pfsp.pfsp_set_pair_order(inst, None)
+        return None
+    return pfsp.pfsp_learn_pair_order(inst, mlp, perm, d1, d2)
+
+
+def _run(pfsp, inst, **kw):
+    t = time.perf_counter()
+    r = pfsp.pfsp_solve(inst, **kw)
+    return r, time.perf_counter() - t
+
+
+def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
+    """Plain and learned solves of one instance (LB2), from its NEH schedule or,
+    with init_ub, in proof mode.
+
+    plain: the full-pair LB2 solver, pairs in index order.
+    learned: a pilot trace ranks the pairs with the network (pfsp_learn_pair_order),
+    then the solve stops each LB2 sweep as soon as one direction's children are
+    all at or above the incumbent, and the network orders the rows of the first
+    `depth` levels (depth = depths[0], default n / 3).  Its wall time includes the
+    pilot and the ranking.
+    Ablations: early exit with the index pair order (no network), early exit with
+    the learned pair order only, and the network's row order alone per depth."""
     n = p.shape[0]
     depths = depths or [max(1, n // 3)]
     inst = pfsp.pfsp_load_instance(p)
-    runs = {
-        "plain": dict(),
-        "capped_static_early_exit": dict(branching=1, learned=4),
-        "learned": dict(branching=1, learned=LEARNED_ALL, mlp=mlp, learn_depth=depths[0]),
-    }
-    for d in depths:
-        runs["child_order_depth_%d" % d] = dict(learned=1, mlp=mlp, learn_depth=d)
+    base = dict(bound=2, time_limit_s=time_limit_s)
+    if init_ub is not None:
+        base["init_ub"] = int(init_ub)
     out = {}
-    for name, kw in runs.items():
-        r = pfsp.pfsp_solve(inst, bound=2, time_limit_s=time_limit_s, **kw)
+
+    def record(name, r, wall, extra_wall=0.0):
         out[name] = {"cmax": r["cmax"], "outcome": r["outcome"], "seconds": r["kernel_seconds"],
-                     "decomposed": r["decomposed"], "bounded": r["bounded_children"]}
+                     "wall_seconds": wall + extra_wall, "decomposed": r["decomposed"],
+                     "bounded": r["bounded_children"]}
+
+    pfsp.pfsp_set_pair_order(inst, None)
+    record("plain", *_run(pfsp, inst, **base))
+    record("early_exit_index_order", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base))
+    for d in depths:
+        record("child_order_depth_%d" % d,
+               *_run(pfsp, inst, learned=pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp, learn_depth=d, **base))
+    t = time.perf_counter()
+    rank_pairs(pfsp, inst, mlp)
+    t_rank = time.perf_counter() - t
+    record("early_exit_learned_pairs", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base), extra_wall=t_rank)
+    record("learned", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
+                            learn_depth=depths[0], **base), extra_wall=t_rank)
+    out["ranking_wall_seconds"] = t_rank
     return out
 
 
 def compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), train_seeds=range(1, 11), time_limit_s=30.0,
-            depth_fracs=(3,)):
+            depth_fracs=(3,), proof=False, mlps=None):
     """Time to the proven optimum, plain vs learned, on the given shapes.
 
     The m-machine network is trained on traces of 20-job instances with the same
-    m (seeds train_seeds); the evaluation instances are n x m with seeds
-    100 + s, disjoint from training."""
+    m (seeds train_seeds), unless mlps maps m to a trained network; the
+    evaluation instances are n x m with seeds 100 + s, disjoint from training.
+    proof=False solves from NEH (find and prove); proof=True first finds the
+    optimum with the plain solver, then times both solvers proving it (incumbent
+    at the optimum, a fixed tree)."""
     report = {}
     for n, m in shapes:
-        train = [inputs.make_instance(20, m, s) for s in train_seeds]
-        mlp, info = train_network(pfsp, m, train)
+        if mlps and m in mlps:
+            mlp, info = mlps[m], {"reused": True}
+        else:
+            t = time.perf_counter()
+            train = [inputs.make_instance(20, m, s) for s in train_seeds]
+            mlp, info = train_network(pfsp, m, train)
+            info["seconds"] = time.perf_counter() - t
         rows = []
         for s in seeds:
             p = inputs.make_instance(n, m, 100 + s)
+            ub = None
+            if proof:
+                inst = pfsp.pfsp_load_instance(p)
+                f = pfsp.pfsp_solve(inst, bound=2, time_limit_s=time_limit_s)
+                if f["outcome"] != pfsp.PFSP_OPTIMAL:
+                    continue
+                ub = f["cmax"]
             r = solve_variants(pfsp, p, mlp, time_limit_s=time_limit_s,
-                               depths=[max(1, n // f) for f in depth_fracs])
+                               depths=[max(1, n // f) for f in depth_fracs], init_ub=ub)
             r["seed"] = 100 + s
             r["same_optimum"] = len({v["cmax"] for v in r.values() if isinstance(v, dict)}) == 1
             rows.append(r)
-        done = [r for r in rows if all(r[k]["outcome"] == 0 for k in ("plain", "learned"))]
-        t_plain = sum(r["plain"]["seconds"] for r in done)
-        t_learn = sum(r["learned"]["seconds"] for r in done)
-        n_plain = sum(r["plain"]["decomposed"] for r in done)
-        n_learn = sum(r["learned"]["decomposed"] for r in done)
+        want = pfsp.PFSP_PROVEN_NO_BETTER if proof else pfsp.PFSP_OPTIMAL
+        done = [r for r in rows if all(r[k]["outcome"] == want for k in ("plain", "learned"))]
+
+        def tot(key, field):
+            return sum(r[key][field] for r in done)
+
+        t_plain, t_learn = tot("plain", "wall_seconds"), tot("learned", "wall_seconds")
+        k_plain, k_learn = tot("plain", "seconds"), tot("learned", "seconds")
+        n_plain, n_learn = tot("plain", "decomposed"), tot("learned", "decomposed")
         report["%dx%d" % (n, m)] = {
-            "training": info, "instances": rows, "solved_by_both": len(done),
-            "time_plain_s": t_plain, "time_learned_s": t_learn,
-            "speedup": (t_plain / t_learn) if t_learn > 0 else None,
+            "mode": "proof" if proof else "find", "training": info, "instances": rows,
+            "solved_by_both": len(done),
+            "wall_plain_s": t_plain, "wall_learned_s": t_learn,
+            "speedup_wall": (t_plain / t_learn) if t_learn > 0 else None,
+            "kernel_plain_s": k_plain, "kernel_learned_s": k_learn,
+            "speedup_kernel": (k_plain / k_learn) if k_learn > 0 else None,
             "node_ratio_learned_over_plain": (n_learn / n_plain) if n_plain > 0 else None,
+            "ablation_wall_s": {key: tot(key, "wall_seconds") for key in done[0] if isinstance(done[0][key], dict)}
+            if done else {},
         }
     return report

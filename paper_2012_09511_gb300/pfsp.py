@@ -47,10 +47,14 @@ class pfsp_stats_t(ctypes.Structure):
                 ("leaves", ctypes.c_uint64), ("pruned", ctypes.c_uint64), ("steals", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("final_ub", ctypes.c_int32),
-                ("explorers", ctypes.c_int32)]
+                ("explorers", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8)]
+
+    PHASES = ("service", "select", "decode", "lb1", "lb2", "branch", "init", "idle")
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "phase_cycles"}
+        d["phase_cycles"] = dict(zip(self.PHASES, [int(x) for x in self.phase_cycles]))
+        return d
 
 
 PFSP_LEARN_CHILD_ORDER = 1
@@ -122,6 +126,14 @@ _lib.pfsp_mlp_rows.restype = ctypes.c_int
 _lib.pfsp_mlp_rows.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
+_lib.pfsp_set_pair_order.restype = ctypes.c_int
+_lib.pfsp_set_pair_order.argtypes = [_vp, _vp]
+_lib.pfsp_get_pair_order.restype = ctypes.c_int
+_lib.pfsp_get_pair_order.argtypes = [_vp, _vp]
+_lib.pfsp_mlp_pair_scores.restype = ctypes.c_int
+_lib.pfsp_mlp_pair_scores.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+_lib.pfsp_learn_pair_order.restype = ctypes.c_int
+_lib.pfsp_learn_pair_order.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
 
 
 def lib():
@@ -394,3 +406,35 @@ def pfsp_mlp_rows(inst: Instance, mlp: Mlp, perm, d1, d2):
     _check(_lib.pfsp_mlp_rows(inst.handle, mlp.handle, k, _ptr(perm), _ptr(d1), _ptr(d2), _ptr(X), _ptr(T),
                               _ptr(M)))
     return X, T, M
+
+
+def pfsp_set_pair_order(inst: Instance, order=None) -> None:
+    """Sweep order of the machine pairs (indices k < l lexicographic); None = index order."""
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    _check(_lib.pfsp_set_pair_order(inst.handle, _ptr(o)))
+
+
+def pfsp_get_pair_order(inst: Instance) -> np.ndarray:
+    out = np.empty(inst.m * (inst.m - 1) // 2, dtype=np.int32)
+    _check(_lib.pfsp_get_pair_order(inst.handle, _ptr(out)))
+    return out
+
+
+def pfsp_mlp_pair_scores(inst: Instance, mlp: Mlp, perm, d1, d2) -> np.ndarray:
+    """Mean network probability per pair over the nodes (pair index order)."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+    d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+    out = np.empty(max(1, inst.m * (inst.m - 1) // 2), dtype=np.float32)
+    _check(_lib.pfsp_mlp_pair_scores(inst.handle, mlp.handle, len(d1), _ptr(perm), _ptr(d1), _ptr(d2), _ptr(out)))
+    return out[:inst.m * (inst.m - 1) // 2]
+
+
+def pfsp_learn_pair_order(inst: Instance, mlp: Mlp, perm, d1, d2) -> np.ndarray:
+    """Rank the pairs by the network's scores over the nodes and apply that order; returns it."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+    d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+    out = np.empty(max(1, inst.m * (inst.m - 1) // 2), dtype=np.int32)
+    _check(_lib.pfsp_learn_pair_order(inst.handle, mlp.handle, len(d1), _ptr(perm), _ptr(d1), _ptr(d2), _ptr(out)))
+    return out[:inst.m * (inst.m - 1) // 2]

@@ -7,7 +7,10 @@
 * The solver's traced nodes are valid nodes of the instance.
 * Exactness: with any network the optimum is unchanged, and in proof mode
   capped MinMin with early exit and learned orders explores exactly the tree
-  of plain capped MinMin (the oracle's capped count).
+  of plain capped MinMin (the oracle's capped count).  Early exit alone, with
+  any pair order, keeps the oracle's counts under either MinMin rule.
+* The pair order changes no bound and no training row; the learned order
+  ranks the pairs by the network's mean pair probability.
 * Training on the solver's own traces lowers the loss and predicts the pair
   targets better than the best constant per pair (what the network adds).
 """
@@ -112,11 +115,84 @@ def test_learned_solver_is_exact(pf, n, m, seed):
     assert g["cmax"] == opt
 
 
+@pytest.mark.parametrize("n,m,seed", [(12, 10, 17), (11, 20, 3), (13, 5, 8), (12, 8, 6)])
+def test_early_exit_keeps_the_tree(pf, n, m, seed):
+    # a node one of whose directions is entirely at or above the incumbent
+    # has no child below it under either MinMin rule, so stopping its LB2
+    # sweep there changes no count, capped or not, whatever the pair order
+    p = inputs.make_instance(n, m, seed)
+    inst = pf.pfsp_load_instance(p)
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    rng = np.random.default_rng(seed)
+    for order in (None, rng.permutation(m * (m - 1) // 2)):
+        pf.pfsp_set_pair_order(inst, order)
+        for capped in (False, True):
+            want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, capped=capped)
+            r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=pf.PFSP_EARLY_EXIT,
+                              branching=pf.PFSP_MINMIN_CAPPED if capped else pf.PFSP_MINMIN)
+            assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+            got = (r["decomposed"], r["bounded_children"], r["pruned"])
+            assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, capped)
+        f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, learned=pf.PFSP_EARLY_EXIT)
+        assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
+
+
+def test_early_exit_proof_counts_20x10(pf):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "solve_20x10_lb2.json")))
+    for g in gold["results"]:
+        if g["proof_decomposed"] > 200000:
+            continue
+        inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, g["seed"]))
+        r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"], learned=pf.PFSP_EARLY_EXIT)
+        assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (
+            g["proof_decomposed"], g["proof_bounded"], g["proof_pruned"]), g["seed"]
+
+
+def test_pair_order_changes_no_bound(pf):
+    n, m = 14, 10
+    p = inputs.make_instance(n, m, 21)
+    inst = pf.pfsp_load_instance(p)
+    perm, d1, d2 = inputs.random_nodes(n, 3000, seed=4, dmax=6)
+    a1, a2 = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    mlp = pf.pfsp_mlp_create(m, seed=2)
+    X0, T0, M0 = pf.pfsp_mlp_rows(inst, mlp, perm[:50], d1[:50], d2[:50])
+    order = np.random.default_rng(1).permutation(m * (m - 1) // 2).astype(np.int32)
+    pf.pfsp_set_pair_order(inst, order)
+    assert (pf.pfsp_get_pair_order(inst) == order).all()
+    b1, b2 = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    assert (a1 == b1).all() and (a2 == b2).all()
+    X1, T1, M1 = pf.pfsp_mlp_rows(inst, mlp, perm[:50], d1[:50], d2[:50])
+    assert (X0 == X1).all() and (T0 == T1).all() and (M0 == M1).all()
+    pf.pfsp_set_pair_order(inst, None)
+    assert (pf.pfsp_get_pair_order(inst) == np.arange(m * (m - 1) // 2)).all()
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_set_pair_order(inst, np.zeros(m * (m - 1) // 2, dtype=np.int32))
+
+
+def test_learned_pair_order_ranks_network_scores(pf):
+    n, m = 16, 10
+    p = inputs.make_instance(n, m, 5)
+    inst = pf.pfsp_load_instance(p)
+    mlp = pf.pfsp_mlp_create(m, seed=9)
+    perm, d1, d2, _ = pf.pfsp_solve_trace(inst, 400, stride=1, bound=pf.PFSP_LB2)
+    score = pf.pfsp_mlp_pair_scores(inst, mlp, perm, d1, d2)
+    # the same mean from the network's forward on the parent rows
+    X, _, _ = pf.pfsp_mlp_rows(inst, mlp, perm, d1, d2)
+    Y = pf.pfsp_mlp_forward(mlp, X[::1 + 2 * n])
+    P = m * (m - 1) // 2
+    want = (1.0 / (1.0 + np.exp(-Y[:, 1:1 + P].astype(np.float64)))).mean(axis=0)
+    assert np.allclose(score, want, rtol=1e-5, atol=1e-6)
+    order = pf.pfsp_learn_pair_order(inst, mlp, perm, d1, d2)
+    assert sorted(order.tolist()) == list(range(P))
+    assert (np.diff(score[order]) <= 0).all()
+    assert (pf.pfsp_get_pair_order(inst) == order).all()
+
+
 def test_learned_options_are_validated(pf):
     p = inputs.make_instance(8, 5, 1)
     inst = pf.pfsp_load_instance(p)
-    with pytest.raises(pf.PfspError):  # early exit without the capped rule
-        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT)
     with pytest.raises(pf.PfspError):  # no network
         pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_LEARN_CHILD_ORDER)
     other = pf.pfsp_mlp_create(10, seed=1)

@@ -241,6 +241,26 @@ def test_minmin_tie_rules():
     assert orc.minmin([20, 30], [25, 40], [0, 1], cap=10) == orc.FWD
 
 
+@pytest.mark.parametrize("capped", [False, True])
+def test_minmin_picks_a_fully_pruned_direction(capped):
+    # Brute force over small bound vectors: when every child of one direction
+    # is at or above the incumbent, MinMin's choice leaves no child below it
+    # (the early exit of the LB2 sweep relies on this).  A plausible slip in
+    # the rule (counting the more frequent minimum, or the smaller sum first)
+    # fails here.
+    rng = np.random.default_rng(7 + capped)
+    ub = 10
+    for _ in range(4000):
+        u = int(rng.integers(1, 5))
+        jobs = list(range(u))
+        full = rng.integers(ub, ub + 4, size=u)      # one direction entirely >= ub
+        other = rng.integers(ub - 3, ub + 3, size=u)  # the other one mixed
+        for lbf, lbb in ((full, other), (other, full)):
+            d = orc.minmin(lbf, lbb, jobs, cap=ub if capped else orc.INT32_MAX)
+            chosen = lbf if d == orc.FWD else lbb
+            assert all(v >= ub for v in chosen), (lbf, lbb, d)
+
+
 # ---------------------------------------------------------------- search ---
 
 @pytest.mark.parametrize("seed", range(1, 11))
