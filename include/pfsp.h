@@ -113,13 +113,17 @@ typedef struct {
     double kernel_seconds;     /* device time of the main kernel (CUDA events) */
     int32_t final_ub;          /* incumbent at the end of a solve */
     int32_t explorers;         /* explorers used by a solve */
-    /* pfsp_solve only (zero elsewhere): SM clock cycles spent by the explorers
-     * in each phase of their loop, summed over explorers: [0] limit checks and
+    /* pfsp_solve with pfsp_options.phase_timers only (zero elsewhere): SM clock
+     * cycles spent by the explorers in each phase of their loop, summed over
+     * explorers: [0] limit checks and
      * answering steal requests, [1] selecting the next node, [2] decoding it,
      * [3] LB1 (wavefronts and children), [4] the LB2 sweep, [5] MinMin,
      * pruning and the new row, [6] rebuilding the path to a stolen interval's
      * start, [7] stealing and waiting without work. */
     uint64_t phase_cycles[8];
+    /* pfsp_solve only: 32-pair slots swept by LB2, summed over decompositions
+     * (fewer than decomposed x ceil(m(m-1)/2 / 32) with PFSP_EARLY_EXIT). */
+    uint64_t lb2_slots;
 } pfsp_stats_t;
 
 /*
@@ -170,7 +174,10 @@ typedef struct {
     const pfsp_mlp *mlp;  /* network used by the PFSP_LEARN_* flags (built for the instance's m) */
     int learned;          /* PFSP_LEARN_* / PFSP_EARLY_EXIT bits; 0 = plain solver */
     int learn_depth;      /* the network orders rows of level < learn_depth only (0 = every level) */
-    int reserved[8];
+    int phase_timers;     /* 1: fill pfsp_stats_t.phase_cycles (reads the SM clock at every phase
+                             boundary, which slows the solve down several times: for relative
+                             profiling only); 0 (default): off */
+    int reserved[7];
 } pfsp_options;
 
 void pfsp_default_options(pfsp_options *opt);
@@ -189,6 +196,38 @@ void pfsp_default_options(pfsp_options *opt);
  */
 int pfsp_solve(const pfsp_instance *inst, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
                int *outcome);
+
+/*
+ * pfsp_solve in resumable segments: the checkpoint of the paper's coordinator
+ * (Section 4.1, a file of the unexplored intervals plus the best solution,
+ * read back on restart), here for the explorer pool of one GPU.
+ *   resume       NULL: search the whole tree; else a checkpoint written by an
+ *                earlier call on this instance with the same bound and
+ *                branching options (resume_bytes its size): the search covers
+ *                exactly the intervals it holds, from its incumbent (opt->init_ub
+ *                is ignored) and with its cap (the first segment's initial
+ *                incumbent, used by PFSP_MINMIN_CAPPED and PFSP_EARLY_EXIT).
+ *   checkpoint   NULL: nothing is recorded.  Else, when the call stops at
+ *                node_limit or time_limit_s, *checkpoint receives a buffer
+ *                allocated by the library (free it with pfsp_free_checkpoint)
+ *                and *checkpoint_bytes its size: the incumbent, a schedule
+ *                reaching it (when one is known) and, for every explorer with
+ *                work left, the rest of its interval and the level of the next
+ *                node it would have decomposed.  When the search finishes,
+ *                *checkpoint is NULL and *checkpoint_bytes 0.
+ * Every node is decomposed in exactly one segment: in proof mode the counters
+ * of the segments add up to those of one uninterrupted pfsp_solve.  The buffer
+ * is plain bytes and can be written to a file; it is only valid for a launch
+ * with at least as many explorers as records (the same device and options).
+ * Errors: those of pfsp_solve; PFSP_ERR_INVALID for a malformed or foreign
+ * checkpoint; PFSP_ERR_UNSUPPORTED when it holds more intervals than the
+ * launch has explorers.
+ */
+int pfsp_solve_resumable(const pfsp_instance *inst, const pfsp_options *opt, const uint8_t *resume,
+                         int64_t resume_bytes, uint8_t **checkpoint, int64_t *checkpoint_bytes, int32_t *best_cmax,
+                         int32_t *best_perm, int *outcome);
+/* Release a checkpoint returned by pfsp_solve_resumable.  NULL is ignored. */
+void pfsp_free_checkpoint(uint8_t *checkpoint);
 
 /*
  * Solve `count` independent instances (any mix of n and m, all loaded on the

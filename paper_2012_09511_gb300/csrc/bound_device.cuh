@@ -384,8 +384,8 @@ __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *
 // registers per direction (u <= NC); NC = 0: they live in W.Acc.  RW: the
 // walks keep their records in registers (u <= kRegWalk).
 template <int NW, int MT, int NC, bool RW>
-__device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                          ChildBounds<NW> &out, int cap, const int *order) {
+__device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
+                                         ChildBounds<NW> &out, int cap, const int *order) {
     using mask_t = umask_t<NW>;
     constexpr bool REGACC = NC > 0;
     const int m = MT ? MT : m_rt;
@@ -407,7 +407,7 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             done_f |= (mask_t)bf << (32 * h);
             done_b |= (mask_t)bb << (32 * h);
         }
-        if ((done_f & all) == all || (done_b & all) == all) return;
+        if ((done_f & all) == all || (done_b & all) == all) return 0;
     }
     int accf[REGACC ? NC : 1], accb[REGACC ? NC : 1];
     if constexpr (REGACC) {
@@ -432,8 +432,10 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             for (int s = 0; s < SC; ++s) UposAll[s] |= mask_t(1) << rj[s * 32];
         }
     }
+    int swept = 0;
 #pragma unroll 1
     for (int si = 0; si < S; ++si) {
+        swept = si + 1;
         const int s = order ? order[si] : si;
         const int klw = T.kl[s * 32 + lane];
         const int k = klw & 0xff, l = klw >> 8;
@@ -483,9 +485,11 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
                 W.Acc[c * 32 + lane] = v;
             }
         }
-        if (cap != INT_MAX && si + 1 < S) {
+        if (cap != INT_MAX && si + 1 < S && S >= 4) {
             // every child of one direction decided? (its LB1 or some pair
-            // term already >= cap)
+            // term already >= cap).  Checked between slots only when several
+            // slots remain to be saved: with two slots (m <= 11) the check
+            // costs about what the second slot would.
             mask_t mf = 0, mb = 0;
             if constexpr (REGACC) {
 #pragma unroll
@@ -546,6 +550,7 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
             out.lb2b[h] = max(out.lb1b[h], mb);
         }
     }
+    return swept;
 }
 
 // LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
@@ -560,13 +565,14 @@ __device__ __forceinline__ void lb2_sweep(const SmemTables &T, const WarpScratch
 // WALK = 1: register walks (n <= kRegWalk, scratch carved with reg_walk);
 // WALK = 0: walks through shared memory (any n).  Fixed per kernel, so that
 // a kernel carries the register demand of one path only.
+// Returns the number of 32-pair slots swept (fewer than S after an early exit).
 template <int NW, int MT, int WALK = 0>
-__device__ __forceinline__ void decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                              ChildBounds<NW> &out, int cap, const int *order) {
-    if (out.u == 0 || (MT ? MT : m_rt) < 2) return;
+__device__ __forceinline__ int decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
+                                             ChildBounds<NW> &out, int cap, const int *order) {
+    if (out.u == 0 || (MT ? MT : m_rt) < 2) return 0;
     static_assert(WALK == 0 || NW == 1, "register walks need n <= 32");
-    if constexpr (WALK == 1) lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, order);
-    else lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, order);
+    if constexpr (WALK == 1) return lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, order);
+    else return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, order);
 }
 
 // Both phases: the bounds of all 2u children of the node.

@@ -35,7 +35,8 @@ struct ExplorerSmem {
     double w[64];   // (n-1-i)! as double, for length estimates
     int etop;
     unsigned seq;   // sequence number of this explorer's last steal request
-    int pad[6];
+    int lvl;        // start level of the interval (-1: the first level below which D is all zero)
+    int pad[5];
     float score[64];   // descend-first logits of the children being ordered
     float sscore[16];  // summed pair probabilities per LB2 slot
     int sorder[16];    // LB2 slot order of the current node
@@ -45,7 +46,7 @@ constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 8 + 64 + 16 + 16 + 2 * kPhases
 static_assert(kExplorerWords % 8 == 0, "explorer scratch keeps 32-byte alignment");
 
 struct Stats {
-    unsigned long long decomposed, bounded, leaves, pruned, steals, iters;
+    unsigned long long decomposed, bounded, leaves, pruned, steals, iters, slots;
 };
 
 // LEARNED: the instantiation that runs the ordering network; the plain
@@ -66,6 +67,7 @@ struct Explorer {
     unsigned long long pending_nodes;
     unsigned long long deadline;
     long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
+    bool timed;        // phase timers on (a.phase != NULL)
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
                         const MlpImage *net_)
@@ -77,7 +79,7 @@ struct Explorer {
         rj = a.rows_job + (size_t)me * a.row_stride;
         rl = a.rows_lb + (size_t)me * a.row_stride;
         I = -1;
-        st = Stats{0, 0, 0, 0, 0, 0};
+        st = Stats{0, 0, 0, 0, 0, 0, 0};
         rng = 0x9e3779b9u * (me + 1) ^ 0x85ebca6bu;
         pending_nodes = 0;
         deadline = a.time_limit_ns ? global_ns() + a.time_limit_ns : 0ull;
@@ -86,15 +88,16 @@ struct Explorer {
             for (int t = 2; t <= n - 1 - i; ++t) w *= t;
             X.w[i] = w;
         }
+        timed = a.phase != nullptr;
         if (lane < kPhases) X.ph[lane] = 0ull;
-        t_mark = clock64();
+        t_mark = timed ? clock64() : 0;
         __syncwarp();
     }
 
-    // Charge the cycles since the last mark to phase p (a few instructions of
-    // lane 0; the sums are reported per solve).
+    // Charge the cycles since the last mark to phase p (lane 0; the sums are
+    // reported per solve).  A uniform test when the timers are off.
     __device__ __forceinline__ void tick(int p) {
-        if (lane == 0) {
+        if (timed && lane == 0) {
             const long long t = clock64();
             X.ph[p] += (unsigned long long)(t - t_mark);
             t_mark = t;
@@ -394,7 +397,9 @@ struct Explorer {
                     order = X.sorder;
                 }
             }
-            decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
+            const int swept =
+                decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
+            if (counted) st.slots += swept;
         }
         tick(counted ? kPhLB2 : kPhInit);
         const int u = cb.u;
@@ -506,7 +511,11 @@ struct Explorer {
 
     // Rebuild the rows along the path to the start digits D and position the
     // explorer on the first live node at or after start.  Returns false when
-    // no such node exists.
+    // no such node exists.  The node that starts the interval is the first
+    // one on the path whose remaining digits are all zero (X.lvl < 0: a
+    // stolen or initial interval), or the node at level X.lvl (a resumed
+    // checkpoint, whose ancestors on the path were decomposed before it even
+    // when they share its leftmost leaf).  Ancestors are not counted.
     __device__ bool init_at_start() {
         I = -1;
         bool zero = true;
@@ -514,7 +523,8 @@ struct Explorer {
             int i = lane + 32 * h;
             zero &= __all_sync(PFSP_FULL, i >= n || X.D[i] == 0);
         }
-        expand(zero);  // the root; counted only by the explorer starting at 0
+        const int lvl = X.lvl;
+        expand(zero && lvl < 0);  // the root; counted only by the explorer starting at 0
         while (true) {
             // I is the level whose row has just been built; follow the digit D[I]
             const int d = X.D[I];
@@ -531,7 +541,7 @@ struct Explorer {
                 int i = lane + 32 * h;
                 rest_zero &= __all_sync(PFSP_FULL, i >= n || i <= I || X.D[i] == 0);
             }
-            if (rest_zero || I >= n - 2) return true;  // this node starts the interval
+            if ((lvl < 0 ? rest_zero : I >= lvl) || I >= n - 2) return true;  // this node starts the interval
             expand(false);
         }
     }
@@ -585,6 +595,7 @@ struct Explorer {
                     de[1 + i] = (uint8_t)X.E[i];
                 }
                 de[0] = (uint8_t)X.etop;
+                if (a.in_level) a.in_level[t] = 0xff;
                 for (int i = 0; i < n; ++i) X.E[i] = q[i];
                 X.etop = 0;
                 atomicAdd(a.active, 1);
@@ -662,6 +673,7 @@ struct Explorer {
             const unsigned long long req = ((unsigned long long)(a.my_inst & 0xffffff) << 40) | (myseq << 20) |
                                            (unsigned long long)me;
             posted = atomicCAS(a.mailbox + best, kNoRequest, req) == kNoRequest;
+            if (posted && a.seq_posted) a.seq_posted[me] = (unsigned)myseq;
         }
         posted = __shfl_sync(PFSP_FULL, posted, 0);
         myseq = __shfl_sync(PFSP_FULL, myseq, 0);
@@ -693,7 +705,11 @@ struct Explorer {
             X.D[i] = ((volatile const uint8_t *)ds)[i];
             X.E[i] = ((volatile const uint8_t *)de)[1 + i];
         }
-        if (lane == 0) X.etop = ((volatile const uint8_t *)de)[0];
+        if (lane == 0) {
+            X.etop = ((volatile const uint8_t *)de)[0];
+            X.lvl = -1;
+            if (a.seq_taken) a.seq_taken[me] = (unsigned)myseq;
+        }
         __syncwarp();
         // never index with digits that are not a valid factoradic number
         bool bad = false;
@@ -808,6 +824,37 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
         ex.tick(kPhIdle);
     }
     ex.flush_limits();
+    // stopped at a limit with work left: record the rest of the interval so
+    // that a later launch resumes exactly where this one stopped
+    if (a.ckpt && state != 0 && (ld_volatile(a.stop) == 1 || ld_volatile(a.stop) == 2)) {
+        int lvl = -1;
+        bool rec = false;
+        if (state == 1) {
+            rec = true;
+            lvl = X.lvl;
+        } else {
+            if (!have_node) have_node = ex.select();
+            if (have_node && ex.pos_before_end()) {
+                rec = true;
+                lvl = ex.I;
+                for (int i = lane; i < a.n; i += 32) X.D[i] = i <= ex.I ? X.V[i] : 0;
+                __syncwarp();
+            }
+        }
+        uint8_t *rp = a.ckpt + (size_t)me * kCkptRecord;
+        if (rec) {
+            for (int i = lane; i < 64; i += 32) {
+                rp[4 + i] = (uint8_t)(i < a.n ? X.D[i] : 0);
+                rp[68 + i] = (uint8_t)(i < a.n ? X.E[i] : 0);
+            }
+            if (lane == 0) {
+                rp[1] = (uint8_t)(lvl < 0 ? 0xff : lvl);
+                rp[2] = (uint8_t)X.etop;
+                rp[0] = 1;
+            }
+        }
+        __syncwarp();
+    }
     ex.publish_length(false);
     ex.tick(kPhService);
     if (lane == 0 && a.phase) {
@@ -820,6 +867,7 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
         atomicAdd(a.counters + 3, ex.st.pruned);
         atomicAdd(a.counters + 4, ex.st.steals);
         atomicAdd(a.counters + 5, ex.st.iters);
+        atomicAdd(a.counters + 7, ex.st.slots);
     }
 }
 

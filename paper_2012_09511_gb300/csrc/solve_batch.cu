@@ -69,6 +69,7 @@ __device__ inline void opening_interval(int n, int W, int w, ExplorerSmem &X) {
         X.E[i] = 0;
     }
     X.etop = 0;
+    X.lvl = -1;
     int L = 0;
     long long PL = 1;
     while (L < n && PL < W) {
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
                     X.E[q] = 0;
                 }
                 X.etop = 0;
+                X.lvl = -1;
             }
             b.len_est[me] = -1.0f;
             __threadfence();

@@ -87,8 +87,28 @@ struct TraceRequest {
     int64_t *count;
 };
 
+// Checkpoint buffer (pfsp_solve_resumable): this header, then `count`
+// explorer records of kCkptRecord bytes (layout in solve_internal.h).
+struct CkptHeader {
+    char magic[8];       // "PFSPCKP1"
+    int32_t n, m, bound, branching;
+    int32_t cap;         // the first segment's initial incumbent (capped MinMin and early exit)
+    int32_t ub;          // incumbent (exclusive) when the segment stopped
+    int32_t count;       // records that follow
+    int32_t have_perm;   // 1: best_perm is a schedule of makespan ub
+    uint8_t best_perm[64];
+};
+static const char kCkptMagic[8] = {'P', 'F', 'S', 'P', 'C', 'K', 'P', '1'};
+
+struct ResumeIO {
+    const uint8_t *resume;  // NULL: start from the whole tree
+    int64_t resume_bytes;
+    uint8_t **ckpt;         // NULL: record nothing
+    int64_t *ckpt_bytes;
+};
+
 static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, const TraceRequest *tr,
-                      int32_t *best_cmax, int32_t *best_perm, int *outcome) {
+                      const ResumeIO *rio, int32_t *best_cmax, int32_t *best_perm, int *outcome) {
     pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
     if (!inst || !opt || !best_cmax || !outcome) return set_error(PFSP_ERR_INVALID, "NULL argument");
     if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
@@ -112,11 +132,33 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const int n = inst->n, m = inst->m;
     const TableLayout &L = inst->lay;
 
+    // a resumed checkpoint: its header fixes the incumbent and the cap
+    CkptHeader rh;
+    memset(&rh, 0, sizeof(rh));
+    const bool resuming = rio && rio->resume;
+    if (resuming) {
+        if (rio->resume_bytes < (int64_t)sizeof(CkptHeader))
+            return set_error(PFSP_ERR_INVALID, "checkpoint shorter than its header");
+        memcpy(&rh, rio->resume, sizeof(rh));
+        if (memcmp(rh.magic, kCkptMagic, 8) != 0) return set_error(PFSP_ERR_INVALID, "not a pfsp checkpoint");
+        if (rh.n != n || rh.m != m) return set_error(PFSP_ERR_INVALID, "checkpoint of a %d x %d instance", rh.n, rh.m);
+        if (rh.bound != opt->bound || rh.branching != opt->branching)
+            return set_error(PFSP_ERR_INVALID, "checkpoint taken with another bound or branching rule");
+        if (rh.count < 0 || rio->resume_bytes != (int64_t)sizeof(CkptHeader) + (int64_t)rh.count * kCkptRecord)
+            return set_error(PFSP_ERR_INVALID, "checkpoint size does not match its record count");
+    }
+
     // incumbent: exclusive; INT32_MAX means "start from the NEH schedule"
     std::vector<int> neh_perm;
     int ub0 = opt->init_ub;
     bool from_neh = false;
-    if (ub0 == INT32_MAX) {
+    if (resuming) {
+        ub0 = rh.ub;
+        if (rh.have_perm) {
+            from_neh = true;  // a schedule of makespan ub0 is known (returned if nothing better is found)
+            neh_perm.assign(rh.best_perm, rh.best_perm + n);
+        }
+    } else if (ub0 == INT32_MAX) {
         ub0 = neh(n, m, inst->p_host, neh_perm);
         from_neh = true;
     }
@@ -136,7 +178,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.off_ptab = L.off_ptab;
     a.bound = opt->bound;
     a.capped = opt->branching == PFSP_MINMIN_CAPPED;
-    a.cap = ub0;
+    a.cap = resuming ? rh.cap : ub0;
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
     // the network's inference image: every output column when it orders the
     // LB2 slots, else only the descend-first column (one 16-column tile)
@@ -207,7 +249,29 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         if (e == PL) he[(size_t)i * 65] = 1;
         else digits(e, &he[(size_t)i * 65 + 1]);
     }
-    const int active0 = (int)Kp;
+    std::vector<uint8_t> hl((size_t)K, 0xff);
+    int active0 = (int)Kp;
+    if (resuming) {
+        if (rh.count > K)
+            return set_error(PFSP_ERR_UNSUPPORTED, "checkpoint holds %d intervals, this launch has %d explorers",
+                             rh.count, K);
+        std::fill(hs.begin(), hs.end(), 0);
+        std::fill(he.begin(), he.end(), 0);
+        const uint8_t *rec = rio->resume + sizeof(CkptHeader);
+        for (int i = 0; i < rh.count; ++i, rec += kCkptRecord) {
+            for (int q = 0; q < n; ++q) {
+                if (rec[4 + q] >= n - q || rec[68 + q] >= n - q)
+                    return set_error(PFSP_ERR_INVALID, "checkpoint record %d holds an invalid digit", i);
+                hs[(size_t)i * 64 + q] = rec[4 + q];
+                he[(size_t)i * 65 + 1 + q] = rec[68 + q];
+            }
+            if (rec[1] != 0xff && rec[1] > n - 2)
+                return set_error(PFSP_ERR_INVALID, "checkpoint record %d holds an invalid level", i);
+            he[(size_t)i * 65] = rec[2] ? 1 : 0;
+            hl[(size_t)i] = rec[1];
+        }
+        active0 = rh.count;
+    }
 
     // device state, one allocation
     size_t off = 0;
@@ -220,6 +284,9 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const size_t o_is = take((size_t)K * 64), o_ie = take((size_t)K * 65);
     const size_t o_mb = take((size_t)K * 8), o_rs = take((size_t)K * 8), o_le = take((size_t)K * 4);
     const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64), o_ph = take(8 * kPhases);
+    const size_t o_lv = take((size_t)K), o_sp = take((size_t)K * 4), o_sq = take((size_t)K * 4);
+    const bool want_ckpt = rio && rio->ckpt;
+    const size_t o_ck = take(want_ckpt ? (size_t)K * kCkptRecord : 0);
     const int64_t tcap = tr ? tr->capacity : 0;
     const size_t o_tp = take((size_t)tcap * n), o_t1 = take((size_t)tcap), o_t2 = take((size_t)tcap),
                  o_tc = take(8);
@@ -239,8 +306,12 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.response = (unsigned long long *)(b + o_rs);
     a.len_est = (float *)(b + o_le);
     a.best_perm = (uint8_t *)(b + o_bp);
+    a.in_level = (uint8_t *)(b + o_lv);
+    a.seq_posted = (unsigned *)(b + o_sp);
+    a.seq_taken = (unsigned *)(b + o_sq);
+    a.ckpt = want_ckpt ? (uint8_t *)(b + o_ck) : nullptr;
     a.counters = (unsigned long long *)(b + o_ct);
-    a.phase = (unsigned long long *)(b + o_ph);
+    a.phase = opt->phase_timers ? (unsigned long long *)(b + o_ph) : nullptr;
     int *sc = (int *)(b + o_sc);  // active, ub, stop, err, best_key (8 bytes at +16)
     a.active = sc + 0;
     a.ub = sc + 1;
@@ -274,10 +345,14 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (e == cudaSuccess) e = cudaMemsetAsync(a.response, 0, (size_t)K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.len_est, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counters, 0, 64, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.phase, 0, 8 * kPhases, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_ph, 0, 8 * kPhases, st);
     if (e == cudaSuccess && tcap > 0) e = cudaMemsetAsync(a.trace_count, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_start, hs.data(), hs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_end, he.data(), he.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_level, hl.data(), hl.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.seq_posted, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.seq_taken, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess && want_ckpt) e = cudaMemsetAsync(a.ckpt, 0, (size_t)K * kCkptRecord, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc, hsc, sizeof(hsc), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess) e = launch_solve(a, blocks, warps, smem, st);
@@ -286,7 +361,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     unsigned long long cnt[8], ph[kPhases];
     if (e == cudaSuccess) e = cudaMemcpyAsync(rsc, sc, sizeof(rsc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, a.counters, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ph, a.phase, sizeof(ph), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ph, b + o_ph, sizeof(ph), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
@@ -316,6 +391,60 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         else if (from_neh)
             for (int j = 0; j < n; ++j) best_perm[j] = neh_perm[j];
     }
+    if (want_ckpt) {
+        *rio->ckpt = nullptr;
+        *rio->ckpt_bytes = 0;
+    }
+    if (want_ckpt && (rsc[2] == 1 || rsc[2] == 2)) {
+        // the explorers' own records, plus intervals granted to thieves that
+        // stopped before taking them in (their answer sits in the response slot)
+        std::vector<uint8_t> rec((size_t)K * kCkptRecord), ins((size_t)K * 64), ine((size_t)K * 65), inl((size_t)K);
+        std::vector<unsigned long long> resp((size_t)K);
+        std::vector<unsigned> sp((size_t)K), sq((size_t)K);
+        e = cudaMemcpy(rec.data(), a.ckpt, rec.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ins.data(), a.in_start, ins.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ine.data(), a.in_end, ine.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(inl.data(), a.in_level, inl.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(resp.data(), a.response, resp.size() * 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sp.data(), a.seq_posted, sp.size() * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sq.data(), a.seq_taken, sq.size() * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "checkpoint readback: %s", cudaGetErrorString(e));
+        std::vector<uint8_t> out;
+        for (int t = 0; t < K; ++t) {
+            const uint8_t *r = &rec[(size_t)t * kCkptRecord];
+            if (r[0]) out.insert(out.end(), r, r + kCkptRecord);
+            const unsigned long long v = resp[t];
+            if ((v & 3ull) == 1ull && (unsigned)(v >> 2) == sp[t] && sq[t] != sp[t]) {
+                uint8_t g[kCkptRecord];
+                memset(g, 0, sizeof(g));
+                g[0] = 1;
+                g[1] = inl[t];
+                g[2] = ine[(size_t)t * 65];
+                memcpy(g + 4, &ins[(size_t)t * 64], 64);
+                memcpy(g + 68, &ine[(size_t)t * 65 + 1], 64);
+                out.insert(out.end(), g, g + kCkptRecord);
+            }
+        }
+        CkptHeader h;
+        memset(&h, 0, sizeof(h));
+        memcpy(h.magic, kCkptMagic, 8);
+        h.n = n;
+        h.m = m;
+        h.bound = opt->bound;
+        h.branching = opt->branching;
+        h.cap = a.cap;
+        h.ub = final_ub;
+        h.count = (int32_t)(out.size() / kCkptRecord);
+        h.have_perm = (found || from_neh) ? 1 : 0;
+        for (int j = 0; j < n; ++j) h.best_perm[j] = (uint8_t)(found ? bp[j] : (from_neh ? neh_perm[j] : 0xff));
+        const size_t bytes = sizeof(h) + out.size();
+        uint8_t *buf = (uint8_t *)malloc(bytes);
+        if (!buf) return set_error(PFSP_ERR_OOM, "host allocation of the checkpoint failed");
+        memcpy(buf, &h, sizeof(h));
+        if (!out.empty()) memcpy(buf + sizeof(h), out.data(), out.size());
+        *rio->ckpt = buf;
+        *rio->ckpt_bytes = (int64_t)bytes;
+    }
     if (tcap > 0) {
         unsigned long long tc = 0;
         e = cudaMemcpy(&tc, a.trace_count, 8, cudaMemcpyDeviceToHost);
@@ -333,6 +462,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     inst->stats.pruned = cnt[3];
     inst->stats.steals = cnt[4];
     inst->stats.iterations = cnt[5];
+    inst->stats.lb2_slots = cnt[7];
     inst->stats.kernel_seconds = ms * 1e-3;
     inst->stats.final_ub = final_ub;
     inst->stats.explorers = K;
@@ -343,8 +473,19 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
 
 int pfsp_solve(const pfsp_instance *inst, const pfsp_options *opt, int32_t *best_cmax, int32_t *best_perm,
                int *outcome) {
-    return solve_impl(inst, opt, nullptr, best_cmax, best_perm, outcome);
+    return solve_impl(inst, opt, nullptr, nullptr, best_cmax, best_perm, outcome);
 }
+
+int pfsp_solve_resumable(const pfsp_instance *inst, const pfsp_options *opt, const uint8_t *resume,
+                         int64_t resume_bytes, uint8_t **checkpoint, int64_t *checkpoint_bytes, int32_t *best_cmax,
+                         int32_t *best_perm, int *outcome) {
+    if (resume && resume_bytes <= 0) return set_error(PFSP_ERR_INVALID, "resume buffer without a size");
+    if (checkpoint && !checkpoint_bytes) return set_error(PFSP_ERR_INVALID, "checkpoint_bytes is NULL");
+    ResumeIO rio{resume, resume_bytes, checkpoint, checkpoint_bytes};
+    return solve_impl(inst, opt, nullptr, &rio, best_cmax, best_perm, outcome);
+}
+
+void pfsp_free_checkpoint(uint8_t *checkpoint) { free(checkpoint); }
 
 int pfsp_solve_trace(const pfsp_instance *inst, const pfsp_options *opt, int64_t capacity, int stride,
                      uint8_t *perm, uint8_t *d1, uint8_t *d2, int64_t *count, int32_t *best_cmax, int *outcome) {
@@ -352,7 +493,7 @@ int pfsp_solve_trace(const pfsp_instance *inst, const pfsp_options *opt, int64_t
         return set_error(PFSP_ERR_INVALID, "bad trace buffers");
     TraceRequest tr{capacity, stride, perm, d1, d2, count};
     *count = 0;
-    return solve_impl(inst, opt, &tr, best_cmax, nullptr, outcome);
+    return solve_impl(inst, opt, &tr, nullptr, best_cmax, nullptr, outcome);
 }
 
 }  // extern "C"

@@ -22,7 +22,9 @@ constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
 #define PFSP_FWD_DIR 0
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
-// (pfsp_stats_t.phase_cycles).
+// (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
+// clock costs enough that a timed solve runs several times slower, so they
+// are off unless asked for.
 constexpr int kPhService = 0;  // limit checks, steal requests answered, length publication
 constexpr int kPhSelect = 1;   // next live cell, backtracking, interval-end check
 constexpr int kPhDecode = 2;   // node decoding into [sigma1 | unscheduled | sigma2]
@@ -32,6 +34,12 @@ constexpr int kPhBranch = 5;   // MinMin, pruning, the new row, leaves (and the 
 constexpr int kPhInit = 6;     // rebuilding the path to a new interval's start
 constexpr int kPhIdle = 7;     // stealing and waiting without work
 constexpr int kPhases = 8;
+
+// Checkpoint record of one explorer (device and host): [0] valid, [1] start
+// level (0xff: the first level below which the start digits are all zero),
+// [2] coefficient of n! of the end, [3] unused, [4..67] start digits,
+// [68..131] end digits.
+constexpr int kCkptRecord = 132;
 
 struct SolveArgs {
     // instance tables (same layout as the bounding kernel)
@@ -54,6 +62,10 @@ struct SolveArgs {
     uint8_t *inst_perm;   // batched solves: [64] recorded permutation (NULL: per-explorer slots)
     uint8_t *in_start;    // [K][64] start digits of an incoming interval
     uint8_t *in_end;      // [K][65] end: [0] = coefficient of n!, [1..n] digits
+    uint8_t *in_level;    // [K] start level of an incoming interval (0xff: first zero-rest level), or NULL
+    unsigned *seq_posted; // [K] sequence number of each explorer's last posted steal request (or NULL)
+    unsigned *seq_taken;  // [K] sequence number of the last answer it took in (or NULL)
+    uint8_t *ckpt;        // [K][kCkptRecord] remaining interval of each explorer at a limit stop (NULL: off)
     unsigned long long *mailbox;   // [K] request: instance << 40 | sequence << 20 | thief, or kNoRequest
     unsigned long long *response;  // [K] answer to a thief: sequence << 2 | 1 granted / 2 denied
     float *len_est;       // [K] log2 of the remaining interval length, -1 if empty
@@ -61,8 +73,8 @@ struct SolveArgs {
     int *ub;              // incumbent (exclusive)
     unsigned long long *best_key;  // (cmax << 32) | explorer
     uint8_t *best_perm;   // [K][64]
-    unsigned long long *counters;  // decomposed, bounded, leaves, pruned, steals, iters, limit count
-    unsigned long long *phase;     // [kPhases] cycles per phase summed over explorers (NULL: not reported)
+    unsigned long long *counters;  // decomposed, bounded, leaves, pruned, steals, iters, limit count, LB2 slots
+    unsigned long long *phase;     // [kPhases] cycles per phase summed over explorers (NULL: timers off)
     long long node_limit;
     unsigned long long time_limit_ns;  // stop after this long on the device clock; 0 = none
     int *stop;            // 0 run, 1 node limit, 2 time limit, 3 error

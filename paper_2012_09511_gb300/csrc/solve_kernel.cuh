@@ -44,6 +44,8 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
     if (lane == 0) {
         X.etop = a.in_end[(size_t)me * 65];
         X.seq = 0;
+        const int lv = a.in_level ? a.in_level[me] : 0xff;
+        X.lvl = lv == 0xff ? -1 : lv;
     }
     __syncwarp();
     run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_words ? &net : nullptr);

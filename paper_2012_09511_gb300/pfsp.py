@@ -47,7 +47,7 @@ class pfsp_stats_t(ctypes.Structure):
                 ("leaves", ctypes.c_uint64), ("pruned", ctypes.c_uint64), ("steals", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("final_ub", ctypes.c_int32),
-                ("explorers", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8)]
+                ("explorers", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8), ("lb2_slots", ctypes.c_uint64)]
 
     PHASES = ("service", "select", "decode", "lb1", "lb2", "branch", "init", "idle")
 
@@ -66,7 +66,8 @@ class pfsp_options(ctypes.Structure):
     _fields_ = [("init_ub", ctypes.c_int32), ("node_limit", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
                 ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
-                ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("phase_timers", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -126,6 +127,12 @@ _lib.pfsp_mlp_rows.restype = ctypes.c_int
 _lib.pfsp_mlp_rows.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.pfsp_stats.restype = ctypes.c_int
 _lib.pfsp_stats.argtypes = [_vp, ctypes.POINTER(pfsp_stats_t)]
+_lib.pfsp_solve_resumable.restype = ctypes.c_int
+_lib.pfsp_solve_resumable.argtypes = [_vp, ctypes.POINTER(pfsp_options), _vp, ctypes.c_int64, ctypes.POINTER(_vp),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]
+_lib.pfsp_free_checkpoint.restype = None
+_lib.pfsp_free_checkpoint.argtypes = [_vp]
 _lib.pfsp_set_pair_order.restype = ctypes.c_int
 _lib.pfsp_set_pair_order.argtypes = [_vp, _vp]
 _lib.pfsp_get_pair_order.restype = ctypes.c_int
@@ -438,3 +445,25 @@ def pfsp_learn_pair_order(inst: Instance, mlp: Mlp, perm, d1, d2) -> np.ndarray:
     out = np.empty(max(1, inst.m * (inst.m - 1) // 2), dtype=np.int32)
     _check(_lib.pfsp_learn_pair_order(inst.handle, mlp.handle, len(d1), _ptr(perm), _ptr(d1), _ptr(d2), _ptr(out)))
     return out[:inst.m * (inst.m - 1) // 2]
+
+
+def pfsp_solve_resumable(inst: Instance, resume: bytes = None, opts: pfsp_options = None, **fields) -> dict:
+    """One segment of a resumable solve; returns dict(cmax, perm, outcome, checkpoint, **stats), where
+    checkpoint is the bytes to resume from (None once the search has finished)."""
+    if opts is None:
+        opts = pfsp_default_options(**fields)
+    best = ctypes.c_int32()
+    out = ctypes.c_int()
+    perm = (ctypes.c_int32 * inst.n)(*([-1] * inst.n))
+    ck = _vp()
+    nb = ctypes.c_int64()
+    rb = None if resume is None else ctypes.create_string_buffer(bytes(resume), len(resume))
+    _check(_lib.pfsp_solve_resumable(inst.handle, ctypes.byref(opts), rb, len(resume) if resume else 0,
+                                     ctypes.byref(ck), ctypes.byref(nb), ctypes.byref(best), perm, ctypes.byref(out)))
+    data = None
+    if ck.value:
+        data = ctypes.string_at(ck.value, nb.value)
+        _lib.pfsp_free_checkpoint(ck)
+    r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value, checkpoint=data)
+    r.update(pfsp_stats(inst))
+    return r

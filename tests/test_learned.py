@@ -150,6 +150,24 @@ def test_early_exit_proof_counts_20x10(pf):
             g["proof_decomposed"], g["proof_bounded"], g["proof_pruned"]), g["seed"]
 
 
+def test_early_exit_skips_lb2_slots(pf):
+    # the exit must actually fire: on a 20 x 10 proof (two 32-pair slots per
+    # sweep) a large share of the nodes is decided by LB1 or the first slot
+    g = [r for r in json_golden() if r["seed"] == 1][0]
+    inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, 1))
+    full = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"])
+    ee = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"], learned=pf.PFSP_EARLY_EXIT)
+    assert full["decomposed"] == ee["decomposed"] == g["proof_decomposed"]
+    assert full["lb2_slots"] == 2 * full["decomposed"]  # every node of this tree has children
+    assert ee["lb2_slots"] < 0.8 * full["lb2_slots"], (ee["lb2_slots"], full["lb2_slots"])
+
+
+def json_golden():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "solve_20x10_lb2.json")))["results"]
+
+
 def test_pair_order_changes_no_bound(pf):
     n, m = 14, 10
     p = inputs.make_instance(n, m, 21)
