@@ -101,3 +101,34 @@ def test_checkpoint_is_bytes_and_is_checked(pf, tmp_path):
         pf.pfsp_solve_resumable(inst, resume=ck, bound=pf.PFSP_LB2, branching=pf.PFSP_MINMIN_CAPPED)
     with pytest.raises(pf.PfspError):  # truncated
         pf.pfsp_solve_resumable(inst, resume=ck[:-5], bound=pf.PFSP_LB2)
+
+
+@pytest.mark.parametrize("workers,seed,limit", [(3, 1, 4000), (2, 8, 20000), (4, 5, 3000)])
+def test_pools_under_the_coordinator_decompose_every_node_once(pf, workers, seed, limit):
+    # several explorer pools (taking turns on this GPU) share the tree through
+    # the work-unit coordinator of Algorithm 1: in proof mode the counters of
+    # all their segments add up to the oracle's counts of the whole tree
+    from paper_2012_09511_gb300 import coordinator as co
+    g = [r for r in json.load(open(GOLDEN))["results"] if r["seed"] == seed][0]
+    inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, seed))
+    ws = [co.PoolWorker(pf, inst, bound=pf.PFSP_LB2, cap=g["optimum"], node_limit=limit) for _ in range(workers)]
+    coord = co.Coordinator(20, ub=g["optimum"])
+    co.solve_with_workers(ws, coord)
+    tot = {k: sum(w.counts[k] for w in ws) for k in ws[0].counts}
+    assert (tot["decomposed"], tot["bounded_children"], tot["pruned"]) == (
+        g["proof_decomposed"], g["proof_bounded"], g["proof_pruned"])
+    assert coord.steals > 0 and coord.ub == g["optimum"] and coord.best_perm is None
+    assert all(w.segments > 1 for w in ws)
+
+
+def test_pools_under_the_coordinator_find_the_optimum(pf):
+    from paper_2012_09511_gb300 import coordinator as co
+    g = [r for r in json.load(open(GOLDEN))["results"] if r["seed"] == 7][0]
+    p = inputs.make_instance(20, 10, 7)
+    inst = pf.pfsp_load_instance(p)
+    ub0 = g["optimum"] + 40
+    ws = [co.PoolWorker(pf, inst, bound=pf.PFSP_LB2, cap=ub0, node_limit=60000) for _ in range(3)]
+    coord = co.Coordinator(20, ub=ub0)
+    co.solve_with_workers(ws, coord)
+    assert coord.ub == g["optimum"]
+    assert sorted(coord.best_perm) == list(range(20)) and orc.makespan(p, coord.best_perm) == g["optimum"]
