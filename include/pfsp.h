@@ -153,14 +153,18 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
 /* Learned-ordering flags (pfsp_options.learned; not in the paper). */
 #define PFSP_LEARN_CHILD_ORDER 1  /* order each new row by the network's descend-first logits */
 #define PFSP_LEARN_PAIR_ORDER 2   /* sweep LB2's 32-pair slots in the order of the network's pair logits */
-#define PFSP_EARLY_EXIT 4         /* skip or stop the LB2 sweep as soon as every child of one
-                                     direction has a bound (its LB1 or a pair term seen) at least the
-                                     solve's initial incumbent: such a node has no child below the
-                                     incumbent under either MinMin rule (the decided direction holds
-                                     no minimum below it, so MinMin picks it), hence the search tree
-                                     and every counter are those of the full sweep.  Best with the
-                                     pairs most likely to decide a child in the first slot
-                                     (pfsp_learn_pair_order). */
+#define PFSP_EARLY_EXIT 4         /* skip the LB2 sweep of a node when every child of one direction
+                                     has an LB1 at least the solve's initial incumbent: such a node
+                                     has no child below the incumbent under either MinMin rule (the
+                                     decided direction holds no minimum below it, so MinMin picks
+                                     it), hence the search tree and every counter are those of the
+                                     full sweep */
+#define PFSP_EARLY_EXIT_SLOTS 8   /* with PFSP_EARLY_EXIT: also stop the sweep after the first
+                                     32-pair slot at which every child of one direction has a pair
+                                     term at least the incumbent (same exactness argument); pairs in
+                                     the instance's order (pfsp_learn_pair_order puts the pairs most
+                                     likely to decide first).  The check after each slot costs
+                                     about as much as it saves on the pools measured so far. */
 
 typedef struct {
     int32_t init_ub;

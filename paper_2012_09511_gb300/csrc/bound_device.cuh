@@ -385,7 +385,7 @@ __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *
 // walks keep their records in registers (u <= kRegWalk).
 template <int NW, int MT, int NC, bool RW>
 __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                         ChildBounds<NW> &out, int cap, const int *order) {
+                                         ChildBounds<NW> &out, int cap, bool slot_checks, const int *order) {
     using mask_t = umask_t<NW>;
     constexpr bool REGACC = NC > 0;
     const int m = MT ? MT : m_rt;
@@ -485,11 +485,9 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
                 W.Acc[c * 32 + lane] = v;
             }
         }
-        if (cap != INT_MAX && si + 1 < S && S >= 4) {
+        if (slot_checks && cap != INT_MAX && si + 1 < S) {
             // every child of one direction decided? (its LB1 or some pair
-            // term already >= cap).  Checked between slots only when several
-            // slots remain to be saved: with two slots (m <= 11) the check
-            // costs about what the second slot would.
+            // term already >= cap)
             mask_t mf = 0, mb = 0;
             if constexpr (REGACC) {
 #pragma unroll
@@ -555,9 +553,10 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
 
 // LB2 phase: lanes = machine pairs, S slots of 32 pairs.  Needs the tables
 // written by decompose_lb1.  `order` (may be NULL) gives the order in which
-// the slots are swept.  With cap < INT_MAX the sweep stops (or is skipped)
-// as soon as every child of one direction is known to have a bound >= cap
-// (its LB1 or a pair term already seen reaches cap).  The values returned are
+// the slots are swept.  With cap < INT_MAX the sweep is skipped when every
+// child of one direction has an LB1 >= cap, and, with slot_checks, stopped
+// after the first slot at which every child of one direction has a bound
+// known to be >= cap (its LB1 or a pair term already seen reaches cap).  The values returned are
 // then lower bounds of the children's LB2 (each is the LB1 or the largest pair
 // term seen).  Such a node has no child below cap in either MinMin rule: the
 // decided direction holds no minimum below cap, so it is chosen whenever the
@@ -568,11 +567,12 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
 // Returns the number of 32-pair slots swept (fewer than S after an early exit).
 template <int NW, int MT, int WALK = 0>
 __device__ __forceinline__ int decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                             ChildBounds<NW> &out, int cap, const int *order) {
+                                             ChildBounds<NW> &out, int cap, bool slot_checks, const int *order) {
     if (out.u == 0 || (MT ? MT : m_rt) < 2) return 0;
     static_assert(WALK == 0 || NW == 1, "register walks need n <= 32");
-    if constexpr (WALK == 1) return lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, order);
-    else return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, order);
+    if constexpr (WALK == 1)
+        return lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order);
+    else return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order);
 }
 
 // Both phases: the bounds of all 2u children of the node.
@@ -582,7 +582,7 @@ __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpSc
                                                ChildBounds<NW> &out) {
     decompose_lb1<NW, MT>(T, W, n, m_rt, kind, job0, job1, d1, d2, out);
     if ((kind & PFSP_LB2) && (MT ? MT : m_rt) >= 2)
-        decompose_lb2<NW, MT, WALK>(T, W, n, m_rt, S_rt, out, INT_MAX, nullptr);
+        decompose_lb2<NW, MT, WALK>(T, W, n, m_rt, S_rt, out, INT_MAX, false, nullptr);
 }
 
 // Stage `words` int32 (a multiple of 4, 16-byte aligned on both sides) from

@@ -57,7 +57,7 @@ struct Explorer {
     const SmemTables &T;
     const WarpScratch &W;
     ExplorerSmem &X;
-    const MlpImage *net;  // the network's image staged in shared memory (NULL: plain solver)
+    const MlpImage *net;  // view of the network's image in global memory (NULL: plain solver)
     int n, m, S, lane, me;
     uint8_t *rj;
     int32_t *rl;
@@ -397,8 +397,9 @@ struct Explorer {
                     order = X.sorder;
                 }
             }
-            const int swept =
-                decompose_lb2<NW, MT>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX, order);
+            const int swept = decompose_lb2<NW, MT>(T, W, n, m, S, cb,
+                                                    (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
+                                                    (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order);
             if (counted) st.slots += swept;
         }
         tick(counted ? kPhLB2 : kPhInit);

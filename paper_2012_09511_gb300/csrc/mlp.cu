@@ -121,19 +121,18 @@ cudaError_t mlp_build_image(const pfsp_mlp *M, int O3, void *dst, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Forward pass with the fused inference path that the solver uses: each CTA
-// copies the image into shared memory, each warp runs 16-row tiles.
+// Forward pass with the fused inference path that the solver uses: the
+// weights are read from the image in global memory, each warp runs 16-row
+// tiles with its activations in its own shared-memory scratch.
 template <int KT1>
 __global__ void mlp_forward_kernel(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
                                    float *Y) {
     extern __shared__ __align__(128) unsigned char sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int D0 = 16 * KT1, ldx = D0 + 8;
-    for (int i = threadIdx.x; i < img_bytes / 16; i += blockDim.x)
-        reinterpret_cast<int4 *>(sm)[i] = reinterpret_cast<const int4 *>(img)[i];
-    __syncthreads();
-    const MlpImage P = mlp_image_view(sm, D0, O);
-    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(sm + img_bytes + wib * mlp_scratch_bytes(D0));
+    (void)img_bytes;
+    const MlpImage P = mlp_image_view(img, D0, O);
+    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(sm + wib * mlp_scratch_bytes(D0));
     const int g = lane >> 2, t = lane & 3;
     const long long tiles = (rows + 15) / 16;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -370,7 +369,7 @@ template <int KT1>
 static cudaError_t forward_t(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
                              float *Y) {
     const int warps = 4;
-    const size_t smem = (size_t)img_bytes + warps * mlp_scratch_bytes(16 * KT1);
+    const size_t smem = (size_t)warps * mlp_scratch_bytes(16 * KT1);
     void (*kern)(const unsigned char *, int, int, const float *, long long, float *) = mlp_forward_kernel<KT1>;
     cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

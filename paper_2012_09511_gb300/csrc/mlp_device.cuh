@@ -66,12 +66,14 @@ __device__ inline void mlp_tile_forward(const MlpDev &P, const __nv_bfloat16 *Xs
 // the elements of the next layer's A fragment for k-tile p (rows g and g + 8,
 // columns 2t, 2t + 1 and 8 + 2t, 9 + 2t, g = lane / 4, t = lane % 4), so bias,
 // ReLU and the bf16 rounding are applied in registers and no activation goes
-// through memory.  B fragments come from the staged image by ldmatrix.
+// through memory.  B fragments are read by each thread straight from the
+// image in global memory through the read-only path (the image, about 50 KB,
+// stays in L1/L2; staging it in shared memory would cost explorer warps).
 //
-// The image (one CTA's copy in shared memory, built by mlp_build_image):
+// The image (in global memory, built by mlp_build_image):
 // W1t [H][D0 + 8], W2t [H][H + 8], W3t [O3][H + 8] bf16, transposed ([out][in])
-// with rows padded by 8 elements so that the eight 16-byte rows one ldmatrix
-// matrix reads start on distinct banks; then b1 [H], b2 [H], b3 [O3] fp32.
+// with rows padded by 8 elements; then b1 [H], b2 [H], b3 [O3] fp32.  Every
+// row and every bias array starts on an 8-byte boundary.
 // O3 (a multiple of 16) output columns are staged: 16 when only the
 // descend-first logit (column 0) is needed, O for the pair head too.
 struct MlpImage {
@@ -124,24 +126,37 @@ __device__ __forceinline__ void mlp_ldsm4(unsigned (&r)[4], const __nv_bfloat16 
                  : "r"(addr));
 }
 
+// B fragments of k-tile kk for the n-tiles 16p..16p+7 (b[0], b[1]) and
+// 16p+8..16p+15 (b[2], b[3]) of transposed weights Wt [N][ldw] in global
+// memory: thread (g, t) takes the bf16 pairs at columns 16kk + 2t and
+// 16kk + 8 + 2t of rows 16p + g and 16p + 8 + g.
+__device__ __forceinline__ void mlp_ldg_b4(unsigned (&b)[4], const __nv_bfloat16 *Wt, int ldw, int p, int kk) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const unsigned *r0 = reinterpret_cast<const unsigned *>(Wt + (size_t)(16 * p + g) * ldw + 16 * kk + 2 * t);
+    const unsigned *r1 = r0 + 4 * ldw;  // 8 rows further (ldw bf16 = ldw / 2 words per row)
+    b[0] = __ldg(r0);
+    b[1] = __ldg(r0 + 4);
+    b[2] = __ldg(r1);
+    b[3] = __ldg(r1 + 4);
+}
+
 // Raw products (no bias) for output columns 16p..16p+15 of a 16-row tile
 // whose KT k-tiles of input come from the shared tile As ([16][lda] bf16,
 // one ldmatrix per k-tile): c0 holds columns 16p + 2t, +1 and c1 columns
 // 16p + 8 + 2t, +1, of rows g ([0], [1]) and g + 8 ([2], [3]).
-// Wt: [N][ldw] transposed weights.
+// Wt: [N][ldw] transposed weights in global memory.
 template <int KT>
 __device__ __forceinline__ void mlp_tile_cols(const __nv_bfloat16 *As, int lda, const __nv_bfloat16 *Wt, int ldw,
                                               int p, float (&c0)[4], float (&c1)[4]) {
     const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
     const __nv_bfloat16 *x = As + (r + 8 * (q & 1)) * lda + 8 * (q >> 1);
-    const __nv_bfloat16 *w = Wt + (16 * p + 8 * (q >> 1) + r) * ldw + 8 * (q & 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) c0[i] = c1[i] = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < KT; ++kk) {
         unsigned av[4], b[4];
         mlp_ldsm4(av, x + 16 * kk);
-        mlp_ldsm4(b, w + 16 * kk);
+        mlp_ldg_b4(b, Wt, ldw, p, kk);
         mlp_mma(c0, av, b[0], b[1]);
         mlp_mma(c1, av, b[2], b[3]);
     }
@@ -159,8 +174,8 @@ __device__ __forceinline__ void mlp_layer_relu(const __nv_bfloat16 *As, int lda,
     for (int p = 0; p < kMlpHidden / 16; ++p) {
         float c0[4], c1[4];
         mlp_tile_cols<KT>(As, lda, Wt, ldw, p, c0, c1);
-        const float2 e0 = *reinterpret_cast<const float2 *>(b + 16 * p + 2 * t);
-        const float2 e1 = *reinterpret_cast<const float2 *>(b + 16 * p + 8 + 2 * t);
+        const float2 e0 = __ldg(reinterpret_cast<const float2 *>(b + 16 * p + 2 * t));
+        const float2 e1 = __ldg(reinterpret_cast<const float2 *>(b + 16 * p + 8 + 2 * t));
         unsigned o[4];
         o[0] = mlp_pack_bf16(fmaxf(c0[0] + e0.x, 0.0f), fmaxf(c0[1] + e0.y, 0.0f));
         o[1] = mlp_pack_bf16(fmaxf(c0[2] + e0.x, 0.0f), fmaxf(c0[3] + e0.y, 0.0f));
@@ -192,10 +207,9 @@ struct MlpFirstCols {
     const __nv_bfloat16 *W3t;
     float (&acc)[4];
     __device__ __forceinline__ void operator()(int p, const unsigned (&o)[4]) const {
-        const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
-        unsigned b[4];
-        mlp_ldsm4(b, W3t + (8 * (q >> 1) + r) * (kMlpHidden + 8) + 16 * p + 8 * (q & 1));
-        mlp_mma(acc, o, b[0], b[1]);
+        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+        const unsigned *r = reinterpret_cast<const unsigned *>(W3t + g * (kMlpHidden + 8) + 16 * p + 2 * t);
+        mlp_mma(acc, o, __ldg(r), __ldg(r + 4));
     }
 };
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
             X[2 * m + lane] = P.y * a.inv_scale;
         }
         if (a.parents_only) continue;
-        decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, nullptr);
+        decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
         const int u = cb.u;
         __syncwarp();
         // children: features, bounds for the pair pass, descend-first targets

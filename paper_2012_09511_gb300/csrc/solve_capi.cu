@@ -118,8 +118,10 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->bound == PFSP_LB2 && !inst->lb2_ok)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
-    if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT))
+    if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT | PFSP_EARLY_EXIT_SLOTS))
         return set_error(PFSP_ERR_INVALID, "unknown bits in learned");
+    if ((opt->learned & PFSP_EARLY_EXIT_SLOTS) && !(opt->learned & PFSP_EARLY_EXIT))
+        return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT_SLOTS needs PFSP_EARLY_EXIT");
     const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
     int net_m = 0, net_D0 = 0, net_O = 0;
     if (use_net) {
@@ -206,11 +208,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int max_warps = use_net ? kSolveWarpsLearned : kSolveWarps;
     int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, max_warps) : max_warps;
-    if (use_net) {
-        // the image is always staged in shared memory (ldmatrix reads it there)
-        a.net_words = img_bytes / 4;
-        a.warp_base = a.net_base + a.net_words;
-    }
+    // the network's image stays in global memory (its weights are read there
+    // by the tensor-core fragments), so it costs no explorer warps
     long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");

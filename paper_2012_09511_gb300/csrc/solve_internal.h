@@ -94,8 +94,8 @@ struct SolveArgs {
     float inv_scale;      // 1 / (mean machine load) for the network's features
     int mlp_off;          // word offset of the network's scratch from the warp's base
     int learn_depth;      // rows of level < learn_depth are ordered by the network
-    int net_base;         // word offset of the staged image in shared memory
-    int net_words;        // words of the staged image (0: no network)
+    int net_base;         // unused (the image is read from global memory)
+    int net_words;        // unused (0)
 };
 
 int solve_warp_words(int n, int m, int bound);

@@ -52,13 +52,13 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
 }
 
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
-    if (a.net_words > 0) return solve_occupancy_learned(a, warps, smem);
+    if (a.net_image) return solve_occupancy_learned(a, warps, smem);
     if (a.n <= 32) { PFSP_DISPATCH(1, false, occupancy_t, warps, smem) }
     PFSP_DISPATCH(2, false, occupancy_t, warps, smem)
 }
 
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    if (a.net_words > 0) return launch_solve_learned(a, blocks, warps, smem, st);
+    if (a.net_image) return launch_solve_learned(a, blocks, warps, smem, st);
     if (a.n <= 32) { PFSP_DISPATCH(1, false, launch_solve_t, a, blocks, warps, smem, st) }
     PFSP_DISPATCH(2, false, launch_solve_t, a, blocks, warps, smem, st)
 }

@@ -28,11 +28,10 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
     WarpScratch W = carve_warp(wbase, a.n, a.m);
     ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
     const int me = blockIdx.x * warps + wib;
-    // the ordering network's inference image, copied once per CTA
+    // the ordering network's inference image (read from global memory)
     __shared__ MlpImage net;
-    if (LEARNED && a.net_words) {
-        stage_tables(smem + a.net_base, reinterpret_cast<const int32_t *>(a.net_image), a.net_words, &bar);
-        if (threadIdx.x == 0) net = mlp_image_view(smem + a.net_base, a.net_D0, a.net_O3);
+    if (LEARNED && a.net_image) {
+        if (threadIdx.x == 0) net = mlp_image_view(a.net_image, a.net_D0, a.net_O3);
         __syncthreads();
     }
     if (me >= a.K) return;
@@ -48,7 +47,7 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
         X.lvl = lv == 0xff ? -1 : lv;
     }
     __syncwarp();
-    run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_words ? &net : nullptr);
+    run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_image ? &net : nullptr);
 }
 
 template <int NW, int MT, bool LEARNED>

@@ -6,13 +6,15 @@ the training rows on the GPU, pfsp_mlp_train trains the network on the GPU,
 pfsp_learn_pair_order ranks the machine pairs with the network, and
 pfsp_solve runs the plain and the learned solvers.
 
-The learned solver sweeps LB2's machine pairs in the network's order (per
-instance, from a short pilot trace), stops a node's sweep as soon as every
-child of one direction is at or above the incumbent (no such node has a child
-below it, so the tree is unchanged), and orders the rows of the first levels
-by the network's descend-first logits.  Its optimum is always the plain
-solver's; the comparison reports the time to the proven optimum (wall time,
-pilot and ranking included) and the decomposed-node counts of both.
+The learned solver skips a node's LB2 sweep when every child of one
+direction already has an LB1 at or above the incumbent (no such node has a
+child below it, so the tree is unchanged), and while the incumbent may still
+improve it orders the rows of the first levels by the network's descend-first
+logits.  The network's pair ranking (per instance, from a short pilot trace)
+feeds the optional between-slot checks of the sweep, reported as an ablation.
+Its optimum is always the plain solver's; the comparison reports the time to
+the proven optimum (wall time, pilot and ranking included) and the
+decomposed-node counts of both.
 """
 from __future__ import annotations
 
@@ -62,7 +64,13 @@ def rank_pairs(pfsp, inst, mlp, **pilot_kw):
     """Learned pair order of `inst`: the network's mean pair probabilities over a
     pilot trace, pairs sorted by decreasing score and applied to the instance
     (so that LB2's first 32-pair slot holds the pairs most likely to decide a
-    child).  Returns the order."""
+    child; it matters only with PFSP_EARLY_EXIT_SLOTS).  Instances with fewer
+    than four 32-pair slots (m < 12) are not ranked.  Returns the order, or
+    None when nothing was ranked."""
+    S = (inst.m * (inst.m - 1) // 2 + 31) // 32
+    if S < 4:
+        pfsp.pfsp_set_pair_order(inst, None)
+        return None
     perm, d1, d2 = pilot_nodes(pfsp, inst, **pilot_kw)
     if len(d1) == 0:
         pfsp.pfsp_set_pair_order(inst, None)
@@ -76,20 +84,28 @@ def _run(pfsp, inst, **kw):
     return r, time.perf_counter() - t
 
 
+def learned_options(pfsp, n, proof, mlp, depth=None):
+    """pfsp_solve options of the learned solver: early exit always; when the
+    incumbent may still improve (not proof mode) the network also orders the
+    rows of the first `depth` levels (default n / 4).  In proof mode the tree
+    is fixed by the incumbent, so row order cannot change it and is left out."""
+    if proof:
+        return dict(learned=pfsp.PFSP_EARLY_EXIT)
+    return dict(learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
+                learn_depth=depth or max(1, n // 4))
+
+
 def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
     """Plain and learned solves of one instance (LB2), from its NEH schedule or,
     with init_ub, in proof mode.
 
     plain: the full-pair LB2 solver, pairs in index order.
-    learned: a pilot trace ranks the pairs with the network (pfsp_learn_pair_order),
-    then the solve stops each LB2 sweep as soon as one direction's children are
-    all at or above the incumbent, and the network orders the rows of the first
-    `depth` levels (depth = depths[0], default n / 3).  Its wall time includes the
-    pilot and the ranking.
-    Ablations: early exit with the index pair order (no network), early exit with
-    the learned pair order only, and the network's row order alone per depth."""
+    learned: learned_options().  Ablations: early exit alone, early exit plus
+    the network's row order at each depth of `depths` (finding mode), and for
+    m >= 12 the between-slot checks with the network's pair order (wall time
+    including the pilot trace and the ranking)."""
     n = p.shape[0]
-    depths = depths or [max(1, n // 3)]
+    depths = depths or [max(1, n // 4)]
     inst = pfsp.pfsp_load_instance(p)
     base = dict(bound=2, time_limit_s=time_limit_s)
     if init_ub is not None:
@@ -99,26 +115,30 @@ def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
     def record(name, r, wall, extra_wall=0.0):
         out[name] = {"cmax": r["cmax"], "outcome": r["outcome"], "seconds": r["kernel_seconds"],
                      "wall_seconds": wall + extra_wall, "decomposed": r["decomposed"],
-                     "bounded": r["bounded_children"]}
+                     "bounded": r["bounded_children"], "lb2_slots": r["lb2_slots"]}
 
     pfsp.pfsp_set_pair_order(inst, None)
     record("plain", *_run(pfsp, inst, **base))
     record("early_exit_index_order", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base))
-    for d in depths:
-        record("child_order_depth_%d" % d,
-               *_run(pfsp, inst, learned=pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp, learn_depth=d, **base))
+    if init_ub is None:
+        for d in depths:
+            record("child_order_depth_%d" % d,
+                   *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
+                         learn_depth=d, **base))
+    record("learned", *_run(pfsp, inst, **learned_options(pfsp, n, init_ub is not None, mlp, depths[0]), **base))
     t = time.perf_counter()
-    rank_pairs(pfsp, inst, mlp)
-    t_rank = time.perf_counter() - t
-    record("early_exit_learned_pairs", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base), extra_wall=t_rank)
-    record("learned", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
-                            learn_depth=depths[0], **base), extra_wall=t_rank)
-    out["ranking_wall_seconds"] = t_rank
+    if rank_pairs(pfsp, inst, mlp) is not None:
+        t_rank = time.perf_counter() - t
+        record("early_exit_slots_learned_pairs",
+               *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_EARLY_EXIT_SLOTS, **base),
+               extra_wall=t_rank)
+        out["ranking_wall_seconds"] = t_rank
+    pfsp.pfsp_set_pair_order(inst, None)
     return out
 
 
 def compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), train_seeds=range(1, 11), time_limit_s=30.0,
-            depth_fracs=(3,), proof=False, mlps=None):
+            depth_fracs=(4,), proof=False, mlps=None):
     """Time to the proven optimum, plain vs learned, on the given shapes.
 
     The m-machine network is trained on traces of 20-job instances with the same

@@ -60,6 +60,7 @@ class pfsp_stats_t(ctypes.Structure):
 PFSP_LEARN_CHILD_ORDER = 1
 PFSP_LEARN_PAIR_ORDER = 2
 PFSP_EARLY_EXIT = 4
+PFSP_EARLY_EXIT_SLOTS = 8
 
 
 class pfsp_options(ctypes.Structure):

@@ -103,7 +103,7 @@ def test_learned_solver_is_exact(pf, n, m, seed):
     mlp = pf.pfsp_mlp_create(m, seed=seed)  # untrained: exactness must not depend on it
     opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
     capped = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, capped=True)
-    every = pf.PFSP_LEARN_CHILD_ORDER | pf.PFSP_LEARN_PAIR_ORDER | pf.PFSP_EARLY_EXIT
+    every = pf.PFSP_LEARN_CHILD_ORDER | pf.PFSP_LEARN_PAIR_ORDER | pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_SLOTS
     r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, branching=pf.PFSP_MINMIN_CAPPED, mlp=mlp,
                       learned=every)
     assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
@@ -128,11 +128,12 @@ def test_early_exit_keeps_the_tree(pf, n, m, seed):
         pf.pfsp_set_pair_order(inst, order)
         for capped in (False, True):
             want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, capped=capped)
-            r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=pf.PFSP_EARLY_EXIT,
-                              branching=pf.PFSP_MINMIN_CAPPED if capped else pf.PFSP_MINMIN)
-            assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
-            got = (r["decomposed"], r["bounded_children"], r["pruned"])
-            assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, capped)
+            for flags in (pf.PFSP_EARLY_EXIT, pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_SLOTS):
+                r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=flags,
+                                  branching=pf.PFSP_MINMIN_CAPPED if capped else pf.PFSP_MINMIN)
+                assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+                got = (r["decomposed"], r["bounded_children"], r["pruned"])
+                assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, capped, flags)
         f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, learned=pf.PFSP_EARLY_EXIT)
         assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
 
@@ -211,6 +212,8 @@ def test_learned_pair_order_ranks_network_scores(pf):
 def test_learned_options_are_validated(pf):
     p = inputs.make_instance(8, 5, 1)
     inst = pf.pfsp_load_instance(p)
+    with pytest.raises(pf.PfspError):  # slot checks without the early exit
+        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT_SLOTS)
     with pytest.raises(pf.PfspError):  # no network
         pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_LEARN_CHILD_ORDER)
     other = pf.pfsp_mlp_create(10, seed=1)
