@@ -93,9 +93,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; otherwise None."""
+def ncu_summary():
+    """The committed ncu summary of the bounding kernel (DRAM bytes per launch,
+    pipe and issue utilisation), if it was taken on the current kernel source;
+    otherwise None."""
     path = os.path.join(ROOT, "profiles", "bound_kernel_traffic.json")
     try:
         with open(path) as f:
@@ -104,7 +105,7 @@ def ncu_traffic():
         return None
     if t.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return t.get("dram_bytes_per_launch_full")
+    return t
 
 
 def measured_peaks():
@@ -351,7 +352,8 @@ def run_native(args):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = nsm * INT32_LANES_PER_SM_CLK * sm_max * 1e6
     achieved = ops / (launch_ms * 1e-3)
-    traffic = ncu_traffic()
+    ncu = ncu_summary()
+    traffic = ncu.get("dram_bytes_per_launch_full") if ncu else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": slowest_s * 1e3 / args.steps, "higher_is_better": True,
@@ -364,7 +366,9 @@ def run_native(args):
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
                          nsm, INT32_LANES_PER_SM_CLK, sm_max),
-                     "ops_per_launch": ops, "kernel_ms": launch_ms},
+                     "ops_per_launch": ops, "kernel_ms": launch_ms,
+                     "ncu_utilisation": {k: ncu[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct",
+                                                             "lsu_pipe_pct") if k in ncu} if ncu else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
                 "d2h_bytes_per_step": int(2 * N * 2 * n * 4)},
         "gpu_launches": args.steps,

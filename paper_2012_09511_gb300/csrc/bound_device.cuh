@@ -519,18 +519,30 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
             if ((done_f & all) == all || (done_b & all) == all) break;
         }
     }
-    // ---- max over lanes (pairs) per child: transpose through padded rows ------
-    __syncwarp();
-    int2 *X = W.X;  // [u][33], aliases the walk records and Cb
+    // ---- max over lanes (pairs) per child -------------------------------------
     if constexpr (REGACC) {
+        // register accumulators (u <= 32): one warp max-reduction per child
+        // and direction, kept by the child's lane
+        static_assert(NW == 1, "register accumulators hold at most 32 children");
+        int mf = kNegInf, mb = kNegInf;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             if (c >= u) break;
-            X[c * 33 + lane] = make_int2(accf[c], accb[c]);
+            const int xf = __reduce_max_sync(PFSP_FULL, accf[c]);
+            const int xb = __reduce_max_sync(PFSP_FULL, accb[c]);
+            mf = lane == c ? xf : mf;
+            mb = lane == c ? xb : mb;
         }
-    } else {
-        for (int c = 0; c < u; ++c) X[c * 33 + lane] = W.Acc[c * 32 + lane];
+        if (lane < u) {
+            out.lb2f[0] = max(out.lb1f[0], mf);
+            out.lb2b[0] = max(out.lb1b[0], mb);
+        }
+        return swept;
     }
+    // shared accumulators: transpose through padded rows
+    __syncwarp();
+    int2 *X = W.X;  // [u][33], aliases the walk records and Cb
+    for (int c = 0; c < u; ++c) X[c * 33 + lane] = W.Acc[c * 32 + lane];
     __syncwarp();
 #pragma unroll
     for (int h = 0; h < NW; ++h) {
