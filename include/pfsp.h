@@ -94,6 +94,10 @@ void pfsp_free_instance(pfsp_instance *inst);
 int pfsp_bound_batch(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
                      const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out);
 
+/* (pfsp_bound_batch moves the batch in chunks of 262,144 nodes over two CUDA
+ * streams, so that the copies of one chunk overlap the kernel of another; the
+ * overlap is complete with page-locked host buffers.) */
+
 /* Same as pfsp_bound_batch on device buffers, enqueued on `stream`.  Depths
  * are not validated on the device beyond clamping (a node with d1 + d2 > n
  * gets all -1 outputs); the host variant validates them. */

@@ -260,43 +260,77 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
     if (rc != PFSP_OK) return rc;
     auto t0 = std::chrono::steady_clock::now();
     const int n = inst->n;
-    for (int64_t i = 0; i < num_nodes; ++i)
-        if ((int)d1[i] + (int)d2[i] > n)
-            return set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i], n);
+    // one pass over the depths: validation and the children count
+    uint64_t depth_sum = 0;
+    int bad = 0;
+    for (int64_t i = 0; i < num_nodes; ++i) {
+        const int d = (int)d1[i] + (int)d2[i];
+        depth_sum += (uint64_t)d;
+        bad |= d > n;
+    }
+    if (bad)
+        for (int64_t i = 0; i < num_nodes; ++i)
+            if ((int)d1[i] + (int)d2[i] > n)
+                return set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i],
+                                 n);
     if (num_nodes == 0) return PFSP_OK;
-    const size_t in_bytes = (size_t)num_nodes * (n + 2);
-    const size_t out_bytes = (size_t)num_nodes * 2 * n * sizeof(int32_t);
+    // Chunks of the batch alternate between two streams, so that the copies
+    // of one chunk (nodes in, both bound arrays out) overlap the kernel of the
+    // other; each stream reuses its own device buffers in stream order.
+    const int64_t chunk = std::min<int64_t>(num_nodes, kBoundChunk);
+    const int64_t nchunks = (num_nodes + chunk - 1) / chunk;
+    const int nst = nchunks > 1 ? 2 : 1;
+    const size_t in_bytes = (size_t)chunk * (n + 2);
+    const size_t out_bytes = (size_t)chunk * 2 * n * sizeof(int32_t);
     const size_t off_out1 = (in_bytes + 255) & ~(size_t)255;
     const size_t off_out2 = off_out1 + (((kind & PFSP_LB1) ? out_bytes : 0) + 255) / 256 * 256;
-    rc = ensure_scratch(inst, off_out2 + ((kind & PFSP_LB2) ? out_bytes : 0));
+    const size_t per_stream = (off_out2 + ((kind & PFSP_LB2) ? out_bytes : 0) + 255) / 256 * 256;
+    rc = ensure_scratch(inst, per_stream * nst);
     if (rc != PFSP_OK) return rc;
-    char *base = (char *)inst->d_scratch;
-    uint8_t *dperm = (uint8_t *)base;
-    uint8_t *dd1 = dperm + (size_t)num_nodes * n;
-    uint8_t *dd2 = dd1 + num_nodes;
-    int32_t *o1 = (kind & PFSP_LB1) ? (int32_t *)(base + off_out1) : nullptr;
-    int32_t *o2 = (kind & PFSP_LB2) ? (int32_t *)(base + off_out2) : nullptr;
-    cudaStream_t st = 0;
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaError_t e = cudaMemcpyAsync(dperm, perm, (size_t)num_nodes * n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1, num_nodes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2, num_nodes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
-    if (e == cudaSuccess) e = launch_bound_batch(inst, kind, num_nodes, dperm, dd1, dd2, o1, o2, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
-    if (e == cudaSuccess && o1) e = cudaMemcpyAsync(lb1_out, o1, out_bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && o2) e = cudaMemcpyAsync(lb2_out, o2, out_bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStream_t st[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> evs((size_t)nchunks * 2, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < nst && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking);
+    for (size_t q = 0; q < evs.size() && e == cudaSuccess; ++q) e = cudaEventCreate(&evs[q]);
+    for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int q = (int)(c % nst);
+        const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
+        char *base = (char *)inst->d_scratch + per_stream * q;
+        uint8_t *dperm = (uint8_t *)base;
+        uint8_t *dd1 = dperm + (size_t)cn * n;
+        uint8_t *dd2 = dd1 + cn;
+        int32_t *o1 = (kind & PFSP_LB1) ? (int32_t *)(base + off_out1) : nullptr;
+        int32_t *o2 = (kind & PFSP_LB2) ? (int32_t *)(base + off_out2) : nullptr;
+        const size_t ob = (size_t)cn * 2 * n * sizeof(int32_t);
+        e = cudaMemcpyAsync(dperm, perm + (size_t)off * n, (size_t)cn * n, cudaMemcpyHostToDevice, st[q]);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
+        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c], st[q]);
+        if (e == cudaSuccess) e = launch_bound_batch(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
+        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c + 1], st[q]);
+        if (e == cudaSuccess && o1)
+            e = cudaMemcpyAsync(lb1_out + (size_t)off * 2 * n, o1, ob, cudaMemcpyDeviceToHost, st[q]);
+        if (e == cudaSuccess && o2)
+            e = cudaMemcpyAsync(lb2_out + (size_t)off * 2 * n, o2, ob, cudaMemcpyDeviceToHost, st[q]);
+    }
+    for (int q = 0; q < nst; ++q)
+        if (st[q]) {
+            cudaError_t e2 = cudaStreamSynchronize(st[q]);
+            if (e == cudaSuccess) e = e2;
+        }
     float ms = 0.f;
-    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
+    for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, evs[2 * c], evs[2 * c + 1]);
+        ms += t;
+    }
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    for (int q = 0; q < nst; ++q)
+        if (st[q]) cudaStreamDestroy(st[q]);
     if (e != cudaSuccess) return cuda_fail(e, "pfsp_bound_batch");
     memset(&inst->stats, 0, sizeof(inst->stats));
-    uint64_t children = 0;
-    for (int64_t i = 0; i < num_nodes; ++i) children += 2 * (uint64_t)(n - d1[i] - d2[i]);
+    const uint64_t children = 2 * ((uint64_t)num_nodes * (uint64_t)n - depth_sum);
     inst->stats.decomposed = (uint64_t)num_nodes;
     inst->stats.bounded_children = children;
     inst->stats.kernel_seconds = ms * 1e-3;

@@ -17,6 +17,7 @@ constexpr int kNegInf = -(1 << 29);         // "minus infinity" of the max-plus 
 constexpr int kMaxTime = (1 << 22) - 1;     // largest accepted processing time
 constexpr long long kMaxTotal = 1LL << 28;  // largest accepted sum of all times
 constexpr int kMaxTableBytes = 160 * 1024;  // LB2 tables must fit in shared memory
+constexpr long long kBoundChunk = 1 << 18;  // nodes per chunk of the host-pointer bounding pipeline
 
 // Instance tables, one contiguous int32 blob in device memory that every CTA
 // copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):

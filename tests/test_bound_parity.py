@@ -133,3 +133,29 @@ def test_full_benchmark_batch_sampled(pf):
     assert (g2 >= g1).all()
     st = pf.pfsp_stats(inst)
     assert st["bounded_children"] == int(2 * u.sum())
+
+
+def test_host_entry_point_chunks_match_one_launch(pf):
+    # the host-pointer entry point bounds the batch in chunks on two streams;
+    # its outputs must equal one launch of the device entry point everywhere,
+    # and the oracle at the chunk boundaries and in the ragged tail
+    import torch
+    n, m = 14, 6
+    N = 4 * 262144 + 777
+    p = inputs.make_instance(n, m, 33)
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=5, dmax=6)
+    inst = pf.pfsp_load_instance(p)
+    h1, h2 = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    dev = torch.device("cuda:0")
+    o1 = torch.empty((N, 2, n), dtype=torch.int32, device=dev)
+    o2 = torch.empty_like(o1)
+    tp, t1, t2 = (torch.from_numpy(x).to(dev) for x in (perm, d1, d2))
+    pf.pfsp_bound_batch_dev(inst, 3, N, tp.data_ptr(), t1.data_ptr(), t2.data_ptr(), o1.data_ptr(), o2.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert (h1 == o1.cpu().numpy()).all() and (h2 == o2.cpu().numpy()).all()
+    idx = np.concatenate([np.arange(262136, 262152), np.arange(786424, 786440), np.arange(N - 40, N)])
+    r1, r2 = orc.children_bounds_batch(p, perm[idx], d1[idx], d2[idx], threads=8)
+    assert (h1[idx] == r1).all() and (h2[idx] == r2).all()
+    lb1_only, none2 = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
+    assert none2 is None and (lb1_only == h1).all()
