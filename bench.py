@@ -208,6 +208,37 @@ def solve_leg(pfsp, seeds=range(1, 11)):
             "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds)}
 
 
+def batch_leg(pfsp):
+    """The uneven batch: 256 independent instances (n in 12..20, m in {5, 10, 20},
+    times uniform in [1, 99]) solved from NEH in one persistent launch recorded in a
+    CUDA graph, with the autotuner's launch parameters; optima checked against the
+    oracle's where it finished."""
+    from paper_2012_09511_gb300 import inputs
+    path = os.path.join(ROOT, "tests", "golden", "batch256_lb2.json")
+    with open(path) as f:
+        gold = {r["i"]: r for r in json.load(f)["results"]}
+    ps = [inputs.make_instance(*inputs.batch_instance_shape(i), 1000 + i) for i in range(256)]
+    insts = [pfsp.pfsp_load_instance(p) for p in ps]
+    t = time.perf_counter()
+    tuned = pfsp.pfsp_autotune_batch(insts, pfsp.pfsp_default_options(bound=pfsp.PFSP_LB2), sample=32)
+    tune_s = time.perf_counter() - t
+    pfsp.pfsp_solve_batch(insts, tuned)  # warm
+    t = time.perf_counter()
+    r = pfsp.pfsp_solve_batch(insts, tuned)
+    wall = time.perf_counter() - t
+    st = r["stats"]
+    checked = [i for i in range(256) if "optimum" in gold.get(i, {})]
+    match = all(int(r["cmax"][i]) == gold[i]["optimum"] for i in checked)
+    return {"workload": "256 instances, n = 12 + (h_i mod 9), m in {5, 10, 20}, seeds 1000-1255, LB2 + MinMin, "
+                        "from NEH, one launch",
+            "kernel_s": st["kernel_seconds"], "wall_s": wall, "decomposed_nodes": st["decomposed"],
+            "decomposed_nodes_per_s": st["decomposed"] / max(st["kernel_seconds"], 1e-9),
+            "all_optimal": bool((r["outcomes"] == pfsp.PFSP_OPTIMAL).all()),
+            "optima_checked_against_oracle": len(checked), "optima_match_oracle": bool(match),
+            "autotuned": {"warps_per_sm": tuned.warps_per_sm, "check_every": tuned.check_every,
+                          "min_steal": tuned.min_steal, "tuning_s": tune_s}}
+
+
 def learned_leg(pfsp):
     """Learned ordering vs the plain full-pair LB2 solver on n = 50, m = 5 and
     n = 30, m = 10 (5 seeds each): from NEH to the proven optimum, and proving a
@@ -378,6 +409,8 @@ def run_native(args):
         out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample)
     if not args.no_solve and ws == 1:
         out["solve"] = solve_leg(pfsp, seeds=[int(x) for x in args.solve_seeds.split(",") if x])
+    if not args.no_solve and ws == 1:
+        out["batch"] = batch_leg(pfsp)
     if not args.no_learned and ws == 1:
         out["learned"] = learned_leg(pfsp)
     print(json.dumps(out), flush=True)

@@ -68,6 +68,7 @@ struct Explorer {
     unsigned long long deadline;
     long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
     bool timed;        // phase timers on (a.phase != NULL)
+    int ub_seen;       // incumbent read by the last selection
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
                         const MlpImage *net_)
@@ -78,6 +79,11 @@ struct Explorer {
         lane = threadIdx.x & 31;
         rj = a.rows_job + (size_t)me * a.row_stride;
         rl = a.rows_lb + (size_t)me * a.row_stride;
+        if (a.rows_smem) {  // rows in shared memory, right after the explorer state
+            int32_t *rb = reinterpret_cast<int32_t *>(&X_) + kExplorerWords;
+            rl = rb;
+            rj = reinterpret_cast<uint8_t *>(rb + a.n * a.n);
+        }
         I = -1;
         st = Stats{0, 0, 0, 0, 0, 0, 0};
         rng = 0x9e3779b9u * (me + 1) ^ 0x85ebca6bu;
@@ -89,6 +95,7 @@ struct Explorer {
             X.w[i] = w;
         }
         timed = a.phase != nullptr;
+        ub_seen = INT_MAX;
         if (lane < kPhases) X.ph[lane] = 0ull;
         t_mark = timed ? clock64() : 0;
         __syncwarp();
@@ -155,6 +162,7 @@ struct Explorer {
             const int len = n - I;
             const int v = X.V[I];
             const int ubv = ub();
+            ub_seen = ubv;
             unsigned b0 = 0, b1 = 0;
             {
                 int c = lane;
@@ -442,7 +450,7 @@ struct Explorer {
 
         // ---- new row: children of the chosen direction, pruned against UB ------
         const int row = I + 1;
-        int ubv = ub();
+        int ubv = ub_seen;  // the incumbent read by the selection of this node (never below the current one)
         int npruned = 0;
         int pos[NW];
         for (int h = 0; h < NW; ++h) pos[h] = lane + 32 * h;
@@ -525,6 +533,7 @@ struct Explorer {
             zero &= __all_sync(PFSP_FULL, i >= n || X.D[i] == 0);
         }
         const int lvl = X.lvl;
+        ub_seen = ub();
         expand(zero && lvl < 0);  // the root; counted only by the explorer starting at 0
         while (true) {
             // I is the level whose row has just been built; follow the digit D[I]
@@ -555,7 +564,23 @@ struct Explorer {
     __device__ void service(bool active) {
         unsigned long long req = 0;
         if (lane == 0) req = *(volatile unsigned long long *)(a.mailbox + me);
-        req = __shfl_sync(PFSP_FULL, req, 0);
+        service_req(__shfl_sync(PFSP_FULL, req, 0), active);
+    }
+
+    // The stop flag and this explorer's mailbox, read together (one round
+    // trip); returns the stop flag, *req receives the request.
+    __device__ int poll(unsigned long long *req) const {
+        int s = 0;
+        unsigned long long r = 0;
+        if (lane == 0) {
+            s = ld_volatile(a.stop);
+            r = *(volatile unsigned long long *)(a.mailbox + me);
+        }
+        *req = __shfl_sync(PFSP_FULL, r, 0);
+        return __shfl_sync(PFSP_FULL, s, 0);
+    }
+
+    __device__ void service_req(unsigned long long req, bool active) {
         if (req == kNoRequest) return;
         const int t = (int)(req & 0xfffffull);
         const unsigned long long rseq = (req >> 20) & 0xfffffull;
@@ -770,8 +795,9 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
             ex.flush_limits();
             ex.publish_length(state == 2);
         }
-        if (ex.stopped()) break;
-        ex.service(state == 2);
+        unsigned long long req;
+        if (ex.poll(&req)) break;
+        ex.service_req(req, state == 2);
         ex.tick(kPhService);
         if (state == 1) {
             have_node = ex.init_at_start();

@@ -211,9 +211,21 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     // the network's image stays in global memory (its weights are read there
     // by the tensor-core fragments), so it costs no explorer warps
     long long fit = ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)per_warp * 4);
+    // each explorer's rows (jobs and bounds of every level) go to shared
+    // memory, after its explorer state, when that costs no explorer warps:
+    // selection and decoding then read them on chip instead of from L2
+    const int rows_words = solve_row_words(n);
+    long long fit_rows =
+        ((long long)optin - 256 - (long long)a.warp_base * 4) / ((long long)(per_warp + rows_words) * 4);
+    int per_warp_eff = per_warp;
+    if (std::min<long long>(warps, fit_rows) >= std::min<long long>(warps, fit)) {
+        a.rows_smem = 1;
+        per_warp_eff = per_warp + rows_words;
+        fit = fit_rows;
+    }
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
-    size_t smem = (size_t)(a.warp_base + warps * per_warp) * 4;
+    size_t smem = (size_t)(a.warp_base + warps * per_warp_eff) * 4;
     int per_sm = solve_occupancy(a, warps, smem);
     if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "solve kernel cannot be resident (occupancy 0)");
     const int blocks = nsm * per_sm;

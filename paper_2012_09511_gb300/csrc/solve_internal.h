@@ -96,7 +96,12 @@ struct SolveArgs {
     int learn_depth;      // rows of level < learn_depth are ordered by the network
     int net_base;         // unused (the image is read from global memory)
     int net_words;        // unused (0)
+    int rows_smem;        // 1: each explorer's rows live in shared memory after its explorer state
 };
+
+// Words of one explorer's rows in shared memory: bounds [n][n] int32, then
+// jobs [n][n] uint8; a multiple of 8 words.
+__host__ __device__ inline int solve_row_words(int n) { return ((n * n + (n * n + 3) / 4) + 7) & ~7; }
 
 int solve_warp_words(int n, int m, int bound);
 // Network scratch placement for a learned solve: sets *off (words from the

@@ -24,7 +24,8 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
-    int *wbase = smem + a.warp_base + wib * (a.warp_words + kExplorerWords);
+    const int rows_words = a.rows_smem ? solve_row_words(a.n) : 0;
+    int *wbase = smem + a.warp_base + wib * (a.warp_words + kExplorerWords + rows_words);
     WarpScratch W = carve_warp(wbase, a.n, a.m);
     ExplorerSmem &X = *reinterpret_cast<ExplorerSmem *>(wbase + a.warp_words);
     const int me = blockIdx.x * warps + wib;
