@@ -173,7 +173,7 @@ def cpu_baseline(p, perm, d1, d2, sample):
     orc.children_bounds_batch(p, perm[:k], d1[:k], d2[:k], threads=cores)
     dt = time.perf_counter() - t
     children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
-    return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
             "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (k, len(d1), dt)}
 
 
@@ -285,8 +285,9 @@ def run_reference(args):
         r = cpu_baseline(p, perm, d1, d2, sample)
         times.append(r)
     value = statistics.median([t["value"] for t in times])
+    step_ms = statistics.median([t["seconds"] for t in times]) * 1e3
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_MACH, "nodes": args.nodes,
                       "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)"},

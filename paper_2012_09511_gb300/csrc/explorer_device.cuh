@@ -68,7 +68,7 @@ struct Explorer {
     unsigned long long deadline;
     long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
     bool timed;        // phase timers on (a.phase != NULL)
-    int ub_seen;       // incumbent read by the last selection
+    int ub_seen;       // incumbent read at the top of the current iteration
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
                         const MlpImage *net_)
@@ -161,8 +161,7 @@ struct Explorer {
         while (I >= 0) {
             const int len = n - I;
             const int v = X.V[I];
-            const int ubv = ub();
-            ub_seen = ubv;
+            const int ubv = ub_seen;
             unsigned b0 = 0, b1 = 0;
             {
                 int c = lane;
@@ -450,7 +449,7 @@ struct Explorer {
 
         // ---- new row: children of the chosen direction, pruned against UB ------
         const int row = I + 1;
-        int ubv = ub_seen;  // the incumbent read by the selection of this node (never below the current one)
+        int ubv = ub_seen;  // read at the top of this iteration (never below the current incumbent)
         int npruned = 0;
         int pos[NW];
         for (int h = 0; h < NW; ++h) pos[h] = lane + 32 * h;
@@ -540,7 +539,7 @@ struct Explorer {
             const int d = X.D[I];
             if (lane == 0) X.V[I] = d;
             __syncwarp();
-            bool alive = rl[I * n + d] < ub();
+            bool alive = rl[I * n + d] < ub_seen;
             if (!alive) {
                 if (lane == 0) X.V[I] = d + 1;
                 __syncwarp();
@@ -567,16 +566,20 @@ struct Explorer {
         service_req(__shfl_sync(PFSP_FULL, req, 0), active);
     }
 
-    // The stop flag and this explorer's mailbox, read together (one round
-    // trip); returns the stop flag, *req receives the request.
-    __device__ int poll(unsigned long long *req) const {
-        int s = 0;
+    // The stop flag, this explorer's mailbox and the incumbent, read together
+    // (one round trip); returns the stop flag, *req receives the request and
+    // ub_seen the incumbent that this iteration's selection and pruning use
+    // (never below the current one, which only decreases).
+    __device__ int poll(unsigned long long *req) {
+        int s = 0, u = 0;
         unsigned long long r = 0;
         if (lane == 0) {
             s = ld_volatile(a.stop);
             r = *(volatile unsigned long long *)(a.mailbox + me);
+            u = ld_volatile(a.ub);
         }
         *req = __shfl_sync(PFSP_FULL, r, 0);
+        ub_seen = __shfl_sync(PFSP_FULL, u, 0);
         return __shfl_sync(PFSP_FULL, s, 0);
     }
 
