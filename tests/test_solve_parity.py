@@ -143,6 +143,21 @@ def test_limits(pf):
     _check_perm(p, r)
 
 
+def test_phase_timers_and_slot_counter(pf):
+    # the opt-in phase timers fill the cycle counters without changing the
+    # search; without them the counters stay zero.  The LB2 slot counter is
+    # one per decomposition with unscheduled jobs (ceil(45 / 32) = 2 at m = 10).
+    g = [r for r in json.load(open(GOLDEN))["results"] if r["seed"] == 1][0]
+    inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, 1))
+    off = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"])
+    on = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"], phase_timers=1)
+    assert off["decomposed"] == on["decomposed"] == g["proof_decomposed"]
+    assert sum(off["phase_cycles"].values()) == 0
+    ph = on["phase_cycles"]
+    assert ph["lb1"] > 0 and ph["lb2"] > 0 and ph["select"] > 0 and ph["branch"] > 0
+    assert off["lb2_slots"] == on["lb2_slots"] == 2 * g["proof_decomposed"]
+
+
 def test_invalid_options(pf):
     p = inputs.make_instance(8, 4, 1)
     inst = pf.pfsp_load_instance(p)
