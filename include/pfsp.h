@@ -286,7 +286,22 @@ int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp
  * PFSP_ERR_CUDA.
  */
 int pfsp_set_pair_order(pfsp_instance *inst, const int32_t *order);
-/* The instance's current pair order (m(m-1)/2 int32). */
+/*
+ * LB2 over a subset of the machine pairs: Section 2.4 notes that the bound
+ * can use anything between m and all m(m-1)/2 pairs (for instance the m - 1
+ * adjacent pairs (k, k+1), whose indices are k (2m - k - 1) / 2).  After this
+ * call LB2 of the instance (bounding and solves alike) is the largest of LB1
+ * and the values of the `count` pairs listed (distinct indices in the order
+ * of pfsp_set_pair_order), swept in that order.  It is a weaker but valid
+ * lower bound, so solves stay exact; their trees differ from the full LB2's.
+ * pairs NULL restores all pairs in index order.  Same synchronisation as
+ * pfsp_set_pair_order.
+ * Errors: PFSP_ERR_INVALID (NULL instance, m = 1, count outside 1..m(m-1)/2,
+ * repeated or out-of-range index), PFSP_ERR_CUDA.
+ */
+int pfsp_set_lb2_pairs(pfsp_instance *inst, const int32_t *pairs, int count);
+/* The pairs LB2 uses, in sweep order, in the first entries of `order`
+ * (m(m-1)/2 int32); entries past the pairs in use are -1. */
 int pfsp_get_pair_order(const pfsp_instance *inst, int32_t *order);
 
 /* Counters of the last pfsp_bound_batch or pfsp_solve call on `inst`. */

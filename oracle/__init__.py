@@ -82,6 +82,12 @@ def lib():
         L.orc_children_bounds_batch.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int,
                                                 ctypes.c_int64, u8p, u8p, u8p, i32p, i32p,
                                                 ctypes.c_int]
+        L.orc_children_bounds_batch_pairs.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int,
+                                                      ctypes.c_int64, u8p, u8p, u8p, i32p, i32p,
+                                                      ctypes.c_int, i32p, ctypes.c_int]
+        L.orc_bb_solve_pairs.restype = ctypes.c_int
+        L.orc_bb_solve_pairs.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p, i32p, ctypes.c_int]
         L.orc_minmin.restype = ctypes.c_int
         L.orc_minmin.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int32]
         L.orc_bb_solve.restype = ctypes.c_int
@@ -221,7 +227,9 @@ def children_bounds(p, perm, d1, d2, kind=LB1 | LB2):
     return o1.reshape(2, n), o2.reshape(2, n)
 
 
-def children_bounds_batch(p, perm, d1, d2, kind=LB1 | LB2, threads=1):
+def children_bounds_batch(p, perm, d1, d2, kind=LB1 | LB2, threads=1, pairs=None):
+    """Bounds of both children sets of every node; pairs (indices in k < l order)
+    restricts LB2 to those machine pairs (LB2 = max(LB1, their values))."""
     n, m = _shape(p)
     count = len(d1)
     P, pp = _i32(p)
@@ -230,9 +238,12 @@ def children_bounds_batch(p, perm, d1, d2, kind=LB1 | LB2, threads=1):
     D2, dp2 = _u8(d2)
     o1 = np.empty(count * 2 * n, dtype=np.int32)
     o2 = np.empty(count * 2 * n, dtype=np.int32)
-    lib().orc_children_bounds_batch(n, m, pp, kind, count, qp, dp1, dp2,
-                                    o1.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                    o2.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), threads)
+    Sp, sp = _i32(pairs if pairs is not None else [0])
+    lib().orc_children_bounds_batch_pairs(n, m, pp, kind, count, qp, dp1, dp2,
+                                          o1.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          o2.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), threads,
+                                          sp if pairs is not None else None,
+                                          len(pairs) if pairs is not None else 0)
     return o1.reshape(count, 2, n), o2.reshape(count, 2, n)
 
 
@@ -246,18 +257,20 @@ def minmin(lbf, lbb, unscheduled, cap=INT32_MAX) -> int:
     return int(lib().orc_minmin(n, fp, bp, up, cap))
 
 
-def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False):
-    """Sequential DFS branch-and-bound.  Returns dict(outcome, cmax, perm, decomposed, bounded,
-    leaves, pruned)."""
+def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None):
+    """Sequential DFS branch-and-bound (LB2 over `pairs` when given).  Returns dict(outcome,
+    cmax, perm, decomposed, bounded, leaves, pruned)."""
     n, m = _shape(p)
     P, pp = _i32(p)
     best = np.zeros(1, dtype=np.int32)
     perm = np.full(n, -1, dtype=np.int32)
     cnt = np.zeros(4, dtype=np.int64)
-    out = lib().orc_bb_solve(n, m, pp, bound, int(bool(capped)), int(init_ub), int(node_limit),
-                             best.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                             perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                             cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    Sp, sp = _i32(pairs if pairs is not None else [0])
+    out = lib().orc_bb_solve_pairs(n, m, pp, bound, int(bool(capped)), int(init_ub), int(node_limit),
+                                   best.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   sp if pairs is not None else None, len(pairs) if pairs is not None else 0)
     return dict(outcome=int(out), cmax=int(best[0]), perm=perm, decomposed=int(cnt[0]),
                 bounded=int(cnt[1]), leaves=int(cnt[2]), pruned=int(cnt[3]))
 

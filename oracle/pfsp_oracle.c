@@ -183,6 +183,7 @@ int32_t orc_johnson(int n, const int32_t *p, int32_t *order_out)
  * schedules (Section 2.4). */
 typedef struct {
     int n, m, npairs;
+    int subset;          /* 1: only some pairs are used (LB2 over a subset) */
     const int32_t *p;
     int32_t *pk, *pl;    /* [pair] machine indices */
     int32_t *lag;        /* [pair][job] */
@@ -219,6 +220,29 @@ static void tables_free(orc_tables *T)
     free(T->pk); free(T->pl); free(T->lag); free(T->order);
 }
 
+/* Keep only the pairs listed (indices in the k < l lexicographic order used
+ * above), in that order.  pairs == NULL keeps every pair. */
+static void tables_select(orc_tables *T, const int32_t *pairs, int count)
+{
+    if (!pairs) return;
+    int n = T->n;
+    int32_t *pk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(count > 0 ? count : 1));
+    int32_t *pl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(count > 0 ? count : 1));
+    int32_t *lag = (int32_t *)malloc(sizeof(int32_t) * (size_t)(count > 0 ? count : 1) * (size_t)n);
+    int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * (size_t)(count > 0 ? count : 1) * (size_t)n);
+    for (int i = 0; i < count; ++i) {
+        int q = pairs[i];
+        pk[i] = T->pk[q];
+        pl[i] = T->pl[q];
+        memcpy(lag + (size_t)i * n, T->lag + (size_t)q * n, sizeof(int32_t) * (size_t)n);
+        memcpy(ord + (size_t)i * n, T->order + (size_t)q * n, sizeof(int32_t) * (size_t)n);
+    }
+    tables_free(T);
+    T->pk = pk; T->pl = pl; T->lag = lag; T->order = ord;
+    T->npairs = count;
+    T->subset = 1;
+}
+
 /* LB2 of a node given its front, back and unscheduled set (Section 2.4).
  * Reading of the silent passage: for every pair k < l, the unscheduled jobs
  * are run through the two-machine problem with time lags in Johnson order,
@@ -226,18 +250,22 @@ static void tables_free(orc_tables *T)
  *     t0 += p[j][k];   t1 = max(t1, t0 + g_j) + p[j][l];
  * and the pair's value adds the tails: max(t0 + back[k], t1 + back[l]).
  * LB2 is the largest pair value.  With a single machine there is no pair and
- * LB2 is defined equal to LB1. */
+ * LB2 is defined equal to LB1.  Over a subset of the pairs (the paper's LB2
+ * uses between m and m(m-1)/2 of them), LB2 is the largest of LB1 and the
+ * values of the pairs kept. */
 static int32_t lb2_from_parts(const orc_tables *T, const int32_t *front, const int32_t *back,
                               const uint8_t *un)
 {
     int n = T->n, m = T->m;
     const int32_t *p = T->p;
-    if (T->npairs == 0) {
+    int32_t lb1 = 0;
+    if (T->npairs == 0 || T->subset) {
         int32_t r[ORC_MAXN];
         orc_remain(n, m, p, un, r);
-        return orc_lb1_combine(m, front, r, back);
+        lb1 = orc_lb1_combine(m, front, r, back);
+        if (T->npairs == 0) return lb1;
     }
-    int32_t best = 0;
+    int32_t best = T->subset ? lb1 : 0;
     for (int q = 0; q < T->npairs; ++q) {
         int k = T->pk[q], l = T->pl[q];
         int32_t t0 = front[k], t1 = front[l];
@@ -250,7 +278,7 @@ static int32_t lb2_from_parts(const orc_tables *T, const int32_t *front, const i
             t1 = imax(t1, t0 + lag[j]) + p[j * m + l];
         }
         int32_t v = imax(t0 + back[k], t1 + back[l]);
-        if (q == 0 || v > best) best = v;
+        if ((q == 0 && !T->subset) || v > best) best = v;
     }
     return best;
 }
@@ -361,12 +389,14 @@ static void *batch_worker(void *arg)
 
 /* Children bounds of `count` nodes; the nodes are independent, so they are
  * split into `threads` contiguous ranges run on plain pthreads. */
-void orc_children_bounds_batch(int n, int m, const int32_t *p, int kind, int64_t count,
-                               const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
-                               int32_t *lb1, int32_t *lb2, int threads)
+void orc_children_bounds_batch_pairs(int n, int m, const int32_t *p, int kind, int64_t count,
+                                     const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
+                                     int32_t *lb1, int32_t *lb2, int threads, const int32_t *pairs,
+                                     int npairs)
 {
     orc_tables T;
     tables_init(&T, n, m, p);
+    tables_select(&T, pairs, npairs);
     if (threads < 1) threads = 1;
     if (threads > 256) threads = 256;
     pthread_t tid[256];
@@ -381,6 +411,13 @@ void orc_children_bounds_batch(int n, int m, const int32_t *p, int kind, int64_t
     batch_worker(&jobs[0]);
     for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
     tables_free(&T);
+}
+
+void orc_children_bounds_batch(int n, int m, const int32_t *p, int kind, int64_t count,
+                               const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
+                               int32_t *lb1, int32_t *lb2, int threads)
+{
+    orc_children_bounds_batch_pairs(n, m, p, kind, count, perm, d1, d2, lb1, lb2, threads, NULL, 0);
 }
 
 /* MinMin (Section 2.3): among both children sets, find the smallest bound;
@@ -483,11 +520,13 @@ int32_t orc_neh(int n, int m, const int32_t *p, int32_t *perm_out);
 /* Solve from the root.  init_ub is exclusive (only makespans < init_ub are
  * sought); INT32_MAX means "start from the NEH schedule".  Returns the
  * outcome code; counters[0..3] = decomposed, bounded, leaves, pruned. */
-int orc_bb_solve(int n, int m, const int32_t *p, int bound, int capped, int32_t init_ub,
-                 int64_t node_limit, int32_t *best_cmax, int32_t *best_perm, int64_t *counters)
+int orc_bb_solve_pairs(int n, int m, const int32_t *p, int bound, int capped, int32_t init_ub,
+                       int64_t node_limit, int32_t *best_cmax, int32_t *best_perm, int64_t *counters,
+                       const int32_t *pairs, int npairs)
 {
     orc_bb *S = (orc_bb *)calloc(1, sizeof(orc_bb));
     tables_init(&S->T, n, m, p);
+    tables_select(&S->T, pairs, npairs);
     S->bound = bound;
     S->capped = capped;
     S->node_limit = node_limit;
@@ -515,6 +554,13 @@ int orc_bb_solve(int n, int m, const int32_t *p, int bound, int capped, int32_t 
     tables_free(&S->T);
     free(S);
     return outcome;
+}
+
+int orc_bb_solve(int n, int m, const int32_t *p, int bound, int capped, int32_t init_ub,
+                 int64_t node_limit, int32_t *best_cmax, int32_t *best_perm, int64_t *counters)
+{
+    return orc_bb_solve_pairs(n, m, p, bound, capped, init_ub, node_limit, best_cmax, best_perm, counters,
+                              NULL, 0);
 }
 
 /* ------------------------------------------------------------------ */

@@ -57,6 +57,7 @@ struct SmemTables {
     const int *kl;        // [S*32]
     const uint8_t *rank;  // [S][n][32] position of job j in the lane's pair order
     const int2 *ptab;     // [S][n][32]
+    int S;                // slots of the table layout (stride of rank); the sweep may use fewer
 };
 
 __host__ __device__ inline int round4(int w) { return (w + 3) & ~3; }
@@ -389,7 +390,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     using mask_t = umask_t<NW>;
     constexpr bool REGACC = NC > 0;
     const int m = MT ? MT : m_rt;
-    const int S = MT ? (MT * (MT - 1) / 2 + 31) / 32 : S_rt;
+    const int S = S_rt;  // slots swept: those holding the instance's pairs
     const int lane = threadIdx.x & 31;
     const int mp = m | 1;
     const mask_t U = out.U;
@@ -455,7 +456,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         } else {
             Upos = 0;
             for (mask_t um = U; um; um &= um - 1)
-                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];
+                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + s) * 32 + lane];
         }
         if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane);
         else scan_slot<NW>(W, pt, E, Upos, u, lane);

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
     T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
+    T.S = (a.off_ptab - a.off_rank) / (8 * a.n);
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -179,7 +180,7 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
     a.tab_words = (kind & PFSP_LB2) ? L.words : L.off_rank;
     a.n = L.n;
     a.m = L.m;
-    a.S = (kind & PFSP_LB2) ? L.S : 0;
+    a.S = (kind & PFSP_LB2) ? L.Ssweep : 0;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
     a.off_kl = L.off_kl;

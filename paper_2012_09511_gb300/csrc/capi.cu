@@ -32,6 +32,7 @@ TableLayout table_layout(int n, int m) {
     L.m = m;
     L.P = m * (m - 1) / 2;
     L.S = (L.P + 31) / 32;
+    L.Ssweep = L.S;
     L.nj = (n + 3) & ~3;
     L.off_pm = 0;
     L.off_tot = L.off_pm + m * L.nj;
@@ -65,11 +66,13 @@ static std::vector<int> johnson_lag_order(int n, int m, const int32_t *p, int k,
     return ord;
 }
 
-void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order) {
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order,
+                  int count) {
     const int n = L.n, m = L.m;
-    // slot position of every pair: pair_order[i] = the pair at position i
-    std::vector<int> where(L.P);
-    for (int i = 0; i < L.P; ++i) where[pair_order ? pair_order[i] : i] = i;
+    // slot position of every pair: pair_order[i] = the pair at position i;
+    // pairs beyond the first `count` positions are left out (-1)
+    std::vector<int> where(L.P, -1);
+    for (int i = 0; i < count; ++i) where[pair_order ? pair_order[i] : i] = i;
     blob.assign(L.words, 0);
     for (int k = 0; k < m; ++k)
         for (int j = 0; j < n; ++j) blob[L.off_pm + k * L.nj + j] = p[j * m + k];
@@ -90,6 +93,7 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
     std::vector<int> lag(n);
     for (int k = 0; k < m; ++k)
         for (int l = k + 1; l < m; ++l, ++q) {
+            if (where[q] < 0) continue;
             const int s = where[q] / 32, lane = where[q] % 32;
             blob[L.off_kl + where[q]] = k | (l << 8);
             for (int j = 0; j < n; ++j) {
@@ -178,7 +182,7 @@ int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out) {
     inst->lay = table_layout(n, m);
     inst->lb2_ok = (size_t)inst->lay.words * 4 <= (size_t)kMaxTableBytes;
     std::vector<int32_t> blob;
-    build_tables(inst->lay, p, blob, nullptr);
+    build_tables(inst->lay, p, blob, nullptr, inst->lay.P);
     cudaError_t e = cudaMalloc(&inst->d_tab, blob.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -206,38 +210,62 @@ void pfsp_free_instance(pfsp_instance *inst) {
     free(inst);
 }
 
+int pfsp_set_lb2_pairs(pfsp_instance *inst, const int32_t *pairs, int count) {
+    g_err[0] = 0;
+    if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
+    const int P = inst->lay.P;
+    if (P == 0) return set_error(PFSP_ERR_INVALID, "an instance with one machine has no machine pair");
+    if (pairs && (count < 1 || count > P)) return set_error(PFSP_ERR_INVALID, "count must be in 1..%d", P);
+    if (!pairs) count = P;
+    std::vector<int32_t> ord(P);
+    std::vector<char> seen(P, 0);
+    int k = 0;
+    if (pairs) {
+        for (int i = 0; i < count; ++i) {
+            if (pairs[i] < 0 || pairs[i] >= P || seen[pairs[i]])
+                return set_error(PFSP_ERR_INVALID, "pairs must be distinct indices in 0..%d (entry %d)", P - 1, i);
+            seen[pairs[i]] = 1;
+            ord[k++] = pairs[i];
+        }
+    }
+    for (int q = 0; q < P; ++q)
+        if (!seen[q]) ord[k++] = q;  // the pairs left out, after the ones in use
+    std::vector<int32_t> blob;
+    build_tables(inst->lay, inst->p_host, blob, ord.data(), count);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(inst->d_tab, blob.data(), blob.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of the instance tables");
+    if (!inst->pair_order) inst->pair_order = (int32_t *)malloc(sizeof(int32_t) * P);
+    if (!inst->pair_order) return set_error(PFSP_ERR_OOM, "host allocation failed");
+    memcpy(inst->pair_order, ord.data(), sizeof(int32_t) * P);
+    inst->pair_count = count;
+    inst->lay.Ssweep = (count + 31) / 32;
+    return PFSP_OK;
+}
+
 int pfsp_set_pair_order(pfsp_instance *inst, const int32_t *order) {
     g_err[0] = 0;
     if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
     const int P = inst->lay.P;
-    std::vector<int32_t> ord(P);
     if (order) {
         std::vector<char> seen(P, 0);
         for (int i = 0; i < P; ++i) {
             if (order[i] < 0 || order[i] >= P || seen[order[i]])
                 return set_error(PFSP_ERR_INVALID, "order is not a permutation of 0..%d (entry %d)", P - 1, i);
             seen[order[i]] = 1;
-            ord[i] = order[i];
         }
-    } else {
-        std::iota(ord.begin(), ord.end(), 0);
     }
-    std::vector<int32_t> blob;
-    build_tables(inst->lay, inst->p_host, blob, ord.data());
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess)
-        e = cudaMemcpy(inst->d_tab, blob.data(), blob.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "upload of reordered instance tables");
-    if (P > 0 && !inst->pair_order) inst->pair_order = (int32_t *)malloc(sizeof(int32_t) * P);
-    if (P > 0 && !inst->pair_order) return set_error(PFSP_ERR_OOM, "host allocation failed");
-    if (P > 0) memcpy(inst->pair_order, ord.data(), sizeof(int32_t) * P);
-    return PFSP_OK;
+    if (P == 0) return PFSP_OK;
+    return pfsp_set_lb2_pairs(inst, order, P);
 }
 
 int pfsp_get_pair_order(const pfsp_instance *inst, int32_t *order) {
     g_err[0] = 0;
     if (!inst || !order) return set_error(PFSP_ERR_INVALID, "NULL argument");
-    for (int i = 0; i < inst->lay.P; ++i) order[i] = inst->pair_order ? inst->pair_order[i] : i;
+    const int used = inst->pair_count > 0 ? inst->pair_count : inst->lay.P;
+    for (int i = 0; i < inst->lay.P; ++i)
+        order[i] = i < used ? (inst->pair_order ? inst->pair_order[i] : i) : -1;
     return PFSP_OK;
 }
 

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
     T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
+    T.S = (a.off_ptab - a.off_rank) / (8 * a.n);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int n = a.n, m = MT ? MT : a.m, S = a.S, mp = m | 1, nj = (n + 3) & ~3;
     int *base = smem + a.tab_words + wib * a.warp_words;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
             const int Bl = W.FRB[l].z;
             umask_t<NW> Upos = 0;
             for (umask_t<NW> um = cb.U; um; um &= um - 1)
-                Upos |= umask_t<NW>(1) << T.rank[((size_t)lowest_bit<NW>(um) * S + s) * 32 + lane];
+                Upos |= umask_t<NW>(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + s) * 32 + lane];
             scan_slot<NW>(W, T.ptab + (size_t)s * n * 32 + lane, E, Upos, u, lane);
             bool hit = false;
             for (int c = 0; c < u; ++c) {
@@ -191,7 +192,7 @@ static RowsArgs rows_args(const pfsp_instance *inst, int D0, int O, long long nu
     a.tab_words = L.words;
     a.n = inst->n;
     a.m = inst->m;
-    a.S = L.S;
+    a.S = L.Ssweep;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
     a.off_kl = L.off_kl;

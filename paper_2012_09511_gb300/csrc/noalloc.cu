@@ -83,7 +83,7 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     if (opt->bound == PFSP_LB2 && (size_t)L.words * 4 > (size_t)kMaxTableBytes)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
     std::vector<int32_t> blob;
-    build_tables(L, p, blob, nullptr);
+    build_tables(L, p, blob, nullptr, L.P);
 
     std::vector<int> neh_perm;
     int ub0 = opt->init_ub;
@@ -98,7 +98,7 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     a.tab_words = opt->bound == PFSP_LB2 ? L.words : L.off_rank;
     a.n = n;
     a.m = m;
-    a.S = opt->bound == PFSP_LB2 ? L.S : 0;
+    a.S = opt->bound == PFSP_LB2 ? L.Ssweep : 0;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
     a.off_kl = L.off_kl;

@@ -36,6 +36,7 @@ constexpr long long kBoundChunk = 1 << 18;  // nodes per chunk of the host-point
 //                      b = kNegInf: the identity map.
 struct TableLayout {
     int n, m, P, S, nj;
+    int Ssweep;  // slots holding the pairs LB2 uses (S unless LB2 uses a subset of the pairs)
     int off_pm, off_tot, off_kl, off_rank, off_ptab, words;
 };
 
@@ -55,6 +56,7 @@ struct pfsp_instance {
     size_t scratch_bytes;
     pfsp_stats_t stats;
     int32_t *pair_order;         // pair at each slot position (NULL: k < l lexicographic)
+    int pair_count;              // pairs LB2 uses (the first ones of pair_order; P by default)
 };
 
 namespace pfsp {
@@ -77,8 +79,11 @@ int mlp_dims(const pfsp_mlp *M, int *m, int *D0, int *O);
 
 // Host-side builders shared by the entry points (capi.cu, solve_capi.cu).
 // pair_order: the pair (index in k < l lexicographic order) placed at each
-// slot position, NULL for the lexicographic order itself.
-void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order);
+// slot position, NULL for the lexicographic order itself; only the first
+// `count` positions hold pairs (count < P: LB2 over that subset), the others
+// are dummy lanes (identity maps).
+void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &blob, const int32_t *pair_order,
+                  int count);
 
 // Index of machine pair k < l in the lexicographic order of all m(m-1)/2 pairs.
 __host__ __device__ inline int pair_index(int k, int l, int m) { return k * (2 * m - k - 1) / 2 + (l - k - 1); }

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
         T.kl = smem + sa.off_kl;
         T.rank = reinterpret_cast<const uint8_t *>(smem + sa.off_rank);
         T.ptab = reinterpret_cast<const int2 *>(smem + sa.off_ptab);
+    T.S = (sa.off_ptab - sa.off_rank) / (8 * sa.n);
         WarpScratch Ws = carve_warp(wbase, sa.n, sa.m);
         if (lane == 0) {
             if (mode == 1) opening_interval(sa.n, W, wib, X);
@@ -339,7 +340,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
         d.tab_words = opt->bound == PFSP_LB2 ? I->lay.words : I->lay.off_rank;
         d.n = I->n;
         d.m = I->m;
-        d.S = opt->bound == PFSP_LB2 ? I->lay.S : 0;
+        d.S = opt->bound == PFSP_LB2 ? I->lay.Ssweep : 0;
         d.off_pm = I->lay.off_pm;
         d.off_tot = I->lay.off_tot;
         d.off_kl = I->lay.off_kl;

@@ -172,7 +172,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.tab_words = opt->bound == PFSP_LB2 ? L.words : L.off_rank;
     a.n = n;
     a.m = m;
-    a.S = opt->bound == PFSP_LB2 ? L.S : 0;
+    a.S = opt->bound == PFSP_LB2 ? L.Ssweep : 0;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
     a.off_kl = L.off_kl;

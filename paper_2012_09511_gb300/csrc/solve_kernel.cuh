@@ -21,6 +21,7 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
     T.ptab = reinterpret_cast<const int2 *>(smem + a.off_ptab);
+    T.S = (a.off_ptab - a.off_rank) / (8 * a.n);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;

@@ -136,6 +136,8 @@ _lib.pfsp_free_checkpoint.restype = None
 _lib.pfsp_free_checkpoint.argtypes = [_vp]
 _lib.pfsp_set_pair_order.restype = ctypes.c_int
 _lib.pfsp_set_pair_order.argtypes = [_vp, _vp]
+_lib.pfsp_set_lb2_pairs.restype = ctypes.c_int
+_lib.pfsp_set_lb2_pairs.argtypes = [_vp, _vp, ctypes.c_int]
 _lib.pfsp_get_pair_order.restype = ctypes.c_int
 _lib.pfsp_get_pair_order.argtypes = [_vp, _vp]
 _lib.pfsp_mlp_pair_scores.restype = ctypes.c_int
@@ -422,10 +424,17 @@ def pfsp_set_pair_order(inst: Instance, order=None) -> None:
     _check(_lib.pfsp_set_pair_order(inst.handle, _ptr(o)))
 
 
+def pfsp_set_lb2_pairs(inst: Instance, pairs=None) -> None:
+    """LB2 over the listed machine pairs only (indices in k < l order); None = all pairs."""
+    q = None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32)
+    _check(_lib.pfsp_set_lb2_pairs(inst.handle, _ptr(q), 0 if q is None else len(q)))
+
+
 def pfsp_get_pair_order(inst: Instance) -> np.ndarray:
+    """The pairs LB2 uses, in sweep order."""
     out = np.empty(inst.m * (inst.m - 1) // 2, dtype=np.int32)
     _check(_lib.pfsp_get_pair_order(inst.handle, _ptr(out)))
-    return out
+    return out[out >= 0]
 
 
 def pfsp_mlp_pair_scores(inst: Instance, mlp: Mlp, perm, d1, d2) -> np.ndarray:

@@ -159,3 +159,34 @@ def test_host_entry_point_chunks_match_one_launch(pf):
     assert (h1[idx] == r1).all() and (h2[idx] == r2).all()
     lb1_only, none2 = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
     assert none2 is None and (lb1_only == h1).all()
+
+
+@pytest.mark.parametrize("n,m,subset", [
+    (16, 20, "adjacent"), (16, 20, "random40"), (14, 20, "random33"), (12, 7, "adjacent"), (12, 7, "random5"),
+    (35, 10, "random20"),
+])
+def test_lb2_over_pair_subsets_bit_exact(pf, n, m, subset):
+    # LB2 over a subset of the machine pairs (max of LB1 and the listed pairs'
+    # values), against the oracle's definition with the same pairs
+    P = m * (m - 1) // 2
+    rng = np.random.default_rng(n * 100 + m)
+    if subset == "adjacent":
+        pairs = [k * (2 * m - k - 1) // 2 for k in range(m - 1)]
+    else:
+        pairs = list(rng.permutation(P)[:int(subset[6:])])
+    p = inputs.make_instance(n, m, 77)
+    perm, d1, d2 = inputs.random_nodes(n, 3000, seed=9, dmax=min(10, n // 3))
+    inst = pf.pfsp_load_instance(p)
+    pf.pfsp_set_lb2_pairs(inst, pairs)
+    assert list(pf.pfsp_get_pair_order(inst)) == [int(q) for q in pairs]
+    g1, g2 = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    o1, o2 = orc.children_bounds_batch(p, perm, d1, d2, threads=8, pairs=pairs)
+    assert (g1 == o1).all()
+    bad = np.argwhere(g2 != o2)
+    assert len(bad) == 0, (bad[:5], g2[tuple(bad[0])], o2[tuple(bad[0])])
+    pf.pfsp_set_lb2_pairs(inst, None)
+    _, full = pf.pfsp_bound_batch(inst, 3, perm, d1, d2)
+    _, ofull = orc.children_bounds_batch(p, perm, d1, d2, threads=8)
+    assert (full == ofull).all() and (g2 <= full).all()
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_set_lb2_pairs(inst, [0, 0])

@@ -169,6 +169,64 @@ def test_lb2_equals_max_over_pairs_of_bruteforce_relaxation():
         assert orc.lb2(p, s1, s2) == want
 
 
+def _pair_list(m):
+    return [(k, l) for k in range(m) for l in range(k + 1, m)]
+
+
+def test_lb2_over_pair_subsets():
+    # LB2 restricted to some machine pairs (the paper's LB2 uses between m and
+    # m(m-1)/2 pairs) is max(LB1, optimum of each kept pair's two-machine
+    # relaxation), the relaxation solved by trying every order of the
+    # unscheduled jobs; all pairs in any order give the full LB2
+    rng = np.random.default_rng(11)
+    n, m = 7, 4
+    P = m * (m - 1) // 2
+    pairs = _pair_list(m)
+    for seed in range(4):
+        p = inputs.make_instance(n, m, 300 + seed)
+        jobs = rng.permutation(n)
+        d1, d2 = int(rng.integers(0, 2)), int(rng.integers(1, 3))
+        perm = np.array(jobs, dtype=np.uint8)
+        b1, b2full = orc.children_bounds_batch(p, perm[None], np.array([d1], np.uint8), np.array([d2], np.uint8))
+        s1, s2 = list(perm[:d1]), list(perm[n - d2:])
+        rest = [j for j in range(n) if j not in s1 and j not in s2]
+        for subset in ([0], [P - 1], [2, 0], list(rng.permutation(P)[:3]), list(rng.permutation(P))):
+            _, b2 = orc.children_bounds_batch(p, perm[None], np.array([d1], np.uint8),
+                                              np.array([d2], np.uint8), pairs=subset)
+            for d in (0, 1):
+                for j in rest:
+                    c1, c2 = (s1 + [j], s2) if d == 0 else (s1, [j] + s2)
+                    others = [x for x in rest if x != j]
+                    f, bk = orc.front(p, c1), orc.back(p, c2)
+                    want = b1[0, d, j]
+                    for q in subset:
+                        k, l = pairs[q]
+                        want = max(want, min(orc.pair_value(p, k, l, f, bk, list(o))
+                                             for o in itertools.permutations(others)))
+                    assert b2[0, d, j] == want, (subset, d, j)
+                    assert b1[0, d, j] <= b2[0, d, j] <= b2full[0, d, j]
+            if len(subset) == P:
+                assert (b2 == b2full).all()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bb_with_adjacent_pairs_matches_brute_force(seed):
+    # any valid bound keeps the search exact: LB2 over the m - 1 adjacent
+    # machine pairs finds the brute-force optimum and explores a tree between
+    # those of LB1 and of the full LB2
+    n, m = 8, 4
+    p = inputs.make_instance(n, m, 40 + seed)
+    adjacent = [k * (2 * m - k - 1) // 2 for k in range(m - 1)]  # pair (k, k + 1)
+    assert [_pair_list(m)[q] for q in adjacent] == [(k, k + 1) for k in range(m - 1)]
+    cb, _ = orc.brute_force(p)
+    r = orc.bb_solve(p, bound=orc.LB2, pairs=adjacent)
+    assert r["cmax"] == cb and orc.makespan(p, r["perm"]) == cb
+    t1 = orc.bb_solve(p, bound=orc.LB1, init_ub=cb)["decomposed"]
+    ta = orc.bb_solve(p, bound=orc.LB2, init_ub=cb, pairs=adjacent)["decomposed"]
+    t2 = orc.bb_solve(p, bound=orc.LB2, init_ub=cb)["decomposed"]
+    assert t2 <= ta <= t1
+
+
 @pytest.mark.parametrize("seed", range(5))
 def test_leaf_bounds_are_exact(seed):
     n, m = 9, 5

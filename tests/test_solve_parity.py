@@ -143,6 +143,27 @@ def test_limits(pf):
     _check_perm(p, r)
 
 
+@pytest.mark.parametrize("n,m,seed", [(12, 10, 2), (11, 20, 3), (12, 6, 4)])
+def test_adjacent_pair_lb2_solve_matches_oracle(pf, n, m, seed):
+    # the paper's LB2 may use as few as the m - 1 adjacent machine pairs: the
+    # solve is exact (optimum) and its proof-mode tree is the oracle's tree for
+    # that bound, node for node
+    p = inputs.make_instance(n, m, seed)
+    adjacent = [k * (2 * m - k - 1) // 2 for k in range(m - 1)]
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, pairs=adjacent)
+    inst = pf.pfsp_load_instance(p)
+    pf.pfsp_set_lb2_pairs(inst, adjacent)
+    r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt)
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+    assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (want["decomposed"], want["bounded"],
+                                                                      want["pruned"])
+    assert r["lb2_slots"] <= r["decomposed"]  # one slot per decomposition at most
+    f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2)
+    assert f["cmax"] == opt
+    _check_perm(p, f)
+
+
 def test_phase_timers_and_slot_counter(pf):
     # the opt-in phase timers fill the cycle counters without changing the
     # search; without them the counters stay zero.  The LB2 slot counter is
