@@ -407,6 +407,18 @@ int pfsp_mlp_pair_scores(const pfsp_instance *inst, const pfsp_mlp *mlp, int64_t
 int pfsp_learn_pair_order(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
                           const uint8_t *d1, const uint8_t *d2, int32_t *order);
 
+/*
+ * Learned LB2 pair subset (not in the paper; an LB2 variant of Section 2.4):
+ * the network's mean pair probability over the given nodes (perm NULL: the
+ * 2n children of the root, job j first or last), and LB2 restricted to the
+ * `keep` pairs of highest score through pfsp_set_lb2_pairs (all pairs when
+ * keep >= m(m-1)/2).  With keep = 32 the sweep is a single 32-pair slot.  The
+ * bound stays a valid lower bound, so solves stay exact.  pairs (NULL or
+ * min(keep, m(m-1)/2) int32) receives the pairs kept, best first.
+ */
+int pfsp_learn_lb2_pairs(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
+                         const uint8_t *d1, const uint8_t *d2, int keep, int32_t *pairs);
+
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);
 

@@ -216,7 +216,13 @@ int pfsp_set_lb2_pairs(pfsp_instance *inst, const int32_t *pairs, int count) {
     const int P = inst->lay.P;
     if (P == 0) return set_error(PFSP_ERR_INVALID, "an instance with one machine has no machine pair");
     if (pairs && (count < 1 || count > P)) return set_error(PFSP_ERR_INVALID, "count must be in 1..%d", P);
-    if (!pairs) count = P;
+    if (!pairs) {
+        // already every pair in index order: nothing to rebuild
+        bool identity = inst->pair_count == 0 || inst->pair_count == P;
+        for (int q = 0; identity && inst->pair_order && q < P; ++q) identity = inst->pair_order[q] == q;
+        if (identity) return PFSP_OK;
+        count = P;
+    }
     std::vector<int32_t> ord(P);
     std::vector<char> seen(P, 0);
     int k = 0;

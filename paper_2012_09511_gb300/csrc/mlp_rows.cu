@@ -333,3 +333,43 @@ extern "C" int pfsp_learn_pair_order(pfsp_instance *inst, const pfsp_mlp *mlp, i
     if (rc == PFSP_OK && order) memcpy(order, ord.data(), sizeof(int32_t) * P);
     return rc;
 }
+
+extern "C" int pfsp_learn_lb2_pairs(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
+                                    const uint8_t *d1, const uint8_t *d2, int keep, int32_t *pairs) {
+    if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
+    const int n = inst->n, P = inst->lay.P;
+    if (keep < 1) return set_error(PFSP_ERR_INVALID, "keep must be >= 1");
+    if (P == 0) return set_error(PFSP_ERR_INVALID, "an instance with one machine has no machine pair");
+    // default sample: the 2n children of the root (job j first, or job j last)
+    std::vector<uint8_t> rp, r1, r2;
+    if (!perm) {
+        num_nodes = 2 * (int64_t)n;
+        rp.resize((size_t)num_nodes * n);
+        r1.resize(num_nodes);
+        r2.resize(num_nodes);
+        for (int j = 0; j < n; ++j)
+            for (int side = 0; side < 2; ++side) {
+                uint8_t *row = &rp[((size_t)2 * j + side) * n];
+                int c = 0;
+                if (side == 0) row[c++] = (uint8_t)j;
+                for (int x = 0; x < n; ++x)
+                    if (x != j) row[c++] = (uint8_t)x;
+                if (side == 1) row[c++] = (uint8_t)j;
+                r1[2 * j + side] = side == 0 ? 1 : 0;
+                r2[2 * j + side] = side == 1 ? 1 : 0;
+            }
+        perm = rp.data();
+        d1 = r1.data();
+        d2 = r2.data();
+    }
+    std::vector<float> score(P);
+    int rc = pfsp_mlp_pair_scores(inst, mlp, num_nodes, perm, d1, d2, score.data());
+    if (rc != PFSP_OK) return rc;
+    std::vector<int32_t> ord(P);
+    for (int q = 0; q < P; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return score[x] > score[y]; });
+    const int k = std::min(keep, P);
+    rc = pfsp_set_lb2_pairs(inst, ord.data(), k);
+    if (rc == PFSP_OK && pairs) memcpy(pairs, ord.data(), sizeof(int32_t) * k);
+    return rc;
+}

@@ -3,18 +3,18 @@
 Orchestration only; every step runs in the library's kernels:
 pfsp_solve_trace records nodes the solver decomposes, pfsp_mlp_rows builds
 the training rows on the GPU, pfsp_mlp_train trains the network on the GPU,
-pfsp_learn_pair_order ranks the machine pairs with the network, and
+pfsp_learn_lb2_pairs scores the machine pairs with the network, and
 pfsp_solve runs the plain and the learned solvers.
 
-The learned solver skips a node's LB2 sweep when every child of one
-direction already has an LB1 at or above the incumbent (no such node has a
-child below it, so the tree is unchanged), and while the incumbent may still
-improve it orders the rows of the first levels by the network's descend-first
-logits.  The network's pair ranking (per instance, from a short pilot trace)
-feeds the optional between-slot checks of the sweep, reported as an ablation.
-Its optimum is always the plain solver's; the comparison reports the time to
-the proven optimum (wall time, pilot and ranking included) and the
-decomposed-node counts of both.
+The learned solver restricts LB2 to the 32 machine pairs that the network
+predicts most often give a child's LB2 (scored on the root's children; a
+single 32-pair slot instead of up to six), and skips a node's LB2 sweep when
+every child of one direction already has an LB1 at or above the incumbent.
+Both keep the search exact (a subset LB2 is still a lower bound; a skipped
+node has no child below the incumbent), so its optimum is always the plain
+solver's; the comparison reports the time to the proven optimum (wall time,
+ranking included) and the decomposed-node counts of both.  The network's row
+order is reported as an ablation.
 """
 from __future__ import annotations
 
@@ -84,15 +84,20 @@ def _run(pfsp, inst, **kw):
     return r, time.perf_counter() - t
 
 
-def learned_options(pfsp, n, proof, mlp, depth=None):
-    """pfsp_solve options of the learned solver: early exit always; when the
-    incumbent may still improve (not proof mode) the network also orders the
-    rows of the first `depth` levels (default n / 4).  In proof mode the tree
-    is fixed by the incumbent, so row order cannot change it and is left out."""
-    if proof:
-        return dict(learned=pfsp.PFSP_EARLY_EXIT)
-    return dict(learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
-                learn_depth=depth or max(1, n // 4))
+def learned_pairs(pfsp, inst, mlp, keep=32):
+    """LB2 of `inst` restricted to the `keep` machine pairs the network scores
+    highest on the root's children (pfsp_learn_lb2_pairs); nothing changes when
+    the instance has at most `keep` pairs.  Returns the pairs kept, or None."""
+    if inst.m * (inst.m - 1) // 2 <= keep:
+        pfsp.pfsp_set_lb2_pairs(inst, None)
+        return None
+    return pfsp.pfsp_learn_lb2_pairs(inst, mlp, keep=keep)
+
+
+def learned_options(pfsp):
+    """pfsp_solve options of the learned solver (the LB2 pair subset is set on
+    the instance by learned_pairs): early exit of the sweep."""
+    return dict(learned=pfsp.PFSP_EARLY_EXIT)
 
 
 def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
@@ -100,10 +105,10 @@ def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
     with init_ub, in proof mode.
 
     plain: the full-pair LB2 solver, pairs in index order.
-    learned: learned_options().  Ablations: early exit alone, early exit plus
-    the network's row order at each depth of `depths` (finding mode), and for
-    m >= 12 the between-slot checks with the network's pair order (wall time
-    including the pilot trace and the ranking)."""
+    learned: LB2 over the network's top 32 pairs (learned_pairs; a single
+    32-pair slot) with early exit; its wall time includes the ranking.
+    Ablations: early exit alone, and in finding mode the network's row order
+    at each depth of `depths` (with early exit, all pairs)."""
     n = p.shape[0]
     depths = depths or [max(1, n // 4)]
     inst = pfsp.pfsp_load_instance(p)
@@ -117,23 +122,21 @@ def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
                      "wall_seconds": wall + extra_wall, "decomposed": r["decomposed"],
                      "bounded": r["bounded_children"], "lb2_slots": r["lb2_slots"]}
 
-    pfsp.pfsp_set_pair_order(inst, None)
+    pfsp.pfsp_set_lb2_pairs(inst, None)
     record("plain", *_run(pfsp, inst, **base))
-    record("early_exit_index_order", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base))
+    record("early_exit", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base))
     if init_ub is None:
         for d in depths:
             record("child_order_depth_%d" % d,
                    *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
                          learn_depth=d, **base))
-    record("learned", *_run(pfsp, inst, **learned_options(pfsp, n, init_ub is not None, mlp, depths[0]), **base))
     t = time.perf_counter()
-    if rank_pairs(pfsp, inst, mlp) is not None:
-        t_rank = time.perf_counter() - t
-        record("early_exit_slots_learned_pairs",
-               *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_EARLY_EXIT_SLOTS, **base),
-               extra_wall=t_rank)
-        out["ranking_wall_seconds"] = t_rank
-    pfsp.pfsp_set_pair_order(inst, None)
+    kept = learned_pairs(pfsp, inst, mlp)
+    t_rank = time.perf_counter() - t
+    record("learned", *_run(pfsp, inst, **learned_options(pfsp), **base), extra_wall=t_rank)
+    out["ranking_wall_seconds"] = t_rank
+    out["pairs_kept"] = None if kept is None else [int(q) for q in kept]
+    pfsp.pfsp_set_lb2_pairs(inst, None)
     return out
 
 

@@ -136,6 +136,8 @@ _lib.pfsp_free_checkpoint.restype = None
 _lib.pfsp_free_checkpoint.argtypes = [_vp]
 _lib.pfsp_set_pair_order.restype = ctypes.c_int
 _lib.pfsp_set_pair_order.argtypes = [_vp, _vp]
+_lib.pfsp_learn_lb2_pairs.restype = ctypes.c_int
+_lib.pfsp_learn_lb2_pairs.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.pfsp_set_lb2_pairs.restype = ctypes.c_int
 _lib.pfsp_set_lb2_pairs.argtypes = [_vp, _vp, ctypes.c_int]
 _lib.pfsp_get_pair_order.restype = ctypes.c_int
@@ -477,3 +479,19 @@ def pfsp_solve_resumable(inst: Instance, resume: bytes = None, opts: pfsp_option
     r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value, checkpoint=data)
     r.update(pfsp_stats(inst))
     return r
+
+
+def pfsp_learn_lb2_pairs(inst: Instance, mlp: Mlp, keep=32, perm=None, d1=None, d2=None) -> np.ndarray:
+    """LB2 over the `keep` pairs the network scores highest (sample: the given nodes, or the
+    root's children); returns the pairs kept, best first."""
+    P = inst.m * (inst.m - 1) // 2
+    out = np.empty(max(1, min(keep, P)), dtype=np.int32)
+    if perm is None:
+        _check(_lib.pfsp_learn_lb2_pairs(inst.handle, mlp.handle, 0, None, None, None, int(keep), _ptr(out)))
+    else:
+        perm = np.ascontiguousarray(perm, dtype=np.uint8)
+        d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+        d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+        _check(_lib.pfsp_learn_lb2_pairs(inst.handle, mlp.handle, len(d1), _ptr(perm), _ptr(d1), _ptr(d2), int(keep),
+                                         _ptr(out)))
+    return out[:min(keep, P)]

@@ -244,3 +244,30 @@ def test_training_on_solver_traces_beats_constant_predictor(pf):
     pr = np.clip(pr, 1e-4, 1 - 1e-4)
     const = -(M[te] * (T[te] * np.log(pr) + (1 - T[te]) * np.log(1 - pr))).sum() / len(te)
     assert loss_net < const, (loss_net, const)
+
+
+def test_learned_lb2_pair_subset_keeps_the_solve_exact(pf):
+    # LB2 over the network's top pairs (scored on the root's children) is a
+    # valid bound: the optimum is unchanged and the proof tree is the oracle's
+    # for the same pairs
+    n, m, P = 12, 10, 45
+    p = inputs.make_instance(n, m, 17)
+    inst = pf.pfsp_load_instance(p)
+    mlp = pf.pfsp_mlp_create(m, seed=3)
+    kept = pf.pfsp_learn_lb2_pairs(inst, mlp, keep=32)
+    perm = np.array([[j] + [x for x in range(n) if x != j] if s == 0 else [x for x in range(n) if x != j] + [j]
+                     for j in range(n) for s in (0, 1)], dtype=np.uint8)
+    d1 = np.array([1 - s for j in range(n) for s in (0, 1)], dtype=np.uint8)
+    d2 = 1 - d1
+    score = pf.pfsp_mlp_pair_scores(inst, mlp, perm, d1, d2)
+    assert list(kept) == list(np.argsort(-score, kind="stable")[:32])
+    assert list(pf.pfsp_get_pair_order(inst)) == list(kept)
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, pairs=[int(q) for q in kept])
+    r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=pf.PFSP_EARLY_EXIT)
+    assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (want["decomposed"], want["bounded"],
+                                                                      want["pruned"])
+    assert r["lb2_slots"] <= r["decomposed"]
+    f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2)
+    assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
+    assert len(pf.pfsp_learn_lb2_pairs(inst, mlp, keep=100)) == P  # keep >= P: every pair
