@@ -240,22 +240,24 @@ def batch_leg(pfsp):
 
 
 def learned_leg(pfsp):
-    """Learned ordering vs the plain full-pair LB2 solver on n = 50, m = 5 and
-    n = 30, m = 10 (5 seeds each): from NEH to the proven optimum, and proving a
-    known optimum (fixed tree).  The m-machine networks are trained on the GPU on
-    the solver's own traces of 20-job instances with the same m; identical optima
-    required; wall times (pilot trace and pair ranking included) and decomposed
-    nodes reported."""
+    """Learned solver vs the plain full-pair LB2 solver on n = 50, m = 5 and
+    n = 30, m = 10 (5 seeds each), from NEH to the proven optimum and proving a
+    known optimum (fixed tree), plus proofs of 16 x 20 and 18 x 20 instances.
+    The m-machine networks are trained on the GPU on the solver's own traces of
+    other instances with the same m; identical optima required; wall times
+    (pair ranking included) and decomposed nodes reported."""
     from paper_2012_09511_gb300 import inputs, learned
     mlps, training = {}, {}
-    for m in (5, 10):
+    for m in (5, 10, 20):
         t = time.perf_counter()
-        mlps[m], info = learned.train_network(pfsp, m, [inputs.make_instance(20, m, s) for s in range(1, 11)])
+        nt = 16 if m == 20 else 20  # 20-machine traces from 16-job instances, which solve in milliseconds
+        mlps[m], info = learned.train_network(pfsp, m, [inputs.make_instance(nt, m, s) for s in range(1, 11)],
+                                              nodes_per_instance=3000 if m == 20 else 4000)
         info["seconds"] = time.perf_counter() - t
         training["m=%d" % m] = info
     out = {"training": training}
-    for proof in (False, True):
-        rep = learned.compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), time_limit_s=20.0,
+    for shapes, proof in ((((50, 5), (30, 10)), False), (((50, 5), (30, 10), (16, 20), (18, 20)), True)):
+        rep = learned.compare(pfsp, shapes=shapes, seeds=range(1, 6), time_limit_s=20.0,
                               depth_fracs=(4,), proof=proof, mlps=mlps)
         for shape, v in rep.items():
             key = "%s_%s" % (shape, "proof" if proof else "find")
