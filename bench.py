@@ -71,7 +71,7 @@ def dist_env():
 
 
 def algorithmic_ops(n, m, d1, d2):
-    """Integer operations the bounding method needs per batch (see DESIGN.md):
+    """Integer operations the bounding method needs per batch:
     front/back wavefronts 2 per cell; per child and machine 6 (recurrence
     max+add, term add+add, max into the bound, remaining-work subtraction);
     LB2 per (pair, unscheduled job) 13: prefix map 2, suffix map 3, C 2 and

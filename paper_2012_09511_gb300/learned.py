@@ -6,9 +6,10 @@ the training rows on the GPU, pfsp_mlp_train trains the network on the GPU,
 pfsp_learn_lb2_pairs scores the machine pairs with the network, and
 pfsp_solve runs the plain and the learned solvers.
 
-The learned solver restricts LB2 to the 32 machine pairs that the network
-predicts most often give a child's LB2 (scored on the root's children; a
-single 32-pair slot instead of up to six), and skips a node's LB2 sweep when
+The learned solver restricts LB2 to the machine pairs that the network
+predicts most often give a child's LB2 (scored on the root's children; half
+of the 32-pair slots: one of two at m = 10, three of six at m = 20), and
+skips a node's LB2 sweep when
 every child of one direction already has an LB1 at or above the incumbent.
 Both keep the search exact (a subset LB2 is still a lower bound; a skipped
 node has no child below the incumbent), so its optimum is always the plain
@@ -84,11 +85,17 @@ def _run(pfsp, inst, **kw):
     return r, time.perf_counter() - t
 
 
-def learned_pairs(pfsp, inst, mlp, keep=32):
+def learned_pairs(pfsp, inst, mlp, keep=None):
     """LB2 of `inst` restricted to the `keep` machine pairs the network scores
-    highest on the root's children (pfsp_learn_lb2_pairs); nothing changes when
-    the instance has at most `keep` pairs.  Returns the pairs kept, or None."""
-    if inst.m * (inst.m - 1) // 2 <= keep:
+    highest on the root's children (pfsp_learn_lb2_pairs).  By default half of
+    the 32-pair slots, rounded up, are kept: 32 of 45 pairs at m = 10 (one slot
+    of two), 96 of 190 at m = 20 (three of six); measured on proofs, fewer
+    pairs weaken the bound more than they save.  Nothing changes when the
+    instance has at most `keep` pairs.  Returns the pairs kept, or None."""
+    P = inst.m * (inst.m - 1) // 2
+    if keep is None:
+        keep = 32 * (((P + 31) // 32 + 1) // 2)
+    if P <= keep:
         pfsp.pfsp_set_lb2_pairs(inst, None)
         return None
     return pfsp.pfsp_learn_lb2_pairs(inst, mlp, keep=keep)
@@ -105,8 +112,8 @@ def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
     with init_ub, in proof mode.
 
     plain: the full-pair LB2 solver, pairs in index order.
-    learned: LB2 over the network's top 32 pairs (learned_pairs; a single
-    32-pair slot) with early exit; its wall time includes the ranking.
+    learned: LB2 over the network's top pairs (learned_pairs: half of the
+    32-pair slots) with early exit; its wall time includes the ranking.
     Ablations: early exit alone, and in finding mode the network's row order
     at each depth of `depths` (with early exit, all pairs)."""
     n = p.shape[0]
