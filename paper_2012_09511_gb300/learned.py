@@ -53,32 +53,6 @@ def train_network(pfsp, m, train_instances, seed=0, epochs=8, batch=4096, lr=2e-
     return mlp, {"rows": int(len(X)), "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
 
 
-def pilot_nodes(pfsp, inst, nodes=4096, stride=2, bound=2, time_limit_s=2.0):
-    """A short trace of the solver on `inst`: the first `nodes` decompositions,
-    every `stride`-th recorded (the sample the pair ranking is computed on)."""
-    perm, d1, d2, _ = pfsp.pfsp_solve_trace(inst, nodes // stride + 64, stride=stride, bound=bound,
-                                            node_limit=nodes, time_limit_s=time_limit_s)
-    return perm, d1, d2
-
-
-def rank_pairs(pfsp, inst, mlp, **pilot_kw):
-    """Learned pair order of `inst`: the network's mean pair probabilities over a
-    pilot trace, pairs sorted by decreasing score and applied to the instance
-    (so that LB2's first 32-pair slot holds the pairs most likely to decide a
-    child; it matters only with PFSP_EARLY_EXIT_SLOTS).  Instances with fewer
-    than four 32-pair slots (m < 12) are not ranked.  Returns the order, or
-    None when nothing was ranked."""
-    S = (inst.m * (inst.m - 1) // 2 + 31) // 32
-    if S < 4:
-        pfsp.pfsp_set_pair_order(inst, None)
-        return None
-    perm, d1, d2 = pilot_nodes(pfsp, inst, **pilot_kw)
-    if len(d1) == 0:
-        pfsp.pfsp_set_pair_order(inst, None)
-        return None
-    return pfsp.pfsp_learn_pair_order(inst, mlp, perm, d1, d2)
-
-
 def _run(pfsp, inst, **kw):
     t = time.perf_counter()
     r = pfsp.pfsp_solve(inst, **kw)
