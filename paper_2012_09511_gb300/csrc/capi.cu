@@ -294,15 +294,21 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
     if (rc != PFSP_OK) return rc;
     auto t0 = std::chrono::steady_clock::now();
     const int n = inst->n;
-    // one pass over the depths: validation and the children count
+    // one pass over the depths: validation and the children count (a plain
+    // reduction the host compiler vectorises)
     uint64_t depth_sum = 0;
-    int bad = 0;
-    for (int64_t i = 0; i < num_nodes; ++i) {
-        const int d = (int)d1[i] + (int)d2[i];
-        depth_sum += (uint64_t)d;
-        bad |= d > n;
+    unsigned dmax = 0;
+    for (int64_t i0 = 0; i0 < num_nodes; i0 += 1 << 16) {
+        const int64_t i1 = std::min<int64_t>(num_nodes, i0 + (1 << 16));
+        uint32_t part = 0;  // at most 65,536 x 128: no overflow
+        for (int64_t i = i0; i < i1; ++i) {
+            const unsigned d = (unsigned)d1[i] + (unsigned)d2[i];
+            part += d;
+            dmax = d > dmax ? d : dmax;
+        }
+        depth_sum += part;
     }
-    if (bad)
+    if (dmax > (unsigned)n)
         for (int64_t i = 0; i < num_nodes; ++i)
             if ((int)d1[i] + (int)d2[i] > n)
                 return set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i],
