@@ -278,10 +278,11 @@ int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp
  * order[i] (i = 0 .. m(m-1)/2 - 1) is the index of the pair placed at sweep
  * position i, pairs being indexed k = 0..m-2, l = k+1..m-1 (the network's
  * column order); positions 0..31 form the first 32-pair slot, and so on.  The
- * order matters only to PFSP_EARLY_EXIT, which can stop after a slot.  order
- * NULL restores the index order.  The instance's device tables are rebuilt
- * (the call synchronises the device first; no call using the instance may
- * run meanwhile).
+ * order matters only to PFSP_EARLY_EXIT_SLOTS, which can stop after a slot.
+ * Every pair is used (this also undoes pfsp_set_lb2_pairs).  order NULL
+ * restores the index order.  The instance's device tables are rebuilt (the
+ * call synchronises the device first; no call using the instance may run
+ * meanwhile).
  * Errors: PFSP_ERR_INVALID (NULL instance, order not a permutation),
  * PFSP_ERR_CUDA.
  */

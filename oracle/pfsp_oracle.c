@@ -16,7 +16,9 @@
  *     combination), with the back obtained by the reversibility property;
  *   - LB2: Section 2.4's two-machine bound over all m(m-1)/2 machine pairs,
  *     each pair solved by Johnson's rule extended to time lags (the reading
- *     of the silent passage is in the header of orc_lb2 below);
+ *     of the silent passage is in the header of lb2_from_parts below), or
+ *     over a given subset of the pairs (the paper's variants use between
+ *     about m and m(m-1)/2 of them);
  *   - branching: forward/backward/dynamic branching and the MinMin rule of
  *     Section 2.3;
  *   - search: depth-first (Section 2.5) with pruning of children whose bound
