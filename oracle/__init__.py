@@ -12,6 +12,8 @@ Functions and the paper passages they follow:
   lb2, johnson ............ Section 2.4 (two-machine bound, Johnson's rule)
   children_bounds ......... Section 2.3 (forward/backward children), 2.4
   minmin .................. Section 2.3 (MinMin branching rule)
+  branch_rule ............. Section 2.3 and Table 4 (readings of MinBranch
+                            and MinSum, which the paper names only)
   bb_solve ................ Sections 2.2-2.5 (DFS branch-and-bound)
   factoradic_*, midpoint .. Section 2.6 (work units, work stealing)
   ivm_decode .............. Section 2.5 (IVM decoding)
@@ -34,6 +36,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FWD, BWD = 0, 1
 LB1, LB2 = 1, 2
+MINMIN, MINMIN_CAPPED, MINBRANCH, MINSUM = 0, 1, 2, 3
 OPTIMAL, PROVEN_NO_BETTER, LIMIT_NODES = 0, 1, 2
 INT32_MAX = 2**31 - 1
 
@@ -90,6 +93,9 @@ def lib():
                                          ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p, i32p, ctypes.c_int]
         L.orc_minmin.restype = ctypes.c_int
         L.orc_minmin.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int32]
+        L.orc_branch_rule.restype = ctypes.c_int
+        L.orc_branch_rule.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int32,
+                                      ctypes.c_int32]
         L.orc_bb_solve.restype = ctypes.c_int
         L.orc_bb_solve.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p]
@@ -257,16 +263,30 @@ def minmin(lbf, lbb, unscheduled, cap=INT32_MAX) -> int:
     return int(lib().orc_minmin(n, fp, bp, up, cap))
 
 
-def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None):
-    """Sequential DFS branch-and-bound (LB2 over `pairs` when given).  Returns dict(outcome,
-    cmax, perm, decomposed, bounded, leaves, pruned)."""
+def branch_rule(lbf, lbb, unscheduled, rule, cap=INT32_MAX, ub=INT32_MAX) -> int:
+    """Direction (0 forward, 1 backward) chosen by branching rule `rule` (MINMIN, MINMIN_CAPPED,
+    MINBRANCH or MINSUM)."""
+    n = len(lbf)
+    F, fp = _i32(lbf)
+    B, bp = _i32(lbb)
+    un = np.zeros(n, dtype=np.uint8)
+    un[list(unscheduled)] = 1
+    U, up = _u8(un)
+    return int(lib().orc_branch_rule(n, fp, bp, up, int(rule), int(cap), int(ub)))
+
+
+def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None, branching=None):
+    """Sequential DFS branch-and-bound (LB2 over `pairs` when given).  `branching` is one of
+    MINMIN, MINMIN_CAPPED, MINBRANCH, MINSUM (default: MinMin, capped when `capped`).
+    Returns dict(outcome, cmax, perm, decomposed, bounded, leaves, pruned)."""
+    rule = (MINMIN_CAPPED if capped else MINMIN) if branching is None else int(branching)
     n, m = _shape(p)
     P, pp = _i32(p)
     best = np.zeros(1, dtype=np.int32)
     perm = np.full(n, -1, dtype=np.int32)
     cnt = np.zeros(4, dtype=np.int64)
     Sp, sp = _i32(pairs if pairs is not None else [0])
-    out = lib().orc_bb_solve_pairs(n, m, pp, bound, int(bool(capped)), int(init_ub), int(node_limit),
+    out = lib().orc_bb_solve_pairs(n, m, pp, bound, rule, int(init_ub), int(node_limit),
                                    best.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),

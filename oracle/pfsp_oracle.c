@@ -20,7 +20,8 @@
  *     over a given subset of the pairs (the paper's variants use between
  *     about m and m(m-1)/2 of them);
  *   - branching: forward/backward/dynamic branching and the MinMin rule of
- *     Section 2.3;
+ *     Section 2.3, and readings of the MinBranch and MinSum rules that
+ *     Table 4 names;
  *   - search: depth-first (Section 2.5) with pruning of children whose bound
  *     is not below the incumbent;
  *   - factorial number system of Section 2.6;
@@ -447,6 +448,35 @@ int orc_minmin(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un,
     return ORC_FWD;
 }
 
+/* The other dynamic branching rules that Table 4 names for earlier solvers
+ * of the same problem (the paper names them without defining them; these
+ * are this oracle's readings):
+ *   MinBranch: choose the set with fewer children whose bound is below the
+ *     incumbent ub (fewer subproblems to explore); on a tie the set with the
+ *     larger sum of bounds; on a further tie, forward.
+ *   MinSum: choose the set whose children leave the smaller total gap
+ *     sum(ub - LB) to the incumbent.  Both sets hold the same children count,
+ *     so this is the set with the larger sum of bounds; on a tie, forward.
+ * rule: 0 MinMin, 1 MinMin on min(LB, cap), 2 MinBranch, 3 MinSum. */
+int orc_branch_rule(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un, int rule,
+                    int32_t cap, int32_t ub)
+{
+    if (rule == 0) return orc_minmin(n, lbf, lbb, un, INT32_MAX);
+    if (rule == 1) return orc_minmin(n, lbf, lbb, un, cap);
+    int kf = 0, kb = 0;
+    int64_t sf = 0, sb = 0;
+    for (int j = 0; j < n; ++j) {
+        if (!un[j]) continue;
+        kf += lbf[j] < ub;
+        kb += lbb[j] < ub;
+        sf += lbf[j];
+        sb += lbb[j];
+    }
+    if (rule == 2 && kf != kb) return kf < kb ? ORC_FWD : ORC_BWD;
+    if (sf != sb) return sf > sb ? ORC_FWD : ORC_BWD;
+    return ORC_FWD;
+}
+
 /* ------------------------------------------------------------------ */
 /* Depth-first branch-and-bound (Sections 2.2-2.5)                      */
 /* ------------------------------------------------------------------ */
@@ -454,7 +484,7 @@ int orc_minmin(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un,
 typedef struct {
     orc_tables T;
     int bound;          /* ORC_LB1 or ORC_LB2 */
-    int capped;         /* MinMin on min(LB, cap) */
+    int rule;           /* branching rule, as orc_branch_rule's */
     int32_t cap;        /* the run's initial incumbent */
     int32_t ub;         /* incumbent: only makespans < ub are sought */
     int32_t best_perm[ORC_MAXN];
@@ -483,7 +513,7 @@ static void bb_dfs(orc_bb *S, const int32_t *perm, int d1, int d2)
     if (u == 1) S->leaves += 2;
     for (int j = 0; j < n; ++j) un[j] = 0;
     for (int i = d1; i < n - d2; ++i) un[perm[i]] = 1;
-    int dir = orc_minmin(n, lb, lb + n, un, S->capped ? S->cap : INT32_MAX);
+    int dir = orc_branch_rule(n, lb, lb + n, un, S->rule, S->cap, S->ub);
     const int32_t *lbd = lb + dir * n;
 
     /* prune at bounding time against the current incumbent */
@@ -519,10 +549,12 @@ static void bb_dfs(orc_bb *S, const int32_t *perm, int d1, int d2)
 
 int32_t orc_neh(int n, int m, const int32_t *p, int32_t *perm_out);
 
-/* Solve from the root.  init_ub is exclusive (only makespans < init_ub are
- * sought); INT32_MAX means "start from the NEH schedule".  Returns the
+/* Solve from the root with branching rule `rule` (0 MinMin, 1 capped MinMin,
+ * 2 MinBranch, 3 MinSum; see orc_branch_rule).  init_ub is exclusive (only
+ * makespans < init_ub are sought); INT32_MAX means "start from the NEH
+ * schedule".  Returns the
  * outcome code; counters[0..3] = decomposed, bounded, leaves, pruned. */
-int orc_bb_solve_pairs(int n, int m, const int32_t *p, int bound, int capped, int32_t init_ub,
+int orc_bb_solve_pairs(int n, int m, const int32_t *p, int bound, int rule, int32_t init_ub,
                        int64_t node_limit, int32_t *best_cmax, int32_t *best_perm, int64_t *counters,
                        const int32_t *pairs, int npairs)
 {
@@ -530,7 +562,7 @@ int orc_bb_solve_pairs(int n, int m, const int32_t *p, int bound, int capped, in
     tables_init(&S->T, n, m, p);
     tables_select(&S->T, pairs, npairs);
     S->bound = bound;
-    S->capped = capped;
+    S->rule = rule;
     S->node_limit = node_limit;
     int from_neh = 0;
     if (init_ub == INT32_MAX) {

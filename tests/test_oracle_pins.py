@@ -290,6 +290,45 @@ def test_minmin_worked_example():
     assert sum(v >= ub for v in g["lb_forward"]) == g["pruned_if_forward"]
 
 
+def test_other_rules_on_the_worked_example():
+    # Fig. 4's decomposition: backward leaves one child below the incumbent
+    # (two pruned) and forward two (one pruned), so MinBranch also branches
+    # backward; backward's bounds sum to 57 against forward's 53, so MinSum does too
+    g = golden("minmin_example.json")
+    n = 7
+    lbf = np.full(n, -1)
+    lbb = np.full(n, -1)
+    jobs = [j - 1 for j in g["jobs_1based"]]
+    lbf[jobs] = g["lb_forward"]
+    lbb[jobs] = g["lb_backward"]
+    ub = g["incumbent"]
+    want = orc.BWD if g["decision"] == "backward" else orc.FWD
+    for rule in (orc.MINMIN, orc.MINBRANCH, orc.MINSUM):
+        assert orc.branch_rule(lbf, lbb, jobs, rule, ub=ub) == want
+
+
+def test_branching_rules_disagree_by_hand():
+    # hand-made bound vectors on which the rules part ways
+    # MinMin: the minimum 16 occurs only backward -> forward.  MinBranch with
+    # incumbent 18: two forward children survive, one backward -> backward.
+    # MinSum: 64 forward against 66 backward -> backward.
+    lbf, lbb = [17, 17, 30], [16, 25, 25]
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINMIN, ub=18) == orc.FWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, ub=18) == orc.BWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, ub=18) == orc.BWD
+    # MinBranch backward (1 survivor of incumbent 20 against 2); MinSum forward (111 > 72)
+    lbf, lbb = [10, 11, 90], [12, 30, 30]
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, ub=20) == orc.BWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, ub=20) == orc.FWD
+    # MinBranch tie (one survivor each) -> larger sum (40 > 32) -> forward
+    assert orc.branch_rule([10, 30], [12, 20], [0, 1], orc.MINBRANCH, ub=15) == orc.FWD
+    # equal sums -> forward under both
+    assert orc.branch_rule([5, 8], [6, 7], [0, 1], orc.MINSUM) == orc.FWD
+    assert orc.branch_rule([5, 8], [6, 7], [0, 1], orc.MINBRANCH, ub=7) == orc.FWD
+    # only unscheduled jobs count
+    assert orc.branch_rule([1, 50, 50], [1, 40, 40], [1, 2], orc.MINSUM) == orc.FWD
+
+
 def test_minmin_tie_rules():
     # equal counts of the minimum -> larger sum wins; equal sums -> forward
     assert orc.minmin([5, 9], [5, 7], [0, 1]) == orc.FWD
@@ -341,7 +380,18 @@ def test_bb_lb2_matches_brute_force(seed):
     assert r["cmax"] == cb and orc.makespan(p, r["perm"]) == cb
 
 
-def _critical_tree_bfs(p, bound, ub, capped=False):
+def _py_rule(rule, lbf, lbb, un, ub):
+    """MinBranch / MinSum decisions restated from their definitions, on Python lists."""
+    f = [int(lbf[j]) for j in un]
+    b = [int(lbb[j]) for j in un]
+    if rule == orc.MINBRANCH:
+        kf, kb = sum(v < ub for v in f), sum(v < ub for v in b)
+        if kf != kb:
+            return orc.FWD if kf < kb else orc.BWD
+    return orc.BWD if sum(b) > sum(f) else orc.FWD
+
+
+def _critical_tree_bfs(p, bound, ub, capped=False, rule=None):
     """Count decomposed nodes level by level (breadth first), independent of the DFS."""
     n = p.shape[0]
     kind = orc.LB1 if bound == orc.LB1 else orc.LB2
@@ -356,7 +406,10 @@ def _critical_tree_bfs(p, bound, ub, capped=False):
             b1, b2 = orc.children_bounds(p, np.array(perm, dtype=np.uint8), d1, d2, kind)
             lb = b1 if bound == orc.LB1 else b2
             un = perm[d1:n - d2]
-            d = orc.minmin(lb[0], lb[1], un, cap=ub if capped else orc.INT32_MAX)
+            if rule is None:
+                d = orc.minmin(lb[0], lb[1], un, cap=ub if capped else orc.INT32_MAX)
+            else:
+                d = _py_rule(rule, lb[0], lb[1], un, ub)
             if u == 1:
                 continue
             for j in un:
@@ -382,6 +435,30 @@ def test_proof_mode_node_count_matches_breadth_first_enumeration(bound, seed):
     rc = orc.bb_solve(p, bound=bound, init_ub=opt, capped=True)
     dec_c, _ = _critical_tree_bfs(p, bound, opt, capped=True)
     assert rc["decomposed"] == dec_c
+
+
+@pytest.mark.parametrize("bound,seed", [(orc.LB1, 5), (orc.LB2, 6), (orc.LB2, 7)])
+@pytest.mark.parametrize("rule", [orc.MINBRANCH, orc.MINSUM])
+def test_other_branching_rules_proof_counts(rule, bound, seed):
+    # the DFS under MinBranch / MinSum explores exactly the tree that a
+    # breadth-first enumeration with the rules restated in Python gives
+    p = inputs.make_instance(8, 4, seed)
+    opt, _ = orc.brute_force(p)
+    r = orc.bb_solve(p, bound=bound, init_ub=opt, branching=rule)
+    assert r["outcome"] == orc.PROVEN_NO_BETTER
+    dec, bnd = _critical_tree_bfs(p, bound, opt, rule=rule)
+    assert r["decomposed"] == dec and r["bounded"] == bnd
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("rule", [orc.MINMIN, orc.MINMIN_CAPPED, orc.MINBRANCH, orc.MINSUM])
+def test_every_branching_rule_finds_the_brute_force_optimum(rule, seed):
+    n, m = 8, 4
+    p = inputs.make_instance(n, m, 60 + seed)
+    cb, _ = orc.brute_force(p)
+    for bound in (orc.LB1, orc.LB2):
+        r = orc.bb_solve(p, bound=bound, branching=rule)
+        assert r["cmax"] == cb and orc.makespan(p, r["perm"]) == cb
 
 
 def test_bb_node_limit():
