@@ -94,8 +94,7 @@ def lib():
         L.orc_minmin.restype = ctypes.c_int
         L.orc_minmin.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int32]
         L.orc_branch_rule.restype = ctypes.c_int
-        L.orc_branch_rule.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int32,
-                                      ctypes.c_int32]
+        L.orc_branch_rule.argtypes = [ctypes.c_int, i32p, i32p, u8p, ctypes.c_int, ctypes.c_int32]
         L.orc_bb_solve.restype = ctypes.c_int
         L.orc_bb_solve.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p]
@@ -263,16 +262,16 @@ def minmin(lbf, lbb, unscheduled, cap=INT32_MAX) -> int:
     return int(lib().orc_minmin(n, fp, bp, up, cap))
 
 
-def branch_rule(lbf, lbb, unscheduled, rule, cap=INT32_MAX, ub=INT32_MAX) -> int:
+def branch_rule(lbf, lbb, unscheduled, rule, cap=INT32_MAX) -> int:
     """Direction (0 forward, 1 backward) chosen by branching rule `rule` (MINMIN, MINMIN_CAPPED,
-    MINBRANCH or MINSUM)."""
+    MINBRANCH or MINSUM); cap is the solve's initial incumbent."""
     n = len(lbf)
     F, fp = _i32(lbf)
     B, bp = _i32(lbb)
     un = np.zeros(n, dtype=np.uint8)
     un[list(unscheduled)] = 1
     U, up = _u8(un)
-    return int(lib().orc_branch_rule(n, fp, bp, up, int(rule), int(cap), int(ub)))
+    return int(lib().orc_branch_rule(n, fp, bp, up, int(rule), int(cap)))
 
 
 def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None, branching=None):

@@ -451,15 +451,18 @@ int orc_minmin(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un,
 /* The other dynamic branching rules that Table 4 names for earlier solvers
  * of the same problem (the paper names them without defining them; these
  * are this oracle's readings):
- *   MinBranch: choose the set with fewer children whose bound is below the
- *     incumbent ub (fewer subproblems to explore); on a tie the set with the
- *     larger sum of bounds; on a further tie, forward.
+ *   MinBranch: choose the set with fewer children whose bound is below c
+ *     (fewer subproblems to explore); on a tie the set with the larger sum
+ *     of bounds; on a further tie, forward.  c is the solve's initial
+ *     incumbent, a constant like the capped MinMin's: the intervals of
+ *     Section 2.6 number the leaves of one fixed tree, so a node's decision
+ *     may not depend on the incumbent as it improves.
  *   MinSum: choose the set whose children leave the smaller total gap
  *     sum(ub - LB) to the incumbent.  Both sets hold the same children count,
  *     so this is the set with the larger sum of bounds; on a tie, forward.
- * rule: 0 MinMin, 1 MinMin on min(LB, cap), 2 MinBranch, 3 MinSum. */
+ * rule: 0 MinMin, 1 MinMin on min(LB, cap), 2 MinBranch below cap, 3 MinSum. */
 int orc_branch_rule(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t *un, int rule,
-                    int32_t cap, int32_t ub)
+                    int32_t cap)
 {
     if (rule == 0) return orc_minmin(n, lbf, lbb, un, INT32_MAX);
     if (rule == 1) return orc_minmin(n, lbf, lbb, un, cap);
@@ -467,8 +470,8 @@ int orc_branch_rule(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t
     int64_t sf = 0, sb = 0;
     for (int j = 0; j < n; ++j) {
         if (!un[j]) continue;
-        kf += lbf[j] < ub;
-        kb += lbb[j] < ub;
+        kf += lbf[j] < cap;
+        kb += lbb[j] < cap;
         sf += lbf[j];
         sb += lbb[j];
     }
@@ -513,7 +516,7 @@ static void bb_dfs(orc_bb *S, const int32_t *perm, int d1, int d2)
     if (u == 1) S->leaves += 2;
     for (int j = 0; j < n; ++j) un[j] = 0;
     for (int i = d1; i < n - d2; ++i) un[perm[i]] = 1;
-    int dir = orc_branch_rule(n, lb, lb + n, un, S->rule, S->cap, S->ub);
+    int dir = orc_branch_rule(n, lb, lb + n, un, S->rule, S->cap);
     const int32_t *lbd = lb + dir * n;
 
     /* prune at bounding time against the current incumbent */

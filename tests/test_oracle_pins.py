@@ -304,27 +304,27 @@ def test_other_rules_on_the_worked_example():
     ub = g["incumbent"]
     want = orc.BWD if g["decision"] == "backward" else orc.FWD
     for rule in (orc.MINMIN, orc.MINBRANCH, orc.MINSUM):
-        assert orc.branch_rule(lbf, lbb, jobs, rule, ub=ub) == want
+        assert orc.branch_rule(lbf, lbb, jobs, rule, cap=ub) == want
 
 
 def test_branching_rules_disagree_by_hand():
     # hand-made bound vectors on which the rules part ways
     # MinMin: the minimum 16 occurs only backward -> forward.  MinBranch with
-    # incumbent 18: two forward children survive, one backward -> backward.
+    # initial incumbent 18: two forward children below it, one backward -> backward.
     # MinSum: 64 forward against 66 backward -> backward.
     lbf, lbb = [17, 17, 30], [16, 25, 25]
-    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINMIN, ub=18) == orc.FWD
-    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, ub=18) == orc.BWD
-    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, ub=18) == orc.BWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINMIN, cap=18) == orc.FWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, cap=18) == orc.BWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, cap=18) == orc.BWD
     # MinBranch backward (1 survivor of incumbent 20 against 2); MinSum forward (111 > 72)
     lbf, lbb = [10, 11, 90], [12, 30, 30]
-    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, ub=20) == orc.BWD
-    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, ub=20) == orc.FWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINBRANCH, cap=20) == orc.BWD
+    assert orc.branch_rule(lbf, lbb, [0, 1, 2], orc.MINSUM, cap=20) == orc.FWD
     # MinBranch tie (one survivor each) -> larger sum (40 > 32) -> forward
-    assert orc.branch_rule([10, 30], [12, 20], [0, 1], orc.MINBRANCH, ub=15) == orc.FWD
+    assert orc.branch_rule([10, 30], [12, 20], [0, 1], orc.MINBRANCH, cap=15) == orc.FWD
     # equal sums -> forward under both
     assert orc.branch_rule([5, 8], [6, 7], [0, 1], orc.MINSUM) == orc.FWD
-    assert orc.branch_rule([5, 8], [6, 7], [0, 1], orc.MINBRANCH, ub=7) == orc.FWD
+    assert orc.branch_rule([5, 8], [6, 7], [0, 1], orc.MINBRANCH, cap=7) == orc.FWD
     # only unscheduled jobs count
     assert orc.branch_rule([1, 50, 50], [1, 40, 40], [1, 2], orc.MINSUM) == orc.FWD
 
