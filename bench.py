@@ -205,7 +205,67 @@ def solve_leg(pfsp, seeds=range(1, 11)):
             "time_to_proof_s": tot_proof, "time_to_optimum_from_neh_s": tot_find,
             "decomposed_nodes": tot_nodes, "decomposed_nodes_per_s": tot_nodes / max(tot_proof, 1e-9),
             "counts_and_optima_match_oracle": bool(exact), "per_seed": per,
-            "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds)}
+            "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds),
+            "branching_rules": rules_leg(pfsp, gold, seeds),
+            "heuristic_threads": heuristic_leg(pfsp, gold, seeds)}
+
+
+def heuristic_leg(pfsp, gold, seeds, threads=4):
+    """Finding mode from NEH with and without the host heuristic threads (Section 4.2):
+    device time and wall time to the proven optimum, nodes decomposed, and what the threads
+    contributed.  Node counts differ between runs here, so only the optima are checked."""
+    from paper_2012_09511_gb300 import inputs
+    out = {"threads": threads}
+    for name, t in (("without", 0), ("with", threads)):
+        kern = wall = 0.0
+        nodes, improved, exact = 0, 0, True
+        for seed in seeds:
+            g = gold[seed]
+            inst = pfsp.pfsp_load_instance(inputs.make_instance(20, 10, seed))
+            r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, heuristic_threads=t, heuristic_seed=seed)
+            exact &= r["cmax"] == g["optimum"] and r["outcome"] == pfsp.PFSP_OPTIMAL
+            kern += r["kernel_seconds"]
+            wall += r["seconds"]
+            nodes += r["decomposed"]
+            improved += int(r["heuristic_improvements"] > 0)
+        out[name] = {"time_to_optimum_kernel_s": kern, "time_to_optimum_wall_s": wall, "decomposed_nodes": nodes,
+                     "seeds_improved_by_threads": improved, "optima_match_oracle": bool(exact)}
+    return out
+
+
+def rules_leg(pfsp, gold, seeds):
+    """The same seeds under the other branching rules (capped MinMin, MinBranch, MinSum):
+    time-to-proof at the optimum (counts checked against the oracle's where recorded) and
+    time to the optimum from NEH."""
+    from paper_2012_09511_gb300 import inputs
+    path = os.path.join(ROOT, "tests", "golden", "solve_20x10_rules.json")
+    rg = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            rg = {r["seed"]: r for r in json.load(f)["results"]}
+    out = {}
+    for name, rule in (("minmin_capped", pfsp.PFSP_MINMIN_CAPPED), ("minbranch", pfsp.PFSP_MINBRANCH),
+                       ("minsum", pfsp.PFSP_MINSUM)):
+        proof = find = 0.0
+        nodes, exact, checked = 0, True, 0
+        for seed in seeds:
+            g = gold[seed]
+            inst = pfsp.pfsp_load_instance(inputs.make_instance(20, 10, seed))
+            r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, init_ub=g["optimum"], branching=rule)
+            f = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, branching=rule)
+            want = g["proof_capped_decomposed"] if name == "minmin_capped" else \
+                rg.get(seed, {}).get(name, {}).get("decomposed")
+            ok = f["cmax"] == g["optimum"] and r["outcome"] == pfsp.PFSP_PROVEN_NO_BETTER
+            if want is not None:
+                ok &= r["decomposed"] == want
+                checked += 1
+            exact &= ok
+            proof += r["kernel_seconds"]
+            find += f["kernel_seconds"]
+            nodes += r["decomposed"]
+        out[name] = {"time_to_proof_s": proof, "time_to_optimum_from_neh_s": find, "decomposed_nodes": nodes,
+                     "counts_checked": checked, "counts_and_optima_match_oracle": bool(exact)}
+    return out
 
 
 def batch_leg(pfsp):

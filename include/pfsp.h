@@ -53,9 +53,18 @@ extern "C" {
 #define PFSP_LB1 1   /* one-machine bound, Section 2.4 steps 1-4 */
 #define PFSP_LB2 2   /* two-machine Johnson bound over all m(m-1)/2 machine pairs, Section 2.4 */
 
-/* MinMin variants (Section 2.3). */
-#define PFSP_MINMIN 0          /* the paper's rule on the exact bounds of all children */
+/* Dynamic branching rules: MinMin (Section 2.3) and its capped variant, and
+ * readings of MinBranch and MinSum, which Table 4 names for earlier solvers
+ * without defining them.  Every rule compares the two children sets of a
+ * node; a tie goes to the set with the larger sum of bounds, then forward. */
+#define PFSP_MINMIN 0          /* the paper's rule on the exact bounds of all children: the set
+                                  where the smallest bound of both sets occurs less often */
 #define PFSP_MINMIN_CAPPED 1   /* the same rule on min(bound, incumbent) */
+#define PFSP_MINBRANCH 2       /* the set with fewer children below the solve's initial incumbent
+                                  (fewer subproblems to explore) */
+#define PFSP_MINSUM 3          /* the set whose children leave the smaller total gap sum(c - LB) to
+                                  the incumbent c: with as many children in both sets, the set with
+                                  the larger sum of bounds */
 
 typedef struct pfsp_instance pfsp_instance; /* opaque, owned by the library */
 
@@ -128,6 +137,14 @@ typedef struct {
     /* pfsp_solve only: 32-pair slots swept by LB2, summed over decompositions
      * (fewer than decomposed x ceil(m(m-1)/2 / 32) with PFSP_EARLY_EXIT). */
     uint64_t lb2_slots;
+    /* pfsp_solve with heuristic_threads only: times the host threads lowered
+     * the incumbent, explorer nodes promoted to complete schedules, the best
+     * makespan the threads found below the initial incumbent (INT32_MAX:
+     * none), and the snapshot rounds the explorers answered. */
+    uint64_t heuristic_improvements;
+    uint64_t promoted;
+    int32_t heuristic_cmax;
+    int32_t snapshots;
 } pfsp_stats_t;
 
 /*
@@ -142,9 +159,15 @@ typedef struct {
  *                every check_every iterations per explorer); 0 = no limit.
  *   time_limit_s stop after this many seconds of device time; 0 = no limit.
  *   bound        PFSP_LB1 or PFSP_LB2 (Section 2.4).
- *   branching    PFSP_MINMIN (default) or PFSP_MINMIN_CAPPED: the MinMin rule
- *                on min(bound, c) with c the solve's initial incumbent (a
- *                constant, so that every node's decision is fixed for the run).
+ *   branching    PFSP_MINMIN (default), PFSP_MINMIN_CAPPED (the MinMin rule
+ *                on min(bound, c) with c the solve's initial incumbent, a
+ *                constant, so that every node's decision is fixed for the
+ *                run), PFSP_MINBRANCH or PFSP_MINSUM.  MinBranch counts the
+ *                children below that same constant c: the explorers'
+ *                intervals number the leaves of one fixed tree (Section
+ *                2.6), so no decision may depend on the incumbent as it
+ *                improves.  PFSP_EARLY_EXIT is refused with PFSP_MINSUM (the
+ *                skipped sweep could change its decision).
  *   warps_per_sm explorers per SM; 0 = as many as fit in shared memory (at
  *                most 12).
  *   check_every  iterations between limit checks and length publications
@@ -185,7 +208,13 @@ typedef struct {
     int phase_timers;     /* 1: fill pfsp_stats_t.phase_cycles (reads the SM clock at every phase
                              boundary, which slows the solve down several times: for relative
                              profiling only); 0 (default): off */
-    int reserved[7];
+    int heuristic_threads; /* pfsp_solve / pfsp_solve_resumable: host threads running the iterated
+                              greedy beside the explorer pool (Section 4.2's heuristic threads);
+                              0 (default): none.  Their improved schedules lower the explorers'
+                              incumbent, so node counts then vary from run to run: a
+                              finding-mode option.  The optimum found stays exact. */
+    int heuristic_seed;   /* seed of the heuristic threads' random choices */
+    int reserved[5];
 } pfsp_options;
 
 void pfsp_default_options(pfsp_options *opt);
@@ -419,6 +448,25 @@ int pfsp_learn_pair_order(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_
  */
 int pfsp_learn_lb2_pairs(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_nodes, const uint8_t *perm,
                          const uint8_t *d1, const uint8_t *d2, int keep, int32_t *pairs);
+
+/*
+ * Host heuristic (Section 4.2's heuristic threads run a local search from
+ * diversified starting points; this is the search they run here): the
+ * iterated greedy of Ruiz and Stuetzle (2007) on the instance p (n x m,
+ * job-major, as pfsp_load_instance), from `start` (a permutation of 0..n-1,
+ * or NULL: the NEH schedule), for `iterations` iterations with the random
+ * choices of `seed` (the same inputs give the same result).  Each iteration
+ * removes 4 random jobs, reinserts each at its best position, improves the
+ * schedule by insertion local search and accepts it by a constant-temperature
+ * annealing test.  best_perm (n int32) and *best_cmax receive the best
+ * schedule seen, never worse than the start after its local search.  Host
+ * code only: needs no GPU.
+ * Errors: PFSP_ERR_INVALID (NULL output, n < 1, m < 1, iterations < 0, a
+ * negative time, a start that is not a permutation), PFSP_ERR_UNSUPPORTED
+ * (n > 64).
+ */
+int pfsp_iterated_greedy(const int32_t *p, int n, int m, const int32_t *start, int64_t iterations,
+                         uint64_t seed, int32_t *best_perm, int32_t *best_cmax);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);

@@ -36,7 +36,8 @@ struct ExplorerSmem {
     int etop;
     unsigned seq;   // sequence number of this explorer's last steal request
     int lvl;        // start level of the interval (-1: the first level below which D is all zero)
-    int pad[5];
+    int last_d1, last_d2;  // depths of the node staged in perm (the last one decomposed)
+    int pad[3];
     float score[64];   // descend-first logits of the children being ordered
     float sscore[16];  // summed pair probabilities per LB2 slot
     int sorder[16];    // LB2 slot order of the current node
@@ -49,10 +50,14 @@ struct Stats {
     unsigned long long decomposed, bounded, leaves, pruned, steals, iters, slots;
 };
 
-// LEARNED: the instantiation that runs the ordering network; the plain
-// solver's kernel carries none of its code (nor its register demand).
-template <int NW, int MT, bool LEARNED>
+// KIND selects the instantiation: kKindPlain, kKindLearned (runs the ordering
+// network) or kKindCoop (exchanges with the host heuristic threads).  The
+// plain solver's kernel carries none of the others' code: the explorer loop is
+// bound by instruction fetch, so even code that never runs slows it down.
+template <int NW, int MT, int KIND>
 struct Explorer {
+    static constexpr bool LEARNED = KIND == kKindLearned;
+    static constexpr bool COOP = KIND == kKindCoop;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -69,6 +74,7 @@ struct Explorer {
     long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
     bool timed;        // phase timers on (a.phase != NULL)
     int ub_seen;       // incumbent read at the top of the current iteration
+    int snap_seen;     // last snapshot request of the host heuristic threads answered
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
                         const MlpImage *net_)
@@ -96,6 +102,7 @@ struct Explorer {
         }
         timed = a.phase != nullptr;
         ub_seen = INT_MAX;
+        snap_seen = 0;
         if (lane < kPhases) X.ph[lane] = 0ull;
         t_mark = timed ? clock64() : 0;
         __syncwarp();
@@ -358,6 +365,10 @@ struct Explorer {
             }
             d1 = __popc(fw[0]) + __popc(fw[1]);
             d2 = __popc(bw[0]) + __popc(bw[1]);
+            if (COOP && lane == 0) {
+                X.last_d1 = d1;
+                X.last_d2 = d2;
+            }
             for (int h = 0; h < NW; ++h) {
                 int i = lane + 32 * h;
                 if (i <= I && i < n) {
@@ -412,7 +423,13 @@ struct Explorer {
         tick(counted ? kPhLB2 : kPhInit);
         const int u = cb.u;
 
-        // ---- MinMin (Section 2.3) ----------------------------------------------
+        // ---- branching rule: MinMin (Section 2.3); MinBranch, MinSum (Table 4)
+        // Each rule counts the children of each set at or below a threshold:
+        // MinMin the overall minimum (nothing lies below it), MinBranch the
+        // initial incumbent minus one, MinSum nothing; fewer wins, then the
+        // larger sum of bounds, then forward.
+        const int rule = a.branching;
+        const bool capped = rule == PFSP_MINMIN_CAPPED;
         int vf[NW], vb[NW];
         int mn = INT_MAX;
         for (int h = 0; h < NW; ++h) {
@@ -420,21 +437,25 @@ struct Explorer {
             vf[h] = a.bound == PFSP_LB2 ? cb.lb2f[h] : cb.lb1f[h];
             vb[h] = a.bound == PFSP_LB2 ? cb.lb2b[h] : cb.lb1b[h];
             if (c < u) {
-                int xf = a.capped ? min(vf[h], a.cap) : vf[h];
-                int xb = a.capped ? min(vb[h], a.cap) : vb[h];
+                int xf = capped ? min(vf[h], a.cap) : vf[h];
+                int xb = capped ? min(vb[h], a.cap) : vb[h];
                 mn = min(mn, min(xf, xb));
             }
         }
         mn = __reduce_min_sync(PFSP_FULL, mn);
+        // MinBranch: a child counts when its bound is below the solve's initial
+        // incumbent (a constant: every node's decision is fixed for the run, as
+        // the intervals need); MinSum: no bound (all >= 0) is at or below -1
+        const int thr = rule == PFSP_MINBRANCH ? max(a.cap, 0) - 1 : rule == PFSP_MINSUM ? -1 : mn;
         int cf = 0, cbk = 0;
         long long sf = 0, sb = 0;
         for (int h = 0; h < NW; ++h) {
             int c = lane + 32 * h;
             bool on = c < u;
-            int xf = a.capped ? min(vf[h], a.cap) : vf[h];
-            int xb = a.capped ? min(vb[h], a.cap) : vb[h];
-            cf += __popc(__ballot_sync(PFSP_FULL, on && xf == mn));
-            cbk += __popc(__ballot_sync(PFSP_FULL, on && xb == mn));
+            int xf = capped ? min(vf[h], a.cap) : vf[h];
+            int xb = capped ? min(vb[h], a.cap) : vb[h];
+            cf += __popc(__ballot_sync(PFSP_FULL, on && xf <= thr));
+            cbk += __popc(__ballot_sync(PFSP_FULL, on && xb <= thr));
             sf += on ? xf : 0;
             sb += on ? xb : 0;
         }
@@ -657,7 +678,31 @@ struct Explorer {
             if (a.node_limit > 0 && tot >= (unsigned long long)a.node_limit) atomicCAS(a.stop, 0, 1);
         }
         if (lane == 0 && deadline && global_ns() > deadline) atomicCAS(a.stop, 0, 2);
+        if constexpr (COOP) coop_exchange();
         __syncwarp();
+    }
+
+    // Host heuristic threads (Section 4.2): take their incumbent if it is
+    // better, and answer a snapshot request with the node last decomposed.
+    __device__ void coop_exchange() {
+        int req = 0;
+        if (lane == 0) {
+            const int hub = a.coop->host_ub;
+            req = a.coop->snap_req;
+            if (hub < ub_seen) atomicMin(a.ub, hub);
+        }
+        req = __shfl_sync(PFSP_FULL, req, 0);
+        if (req == snap_seen) return;
+        snap_seen = req;
+        CoopSlot &s = a.coop_slots[me];
+        for (int i = lane; i < n; i += 32) s.perm[i] = (uint8_t)X.perm[i];
+        if (lane == 0) {
+            s.d1 = (uint8_t)X.last_d1;
+            s.d2 = (uint8_t)X.last_d2;
+        }
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) s.seq = req;
     }
 
     // Thief side: pick a victim, post a request, wait (bounded) for the answer.
@@ -762,11 +807,11 @@ struct Explorer {
 // X.D / X.E / X.etop (empty if start >= end), then select, decompose, answer
 // steal requests and steal until no explorer of the instance holds work or
 // the solve is stopped.  Counters are added to a.counters on return.
-template <int NW, int MT, bool LEARNED = false>
+template <int NW, int MT, int KIND = kKindPlain>
 __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const WarpScratch &W, ExplorerSmem &X,
                              int me, const MlpImage *net) {
     const int lane = threadIdx.x & 31;
-    Explorer<NW, MT, LEARNED> ex(a, T, W, X, me, net);
+    Explorer<NW, MT, KIND> ex(a, T, W, X, me, net);
     bool nonempty = false;
     {
         // start < end ?

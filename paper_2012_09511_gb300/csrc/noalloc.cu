@@ -71,8 +71,8 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     if (total >= kMaxTotal) return set_error(PFSP_ERR_UNSUPPORTED, "sum of processing times >= 2^28");
     if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
         return set_error(PFSP_ERR_INVALID, "bound must be PFSP_LB1 or PFSP_LB2");
-    if (opt->branching != PFSP_MINMIN && opt->branching != PFSP_MINMIN_CAPPED)
-        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN or PFSP_MINMIN_CAPPED");
+    if (opt->branching < PFSP_MINMIN || opt->branching > PFSP_MINSUM)
+        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN, PFSP_MINMIN_CAPPED, PFSP_MINBRANCH or PFSP_MINSUM");
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
 
     void *scratch = nullptr;
@@ -105,9 +105,10 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     a.off_rank = L.off_rank;
     a.off_ptab = L.off_ptab;
     a.bound = opt->bound;
-    a.capped = opt->branching == PFSP_MINMIN_CAPPED;
+    a.branching = opt->branching;
     a.cap = ub0;
     if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs the plain solver only");
+    if (opt->heuristic_threads) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs no heuristic threads");
     a.warp_words = (warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2) + 7) & ~7;
     a.warp_base = (a.tab_words + 7) & ~7;
     const int per_warp = a.warp_words + kExplorerWords;

@@ -34,7 +34,7 @@ struct InstDesc {
 struct BatchArgs {
     const InstDesc *desc;
     int count;
-    int bound, capped;
+    int bound, branching;
     int K, row_stride, warp_stride, max_tab_words;
     uint8_t *rows_job;
     int32_t *rows_lb;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
                 sa.off_ptab = d.off_ptab;
                 sa.warp_words = d.warp_words;
                 sa.bound = b.bound;
-                sa.capped = b.capped;
+                sa.branching = b.branching;
                 sa.cap = d.cap;
                 sa.K = b.K;
                 sa.row_stride = b.row_stride;
@@ -304,10 +304,11 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     if (count == 0) return PFSP_OK;
     if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
         return set_error(PFSP_ERR_INVALID, "bound must be PFSP_LB1 or PFSP_LB2");
-    if (opt->branching != PFSP_MINMIN && opt->branching != PFSP_MINMIN_CAPPED)
-        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN or PFSP_MINMIN_CAPPED");
+    if (opt->branching < PFSP_MINMIN || opt->branching > PFSP_MINSUM)
+        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN, PFSP_MINMIN_CAPPED, PFSP_MINBRANCH or PFSP_MINSUM");
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs the plain solver only");
+    if (opt->heuristic_threads) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs no heuristic threads");
     int dev = 0;
     cudaGetDevice(&dev);
     for (int i = 0; i < count; ++i) {
@@ -375,7 +376,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     b.desc = (const InstDesc *)(B + o_desc);
     b.count = count;
     b.bound = opt->bound;
-    b.capped = opt->branching == PFSP_MINMIN_CAPPED;
+    b.branching = opt->branching;
     b.K = K;
     b.row_stride = rs;
     b.warp_stride = P.warp_stride;

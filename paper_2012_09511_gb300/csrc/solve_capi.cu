@@ -7,9 +7,12 @@
 #include <chrono>
 #include <climits>
 #include <cstring>
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include "bound_device.cuh"
+#include "heuristic.h"
 #include "pfsp_internal.h"
 #include "solve_internal.h"
 
@@ -113,8 +116,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (!inst || !opt || !best_cmax || !outcome) return set_error(PFSP_ERR_INVALID, "NULL argument");
     if (opt->bound != PFSP_LB1 && opt->bound != PFSP_LB2)
         return set_error(PFSP_ERR_INVALID, "bound must be PFSP_LB1 or PFSP_LB2");
-    if (opt->branching != PFSP_MINMIN && opt->branching != PFSP_MINMIN_CAPPED)
-        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN or PFSP_MINMIN_CAPPED");
+    if (opt->branching < PFSP_MINMIN || opt->branching > PFSP_MINSUM)
+        return set_error(PFSP_ERR_INVALID, "branching must be PFSP_MINMIN, PFSP_MINMIN_CAPPED, PFSP_MINBRANCH or PFSP_MINSUM");
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->bound == PFSP_LB2 && !inst->lb2_ok)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
@@ -122,6 +125,12 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         return set_error(PFSP_ERR_INVALID, "unknown bits in learned");
     if ((opt->learned & PFSP_EARLY_EXIT_SLOTS) && !(opt->learned & PFSP_EARLY_EXIT))
         return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT_SLOTS needs PFSP_EARLY_EXIT");
+    if ((opt->learned & PFSP_EARLY_EXIT) && opt->branching == PFSP_MINSUM)
+        return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT keeps the tree of MinMin and MinBranch only");
+    if (opt->heuristic_threads < 0 || opt->heuristic_threads > 256)
+        return set_error(PFSP_ERR_INVALID, "heuristic_threads must be in 0..256");
+    if (opt->heuristic_threads && (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)))
+        return set_error(PFSP_ERR_UNSUPPORTED, "heuristic threads run beside the plain solver only");
     const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
     int net_m = 0, net_D0 = 0, net_O = 0;
     if (use_net) {
@@ -179,7 +188,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.off_rank = L.off_rank;
     a.off_ptab = L.off_ptab;
     a.bound = opt->bound;
-    a.capped = opt->branching == PFSP_MINMIN_CAPPED;
+    a.branching = opt->branching;
     a.cap = resuming ? rh.cap : ub0;
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
     // the network's inference image: every output column when it orders the
@@ -197,9 +206,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.learned = opt->learned;
     a.learn_depth = opt->learn_depth > 0 ? opt->learn_depth : n;
     a.warp_words = (a.warp_words + 7) & ~7;  // keeps every warp's scratch 32-byte aligned
-    a.net_base = (a.tab_words + 7) & ~7;
-    a.net_words = 0;
-    a.warp_base = a.net_base;
+    a.warp_base = (a.tab_words + 7) & ~7;
     const int per_warp = a.warp_words + (solve_warp_words(n, m, opt->bound) -
                                          warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2));
     int dev = 0, nsm = 1, optin = 48 * 1024;
@@ -226,6 +233,17 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "explorer state does not fit in shared memory");
     size_t smem = (size_t)(a.warp_base + warps * per_warp_eff) * 4;
+    // host heuristic threads (Section 4.2), exchanging with the explorers
+    // through host-mapped memory; a.coop also selects their kernel
+    std::unique_ptr<HeuristicPool> hp;
+    std::vector<int> h_start;
+    if (opt->heuristic_threads > 0) {
+        hp.reset(new HeuristicPool(n, m, inst->p_host, opt->heuristic_threads, (uint64_t)(uint32_t)opt->heuristic_seed));
+        if (!hp->ok()) return set_error(PFSP_ERR_OOM, "host-mapped memory for the heuristic threads");
+        a.coop = hp->device_shared();
+        if ((int)neh_perm.size() == n) h_start = neh_perm;
+        else neh(n, m, inst->p_host, h_start);
+    }
     int per_sm = solve_occupancy(a, warps, smem);
     if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "solve kernel cannot be resident (occupancy 0)");
     const int blocks = nsm * per_sm;
@@ -237,6 +255,11 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.inst_perm = nullptr;
     a.perm_lock = nullptr;
     a.perm_cmax = nullptr;
+
+    if (hp) {
+        if (!hp->attach(K)) return set_error(PFSP_ERR_OOM, "host-mapped memory for the heuristic threads");
+        a.coop_slots = hp->device_slots();
+    }
 
     // initial partition of [0, n!): equal chunks of the first L levels
     int Lv = 0;
@@ -368,6 +391,19 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess) e = launch_solve(a, blocks, warps, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess && hp) {
+        // the heuristic threads search while the explorers run; this thread
+        // drives the snapshots until the kernel is done (before the result
+        // copies below, which wait for it)
+        hp->start(ub0, h_start);
+        cudaError_t q;
+        while ((q = cudaEventQuery(ev1)) == cudaErrorNotReady) {
+            hp->tick();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        hp->stop();
+        if (q != cudaSuccess) e = q;
+    }
     int rsc[6];
     unsigned long long cnt[8], ph[kPhases];
     if (e == cudaSuccess) e = cudaMemcpyAsync(rsc, sc, sizeof(rsc), cudaMemcpyDeviceToHost, st);
@@ -391,17 +427,25 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         e = cudaMemcpy(bp.data(), a.best_perm + (size_t)eid * 64, 64, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "pfsp_solve readback: %s", cudaGetErrorString(e));
     }
+    // the best schedule: the explorers' record when it reaches the final
+    // incumbent, else the heuristic threads' (whose makespan the explorers
+    // took as their incumbent, or found after the explorers stopped at a
+    // limit), else the initial one
+    std::vector<int> hperm;
+    const int hc = hp ? hp->best(&hperm) : INT_MAX;
+    const int best = std::min(final_ub, hc);
+    const bool dev_best = found && (int)(key >> 32) == best;
+    const bool heur_best = !dev_best && hc == best && hc != INT_MAX;
+    const bool have_perm = dev_best || heur_best || from_neh;
+    std::vector<int> fperm(n, -1);
+    for (int j = 0; j < n && have_perm; ++j) fperm[j] = dev_best ? bp[j] : heur_best ? hperm[j] : neh_perm[j];
     if (rsc[2] == 1) *outcome = PFSP_LIMIT_NODES;
     else if (rsc[2] == 2) *outcome = PFSP_LIMIT_TIME;
-    else if (found || from_neh) *outcome = PFSP_OPTIMAL;
+    else if (have_perm) *outcome = PFSP_OPTIMAL;
     else *outcome = PFSP_PROVEN_NO_BETTER;
-    *best_cmax = final_ub;
-    if (best_perm) {
-        if (found)
-            for (int j = 0; j < n; ++j) best_perm[j] = bp[j];
-        else if (from_neh)
-            for (int j = 0; j < n; ++j) best_perm[j] = neh_perm[j];
-    }
+    *best_cmax = best;
+    if (best_perm && have_perm)
+        for (int j = 0; j < n; ++j) best_perm[j] = fperm[j];
     if (want_ckpt) {
         *rio->ckpt = nullptr;
         *rio->ckpt_bytes = 0;
@@ -444,10 +488,10 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         h.bound = opt->bound;
         h.branching = opt->branching;
         h.cap = a.cap;
-        h.ub = final_ub;
+        h.ub = best;
         h.count = (int32_t)(out.size() / kCkptRecord);
-        h.have_perm = (found || from_neh) ? 1 : 0;
-        for (int j = 0; j < n; ++j) h.best_perm[j] = (uint8_t)(found ? bp[j] : (from_neh ? neh_perm[j] : 0xff));
+        h.have_perm = have_perm ? 1 : 0;
+        for (int j = 0; j < n; ++j) h.best_perm[j] = (uint8_t)(have_perm ? fperm[j] : 0xff);
         const size_t bytes = sizeof(h) + out.size();
         uint8_t *buf = (uint8_t *)malloc(bytes);
         if (!buf) return set_error(PFSP_ERR_OOM, "host allocation of the checkpoint failed");
@@ -475,8 +519,12 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     inst->stats.iterations = cnt[5];
     inst->stats.lb2_slots = cnt[7];
     inst->stats.kernel_seconds = ms * 1e-3;
-    inst->stats.final_ub = final_ub;
+    inst->stats.final_ub = best;
     inst->stats.explorers = K;
+    inst->stats.heuristic_improvements = hp ? hp->improvements() : 0;
+    inst->stats.promoted = hp ? hp->promoted() : 0;
+    inst->stats.heuristic_cmax = hc;
+    inst->stats.snapshots = hp ? hp->snapshots() : 0;
     for (int p = 0; p < kPhases; ++p) inst->stats.phase_cycles[p] = ph[p];
     inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return PFSP_OK;

@@ -21,6 +21,11 @@ constexpr unsigned long long kNoRequest = ~0ull;  // empty mailbox
 constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
 #define PFSP_FWD_DIR 0
 
+// Explorer-pool kernel instantiations
+constexpr int kKindPlain = 0;    // the paper's solver
+constexpr int kKindLearned = 1;  // with the ordering network
+constexpr int kKindCoop = 2;     // with the host heuristic threads' exchange
+
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
 // clock costs enough that a timed solve runs several times slower, so they
@@ -34,6 +39,22 @@ constexpr int kPhBranch = 5;   // MinMin, pruning, the new row, leaves (and the 
 constexpr int kPhInit = 6;     // rebuilding the path to a new interval's start
 constexpr int kPhIdle = 7;     // stealing and waiting without work
 constexpr int kPhases = 8;
+
+// Exchange with the host heuristic threads, in host-mapped memory.  The
+// explorers read host_ub and snap_req at their limit checks: host_ub is folded
+// into the device incumbent, and a new snap_req asks each explorer to copy the
+// node it last decomposed into its slot, then to set the slot's seq to it.
+struct CoopShared {
+    volatile int host_ub;
+    volatile int snap_req;
+    int pad[14];
+};
+struct CoopSlot {
+    volatile int seq;  // snap_req answered
+    uint8_t d1, d2, pad[2];
+    uint8_t perm[64];  // [sigma1 | unscheduled | sigma2]
+};
+static_assert(sizeof(CoopShared) == 64 && sizeof(CoopSlot) == 72, "exchange layout");
 
 // Checkpoint record of one explorer (device and host): [0] valid, [1] start
 // level (0xff: the first level below which the start digits are all zero),
@@ -49,7 +70,7 @@ struct SolveArgs {
     int off_pm, off_tot, off_kl, off_rank, off_ptab;
     int warp_words;  // bound scratch words per warp (excluding explorer words)
     int bound;       // PFSP_LB1 or PFSP_LB2
-    int capped;      // MinMin on min(bound, cap)
+    int branching;   // PFSP_MINMIN, PFSP_MINMIN_CAPPED, PFSP_MINBRANCH or PFSP_MINSUM
     int cap;
     int K;           // explorers = warps in the grid
     int row_stride;       // row elements per explorer (n * n, or the batch's largest n squared)
@@ -94,8 +115,8 @@ struct SolveArgs {
     float inv_scale;      // 1 / (mean machine load) for the network's features
     int mlp_off;          // word offset of the network's scratch from the warp's base
     int learn_depth;      // rows of level < learn_depth are ordered by the network
-    int net_base;         // unused (the image is read from global memory)
-    int net_words;        // unused (0)
+    CoopShared *coop;     // host heuristic threads' exchange (NULL: none)
+    CoopSlot *coop_slots; // [K] the explorers' snapshot slots
     int rows_smem;        // 1: each explorer's rows live in shared memory after its explorer state
 };
 
@@ -112,5 +133,7 @@ cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem,
 // The same for the kernels with the ordering network (solve_learned.cu).
 int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+int solve_occupancy_coop(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve_coop(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 
 }  // namespace pfsp

@@ -6,8 +6,9 @@
 // selected at every level i (the factoradic position of Section 2.6), the
 // branching direction of every level, and per level a row of the jobs still
 // to place with the bound of the child each one makes (INT32_MAX once the
-// child is pruned).  Rows live in global memory (L2 resident); digits and
-// directions in shared memory.
+// child is pruned).  Digits and directions live in shared memory, and so do
+// the rows when they fit without costing explorer warps (else in L2-resident
+// global memory).
 //
 // Work units are factoradic intervals [start, end) of leaf indices.  An
 // explorer decomposes a node only while the node's leftmost leaf lo(node) is
@@ -53,14 +54,16 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
 
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
     if (a.net_image) return solve_occupancy_learned(a, warps, smem);
-    if (a.n <= 32) { PFSP_DISPATCH(1, false, occupancy_t, warps, smem) }
-    PFSP_DISPATCH(2, false, occupancy_t, warps, smem)
+    if (a.coop) return solve_occupancy_coop(a, warps, smem);
+    if (a.n <= 32) { PFSP_DISPATCH(1, kKindPlain, occupancy_t, warps, smem) }
+    PFSP_DISPATCH(2, kKindPlain, occupancy_t, warps, smem)
 }
 
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
     if (a.net_image) return launch_solve_learned(a, blocks, warps, smem, st);
-    if (a.n <= 32) { PFSP_DISPATCH(1, false, launch_solve_t, a, blocks, warps, smem, st) }
-    PFSP_DISPATCH(2, false, launch_solve_t, a, blocks, warps, smem, st)
+    if (a.coop) return launch_solve_coop(a, blocks, warps, smem, st);
+    if (a.n <= 32) { PFSP_DISPATCH(1, kKindPlain, launch_solve_t, a, blocks, warps, smem, st) }
+    PFSP_DISPATCH(2, kKindPlain, launch_solve_t, a, blocks, warps, smem, st)
 }
 
 }  // namespace pfsp

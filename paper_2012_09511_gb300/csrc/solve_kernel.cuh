@@ -1,7 +1,8 @@
 // solve_kernel.cuh -- the explorer-pool kernel template and its launch
-// helpers, instantiated by solve_kernel.cu (plain solver) and
-// solve_learned.cu (solver with the ordering network), two translation units
-// that compile in parallel.
+// helpers, instantiated by solve_kernel.cu (plain solver), solve_learned.cu
+// (solver with the ordering network) and solve_coop.cu (solver exchanging
+// with the host heuristic threads), translation units that compile in
+// parallel.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,8 +11,10 @@
 
 namespace pfsp {
 
-template <int NW, int MT, bool LEARNED>
-__global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) * 32, 1) solve_kernel(SolveArgs a) {
+template <int NW, int MT, int KIND>
+__global__ void __launch_bounds__((KIND == kKindLearned ? kSolveWarpsLearned : kSolveWarps) * 32, 1)
+    solve_kernel(SolveArgs a) {
+    constexpr bool LEARNED = KIND == kKindLearned;
     extern __shared__ __align__(128) int smem[];
     __shared__ uint64_t bar;
     stage_tables(smem, a.tab, a.tab_words, &bar);
@@ -49,21 +52,21 @@ __global__ void __launch_bounds__((LEARNED ? kSolveWarpsLearned : kSolveWarps) *
         X.lvl = lv == 0xff ? -1 : lv;
     }
     __syncwarp();
-    run_explorer<NW, MT, LEARNED>(a, T, W, X, me, LEARNED && a.net_image ? &net : nullptr);
+    run_explorer<NW, MT, KIND>(a, T, W, X, me, LEARNED && a.net_image ? &net : nullptr);
 }
 
-template <int NW, int MT, bool LEARNED>
+template <int NW, int MT, int KIND>
 inline cudaError_t launch_solve_t(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    auto kern = solve_kernel<NW, MT, LEARNED>;
+    auto kern = solve_kernel<NW, MT, KIND>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(warps * 32), args, smem, st);
 }
 
-template <int NW, int MT, bool LEARNED>
+template <int NW, int MT, int KIND>
 inline int occupancy_t(int warps, size_t smem) {
-    auto kern = solve_kernel<NW, MT, LEARNED>;
+    auto kern = solve_kernel<NW, MT, KIND>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem) != cudaSuccess) return 0;

@@ -8,13 +8,13 @@
 namespace pfsp {
 
 int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem) {
-    if (a.n <= 32) { PFSP_DISPATCH(1, true, occupancy_t, warps, smem) }
-    PFSP_DISPATCH(2, true, occupancy_t, warps, smem)
+    if (a.n <= 32) { PFSP_DISPATCH(1, kKindLearned, occupancy_t, warps, smem) }
+    PFSP_DISPATCH(2, kKindLearned, occupancy_t, warps, smem)
 }
 
 cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
-    if (a.n <= 32) { PFSP_DISPATCH(1, true, launch_solve_t, a, blocks, warps, smem, st) }
-    PFSP_DISPATCH(2, true, launch_solve_t, a, blocks, warps, smem, st)
+    if (a.n <= 32) { PFSP_DISPATCH(1, kKindLearned, launch_solve_t, a, blocks, warps, smem, st) }
+    PFSP_DISPATCH(2, kKindLearned, launch_solve_t, a, blocks, warps, smem, st)
 }
 
 }  // namespace pfsp

@@ -33,6 +33,8 @@ PFSP_LB1 = 1
 PFSP_LB2 = 2
 PFSP_MINMIN = 0
 PFSP_MINMIN_CAPPED = 1
+PFSP_MINBRANCH = 2
+PFSP_MINSUM = 3
 INT32_MAX = 2**31 - 1
 
 
@@ -47,7 +49,9 @@ class pfsp_stats_t(ctypes.Structure):
                 ("leaves", ctypes.c_uint64), ("pruned", ctypes.c_uint64), ("steals", ctypes.c_uint64),
                 ("iterations", ctypes.c_uint64), ("seconds", ctypes.c_double),
                 ("kernel_seconds", ctypes.c_double), ("final_ub", ctypes.c_int32),
-                ("explorers", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8), ("lb2_slots", ctypes.c_uint64)]
+                ("explorers", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8), ("lb2_slots", ctypes.c_uint64),
+                ("heuristic_improvements", ctypes.c_uint64), ("promoted", ctypes.c_uint64),
+                ("heuristic_cmax", ctypes.c_int32), ("snapshots", ctypes.c_int32)]
 
     PHASES = ("service", "select", "decode", "lb1", "lb2", "branch", "init", "idle")
 
@@ -68,7 +72,7 @@ class pfsp_options(ctypes.Structure):
                 ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
                 ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("phase_timers", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("heuristic_threads", ctypes.c_int), ("heuristic_seed", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -99,6 +103,9 @@ _lib.pfsp_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.POIN
 _lib.pfsp_solve_batch.restype = ctypes.c_int
 _lib.pfsp_solve_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options), _vp,
                                   _vp, _vp, _vp, ctypes.POINTER(pfsp_stats_t)]
+_lib.pfsp_iterated_greedy.restype = ctypes.c_int
+_lib.pfsp_iterated_greedy.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_uint64,
+                                      _vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.pfsp_autotune_batch.restype = ctypes.c_int
 _lib.pfsp_autotune_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options),
                                      ctypes.c_int, ctypes.POINTER(pfsp_options)]
@@ -254,6 +261,18 @@ def pfsp_solve(inst: Instance, opts: pfsp_options = None, **fields) -> dict:
     r = dict(cmax=best.value, perm=np.array(perm[:], dtype=np.int32), outcome=out.value)
     r.update(pfsp_stats(inst))
     return r
+
+
+def pfsp_iterated_greedy(p, iterations, seed=0, start=None):
+    """Host iterated greedy on p ([n, m] job-major) from `start` (None: NEH).
+    Returns (cmax, perm)."""
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    n, m = p.shape
+    s = None if start is None else np.ascontiguousarray(start, dtype=np.int32)
+    perm = np.full(n, -1, dtype=np.int32)
+    c = ctypes.c_int32()
+    _check(_lib.pfsp_iterated_greedy(_ptr(p), n, m, _ptr(s), int(iterations), int(seed), _ptr(perm), ctypes.byref(c)))
+    return c.value, perm
 
 
 def pfsp_solve_noalloc(p, opts: pfsp_options = None, **fields) -> dict:

@@ -56,12 +56,14 @@ def test_small_uneven_batch_optima(pf, bound):
         _check_perm(p, r["perms"][i], want)
 
 
-def test_small_batch_proof_mode_counts(pf):
+@pytest.mark.parametrize("rule", ["MINMIN", "MINBRANCH", "MINSUM"])
+def test_small_batch_proof_mode_counts(pf, rule):
     ps = _small_batch(18)
     opts = [orc.bb_solve(p, bound=2)["cmax"] for p in ps]
-    want = sum(orc.bb_solve(p, bound=2, init_ub=o)["decomposed"] for p, o in zip(ps, opts))
+    br = getattr(orc, rule)
+    want = sum(orc.bb_solve(p, bound=2, init_ub=o, branching=br)["decomposed"] for p, o in zip(ps, opts))
     insts = [pf.pfsp_load_instance(p) for p in ps]
-    r = pf.pfsp_solve_batch(insts, bound=2, init_ubs=opts)
+    r = pf.pfsp_solve_batch(insts, bound=2, init_ubs=opts, branching=getattr(pf, "PFSP_" + rule))
     assert (r["outcomes"] == pf.PFSP_PROVEN_NO_BETTER).all()
     assert (r["cmax"] == np.array(opts)).all()
     assert r["stats"]["decomposed"] == want

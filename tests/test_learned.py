@@ -119,21 +119,23 @@ def test_learned_solver_is_exact(pf, n, m, seed):
 def test_early_exit_keeps_the_tree(pf, n, m, seed):
     # a node one of whose directions is entirely at or above the incumbent
     # has no child below it under either MinMin rule, so stopping its LB2
-    # sweep there changes no count, capped or not, whatever the pair order
+    # sweep there changes no count, capped or not, whatever the pair order;
+    # under MinBranch that direction has no survivor, so it is chosen unless
+    # the other has none either, and then no child is explored either way
     p = inputs.make_instance(n, m, seed)
     inst = pf.pfsp_load_instance(p)
     opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
     rng = np.random.default_rng(seed)
     for order in (None, rng.permutation(m * (m - 1) // 2)):
         pf.pfsp_set_pair_order(inst, order)
-        for capped in (False, True):
-            want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, capped=capped)
+        for rule in ("MINMIN", "MINMIN_CAPPED", "MINBRANCH"):
+            want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, branching=getattr(orc, rule))
             for flags in (pf.PFSP_EARLY_EXIT, pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_SLOTS):
                 r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=flags,
-                                  branching=pf.PFSP_MINMIN_CAPPED if capped else pf.PFSP_MINMIN)
+                                  branching=getattr(pf, "PFSP_" + rule))
                 assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
                 got = (r["decomposed"], r["bounded_children"], r["pruned"])
-                assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, capped, flags)
+                assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, rule, flags)
         f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, learned=pf.PFSP_EARLY_EXIT)
         assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
 

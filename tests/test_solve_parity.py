@@ -79,6 +79,25 @@ def test_capped_minmin_proof_counts(pf, bound):
     assert (r["decomposed"], r["bounded_children"]) == (proof["decomposed"], proof["bounded"])
 
 
+@pytest.mark.parametrize("rule", ["MINBRANCH", "MINSUM"])
+@pytest.mark.parametrize("n,m,bound,seed", [(15, 5, 1, 46), (13, 8, 2, 45), (14, 6, 2, 48), (13, 8, 2, 49)])
+def test_other_branching_rules_proof_counts(pf, rule, n, m, bound, seed):
+    # MinBranch / MinSum (Table 4's rules): the proof tree and every counter
+    # equal the oracle's; finding mode reaches the oracle's optimum
+    br = getattr(pf, "PFSP_" + rule)
+    p = inputs.make_instance(n, m, seed)
+    opt = orc.bb_solve(p, bound=bound)["cmax"]
+    proof = orc.bb_solve(p, bound=bound, init_ub=opt, branching=getattr(orc, rule))
+    inst = pf.pfsp_load_instance(p)
+    r = pf.pfsp_solve(inst, bound=bound, init_ub=opt, branching=br)
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+    assert (r["decomposed"], r["bounded_children"]) == (proof["decomposed"], proof["bounded"])
+    assert r["leaves"] == proof["leaves"] and r["pruned"] == proof["pruned"]
+    g = pf.pfsp_solve(inst, bound=bound, branching=br)
+    assert g["outcome"] == pf.PFSP_OPTIMAL and g["cmax"] == opt
+    _check_perm(p, g)
+
+
 def test_fixed_tree_below_optimum(pf):
     # the paper's fixed-tree runs start from an incumbent at or below the optimum
     p = inputs.make_instance(13, 6, 9)
@@ -182,7 +201,8 @@ def test_phase_timers_and_slot_counter(pf):
 def test_invalid_options(pf):
     p = inputs.make_instance(8, 4, 1)
     inst = pf.pfsp_load_instance(p)
-    for bad in (dict(bound=3), dict(branching=5), dict(node_limit=-1)):
+    for bad in (dict(bound=3), dict(branching=5), dict(branching=-1), dict(node_limit=-1),
+                dict(branching=pf.PFSP_MINSUM, learned=pf.PFSP_EARLY_EXIT)):
         with pytest.raises(pf.PfspError) as e:
             pf.pfsp_solve(inst, **bad)
         assert e.value.code == pf.PFSP_ERR_INVALID
