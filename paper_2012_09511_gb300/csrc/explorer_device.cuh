@@ -490,6 +490,12 @@ struct Explorer {
                 if (lb < prev && !a.inst_perm) {
                     uint8_t *bp = a.best_perm + (size_t)me * 64;
                     for (int q = 0; q < n; ++q) bp[q] = (uint8_t)(q == d1 ? j : X.perm[q]);
+                    if constexpr (COOP) {
+                        // the host heuristic threads promote with the incumbent's order
+                        for (int q = 0; q < n; ++q) a.coop->dev_perm[q] = bp[q];
+                        __threadfence_system();
+                        a.coop->dev_cmax = lb;
+                    }
                     __threadfence();
                     atomicMin(a.best_key, ((unsigned long long)(unsigned)lb << 32) | (unsigned)me);
                 } else if (lb < prev) {

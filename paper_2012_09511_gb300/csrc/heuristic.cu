@@ -181,6 +181,7 @@ HeuristicPool::HeuristicPool(int n, int m, const int32_t *p, int threads, uint64
     shared_ = (CoopShared *)h;
     dshared_ = (CoopShared *)d;
     shared_->host_ub = INT_MAX;
+    shared_->dev_cmax = INT_MAX;
 }
 
 bool HeuristicPool::attach(int explorers) {
@@ -201,6 +202,7 @@ HeuristicPool::~HeuristicPool() {
 void HeuristicPool::start(int ub0, const std::vector<int> &start) {
     ub0_ = ub0;
     best_c_ = ub0;
+    own_c_ = INT_MAX;
     best_ = start;
     shared_->host_ub = ub0;
     IteratedGreedy probe(n_, m_, p_.data(), 0);
@@ -226,6 +228,7 @@ int HeuristicPool::best(std::vector<int> *seq) {
 // explorers fold host_ub into theirs at their next limit check.
 void HeuristicPool::offer(const std::vector<int> &seq, int c) {
     std::lock_guard<std::mutex> g(mu_);
+    if (c < own_c_) own_c_ = c;
     if (c >= best_c_) return;
     best_c_ = c;
     best_ = seq;
@@ -252,6 +255,7 @@ void HeuristicPool::worker(int id) {
 }
 
 void HeuristicPool::tick() {
+    adopt_device_incumbent();
     const double t = now_s();
     if (!pending_) {
         if (t - last_snap_ < kSnapPeriod) return;
@@ -268,6 +272,31 @@ void HeuristicPool::tick() {
     snapshots_ += 1;
     pending_ = false;
     last_snap_ = now_s();
+}
+
+// The explorers' incumbent schedule, when it is better than the threads' best,
+// becomes their best too: promotions complete nodes in its order and the
+// threads restart from it.  It is not counted as an improvement of theirs.
+void HeuristicPool::adopt_device_incumbent() {
+    const int c = shared_->dev_cmax;
+    if (c == dev_seen_) return;
+    dev_seen_ = c;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    std::vector<int> seq(n_);
+    std::vector<char> seen(n_, 0);
+    for (int i = 0; i < n_; ++i) {
+        const int j = shared_->dev_perm[i];
+        if (j >= n_ || seen[j]) return;  // torn by a concurrent writer
+        seen[j] = 1;
+        seq[i] = j;
+    }
+    IteratedGreedy ev(n_, m_, p_.data(), 0);
+    const int mk = ev.makespan(seq.data(), n_);
+    std::lock_guard<std::mutex> g(mu_);
+    if (mk >= best_c_) return;
+    best_c_ = mk;
+    best_ = seq;
+    shared_->host_ub = mk;
 }
 
 // Promote the explorers' nodes to complete schedules: sigma1, then the

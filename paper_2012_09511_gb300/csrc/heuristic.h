@@ -78,6 +78,10 @@ class HeuristicPool {
     void tick();  // called repeatedly by the host thread while the kernel runs
     void stop();
     int best(std::vector<int> *seq);  // best makespan below ub0 (INT32_MAX if none)
+    int own_best() {  // best makespan the threads themselves found below ub0
+        std::lock_guard<std::mutex> g(mu_);
+        return own_c_ < ub0_ ? own_c_ : INT32_MAX;
+    }
     uint64_t improvements() const { return improvements_.load(); }
     uint64_t promoted() const { return promoted_; }
     int snapshots() const { return snapshots_; }
@@ -86,6 +90,7 @@ class HeuristicPool {
     void worker(int id);
     void offer(const std::vector<int> &seq, int c);
     void collect();
+    void adopt_device_incumbent();
 
     int n_, m_, threads_, K_;
     std::vector<int32_t> p_;
@@ -95,7 +100,9 @@ class HeuristicPool {
     std::vector<std::thread> pool_;
     std::atomic<int> stop_{0};
     std::mutex mu_;
-    int best_c_ = 0;
+    int best_c_ = 0;    // best makespan known: the threads' or the explorers'
+    int own_c_ = 0;     // best makespan the threads found
+    int dev_seen_ = INT32_MAX;
     std::vector<int> best_;
     std::vector<std::pair<int, std::vector<int>>> starts_;  // best promoted schedules
     uint64_t next_start_ = 0;

@@ -523,7 +523,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     inst->stats.explorers = K;
     inst->stats.heuristic_improvements = hp ? hp->improvements() : 0;
     inst->stats.promoted = hp ? hp->promoted() : 0;
-    inst->stats.heuristic_cmax = hc;
+    inst->stats.heuristic_cmax = hp ? hp->own_best() : INT_MAX;
     inst->stats.snapshots = hp ? hp->snapshots() : 0;
     for (int p = 0; p < kPhases; ++p) inst->stats.phase_cycles[p] = ph[p];
     inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -43,18 +43,23 @@ constexpr int kPhases = 8;
 // Exchange with the host heuristic threads, in host-mapped memory.  The
 // explorers read host_ub and snap_req at their limit checks: host_ub is folded
 // into the device incumbent, and a new snap_req asks each explorer to copy the
-// node it last decomposed into its slot, then to set the slot's seq to it.
+// node it last decomposed into its slot, then to set the slot's seq to it.  An
+// explorer that lowers the incumbent with a leaf also copies that schedule to
+// dev_perm and then its makespan to dev_cmax (concurrent writers may tear the
+// copy: the host recomputes the makespan of what it reads).
 struct CoopShared {
     volatile int host_ub;
     volatile int snap_req;
-    int pad[14];
+    volatile int dev_cmax;
+    int pad[13];
+    uint8_t dev_perm[64];
 };
 struct CoopSlot {
     volatile int seq;  // snap_req answered
     uint8_t d1, d2, pad[2];
     uint8_t perm[64];  // [sigma1 | unscheduled | sigma2]
 };
-static_assert(sizeof(CoopShared) == 64 && sizeof(CoopSlot) == 72, "exchange layout");
+static_assert(sizeof(CoopShared) == 128 && sizeof(CoopSlot) == 72, "exchange layout");
 
 // Checkpoint record of one explorer (device and host): [0] valid, [1] start
 // level (0xff: the first level below which the start digits are all zero),
