@@ -164,8 +164,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(p, perm, d1, d2, sample):
-    """The oracle as it stands, on the host cores, over a bounded sample of the batch."""
+def cpu_baseline(p, perm, d1, d2, sample, total=None):
+    """The oracle as it stands, on the host cores, over a bounded sample of the batch (the
+    first `sample` of its `total` nodes; the node generator is counter-based, so a shorter
+    draw is a prefix of the full batch)."""
     import oracle as orc
     cores = os.cpu_count() or 1
     k = min(sample, len(d1))
@@ -174,7 +176,8 @@ def cpu_baseline(p, perm, d1, d2, sample):
     dt = time.perf_counter() - t
     children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
     return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
-            "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (k, len(d1), dt)}
+            "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (
+                k, total or len(d1), dt)}
 
 
 def solve_leg(pfsp, seeds=range(1, 11)):
@@ -344,7 +347,7 @@ def run_reference(args):
         cpu_baseline(p, perm, d1, d2, min(2000, sample))
     times, children = [], 0
     for _ in range(args.steps):
-        r = cpu_baseline(p, perm, d1, d2, sample)
+        r = cpu_baseline(p, perm, d1, d2, sample, total=args.nodes)
         times.append(r)
     value = statistics.median([t["value"] for t in times])
     step_ms = statistics.median([t["seconds"] for t in times]) * 1e3
