@@ -184,8 +184,10 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
                                      has an LB1 at least the solve's initial incumbent: such a node
                                      has no child below the incumbent under either MinMin rule (the
                                      decided direction holds no minimum below it, so MinMin picks
-                                     it), hence the search tree and every counter are those of the
-                                     full sweep */
+                                     it) nor under MinBranch (it has no child below the incumbent, so
+                                     MinBranch picks it unless the other direction has none either),
+                                     hence the search tree and every counter are those of the full
+                                     sweep; refused with PFSP_MINSUM */
 #define PFSP_EARLY_EXIT_SLOTS 8   /* with PFSP_EARLY_EXIT: also stop the sweep after the first
                                      32-pair slot at which every child of one direction has a pair
                                      term at least the incumbent (same exactness argument); pairs in
