@@ -8,7 +8,10 @@ may import it; the product package never does, and the two share no code.
 
 Functions and the paper passages they follow:
   makespan / completion ... Eq. 1 (Section 2.1)
-  front, back, remain, lb1  Section 2.4, LB1 steps 1-4
+  front, back, remain, lb1  Section 2.4, LB1 steps 1-4 (lb1 minht=True: empty
+                            heads and tails raised to the least upstream /
+                            downstream work of an unscheduled job; not in the
+                            paper)
   lb2, johnson ............ Section 2.4 (two-machine bound, Johnson's rule)
   children_bounds ......... Section 2.3 (forward/backward children), 2.4
   minmin .................. Section 2.3 (MinMin branching rule)
@@ -36,6 +39,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FWD, BWD = 0, 1
 LB1, LB2 = 1, 2
+MINHT = 4  # bit of kind / bound: LB1 with the heads and tails refinement (not in the paper)
 MINMIN, MINMIN_CAPPED, MINBRANCH, MINSUM = 0, 1, 2, 3
 OPTIMAL, PROVEN_NO_BETTER, LIMIT_NODES = 0, 1, 2
 INT32_MAX = 2**31 - 1
@@ -71,7 +75,7 @@ def lib():
         L.orc_remain.argtypes = [ctypes.c_int, ctypes.c_int, i32p, u8p, i32p]
         L.orc_lb1_combine.restype = ctypes.c_int32
         L.orc_lb1_combine.argtypes = [ctypes.c_int, i32p, i32p, i32p]
-        for f in (L.orc_lb1, L.orc_lb2):
+        for f in (L.orc_lb1, L.orc_lb2, L.orc_lb1_minht):
             f.restype = ctypes.c_int32
             f.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int, i32p, ctypes.c_int]
         L.orc_pair_value.restype = ctypes.c_int32
@@ -186,8 +190,9 @@ def _bound(fn, p, sigma1, sigma2):
     return int(fn(n, m, pp, s1, len(sigma1), s2, len(sigma2)))
 
 
-def lb1(p, sigma1, sigma2) -> int:
-    return _bound(lib().orc_lb1, p, sigma1, sigma2)
+def lb1(p, sigma1, sigma2, minht=False) -> int:
+    """LB1 of the node (sigma1, sigma2); minht: with the heads and tails refinement."""
+    return _bound(lib().orc_lb1_minht if minht else lib().orc_lb1, p, sigma1, sigma2)
 
 
 def lb2(p, sigma1, sigma2) -> int:
@@ -234,7 +239,8 @@ def children_bounds(p, perm, d1, d2, kind=LB1 | LB2):
 
 def children_bounds_batch(p, perm, d1, d2, kind=LB1 | LB2, threads=1, pairs=None):
     """Bounds of both children sets of every node; pairs (indices in k < l order)
-    restricts LB2 to those machine pairs (LB2 = max(LB1, their values))."""
+    restricts LB2 to those machine pairs (LB2 = max(LB1, their values)); the MINHT
+    bit of kind refines LB1's empty heads and tails (LB2 = max(that LB1, pairs))."""
     n, m = _shape(p)
     count = len(d1)
     P, pp = _i32(p)
@@ -274,10 +280,13 @@ def branch_rule(lbf, lbb, unscheduled, rule, cap=INT32_MAX) -> int:
     return int(lib().orc_branch_rule(n, fp, bp, up, int(rule), int(cap)))
 
 
-def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None, branching=None):
+def bb_solve(p, bound=LB1, init_ub=INT32_MAX, node_limit=0, capped=False, pairs=None, branching=None,
+             minht=False):
     """Sequential DFS branch-and-bound (LB2 over `pairs` when given).  `branching` is one of
-    MINMIN, MINMIN_CAPPED, MINBRANCH, MINSUM (default: MinMin, capped when `capped`).
+    MINMIN, MINMIN_CAPPED, MINBRANCH, MINSUM (default: MinMin, capped when `capped`); minht
+    refines LB1's empty heads and tails.
     Returns dict(outcome, cmax, perm, decomposed, bounded, leaves, pruned)."""
+    bound = int(bound) | (MINHT if minht else 0)
     rule = (MINMIN_CAPPED if capped else MINMIN) if branching is None else int(branching)
     n, m = _shape(p)
     P, pp = _i32(p)

@@ -40,6 +40,7 @@
 #define ORC_BWD 1
 #define ORC_LB1 1
 #define ORC_LB2 2
+#define ORC_MINHT 4  /* kind / bound bit: the heads and tails refinement (refine_heads_tails) */
 
 #define ORC_OPTIMAL 0
 #define ORC_PROVEN_NO_BETTER 1
@@ -126,6 +127,46 @@ static void node_unscheduled(int n, const int32_t *s1, int d1, const int32_t *s2
     for (int j = 0; j < n; ++j) un[j] = 1;
     for (int i = 0; i < d1; ++i) un[s1[i]] = 0;
     for (int i = 0; i < d2; ++i) un[s2[i]] = 0;
+}
+
+/* The heads and tails refinement of LB1 (not in the paper, which leaves the
+ * front of an empty sigma1 and the back of an empty sigma2 at zero; an
+ * option, off by default).  With sigma1 empty, an unscheduled job j cannot
+ * start on machine k before its own work on machines 0..k-1 is done, so
+ * front[k] is raised to the least such work over the unscheduled jobs; with
+ * sigma2 empty, back[k] is raised to the least work on machines k+1..m-1.
+ * A node without unscheduled jobs is a complete schedule: nothing changes. */
+static void refine_heads_tails(int n, int m, const int32_t *p, const uint8_t *un, int d1, int d2,
+                               int32_t *front, int32_t *back)
+{
+    int any = 0;
+    for (int j = 0; j < n; ++j) any |= un[j];
+    if (!any) return;
+    for (int k = 0; k < m; ++k) {
+        int32_t head = INT32_MAX, tail = INT32_MAX;
+        for (int j = 0; j < n; ++j) {
+            if (!un[j]) continue;
+            int32_t h = 0, t = 0;
+            for (int q = 0; q < k; ++q) h += p[j * m + q];
+            for (int q = k + 1; q < m; ++q) t += p[j * m + q];
+            head = imin(head, h);
+            tail = imin(tail, t);
+        }
+        if (d1 == 0) front[k] = head;
+        if (d2 == 0) back[k] = tail;
+    }
+}
+
+int32_t orc_lb1_minht(int n, int m, const int32_t *p, const int32_t *s1, int d1, const int32_t *s2, int d2)
+{
+    int32_t f[ORC_MAXN], r[ORC_MAXN], b[ORC_MAXN];
+    uint8_t un[ORC_MAXN];
+    node_unscheduled(n, s1, d1, s2, d2, un);
+    orc_front(m, p, s1, d1, f);
+    orc_remain(n, m, p, un, r);
+    orc_back(m, p, s2, d2, b);
+    refine_heads_tails(n, m, p, un, d1, d2, f, b);
+    return orc_lb1_combine(m, f, r, b);
 }
 
 int32_t orc_lb1(int n, int m, const int32_t *p, const int32_t *s1, int d1, const int32_t *s2, int d2)
@@ -325,7 +366,9 @@ int32_t orc_pair_value(int n, int m, const int32_t *p, int k, int l, const int32
  * hold sigma1, [n-d2, n) hold sigma2).  Each child is bounded from scratch:
  * forward child of j is (sigma1 j, sigma2), backward child is (sigma1, j sigma2).
  * Output layout [dir][job]; scheduled jobs get -1.  kind is a bit mask of
- * ORC_LB1 / ORC_LB2; a NULL output is skipped. */
+ * ORC_LB1 / ORC_LB2 / ORC_MINHT; a NULL output is skipped.  With ORC_MINHT,
+ * LB1 takes the refined heads and tails and LB2 is the larger of that LB1 and
+ * the pair values (which keep the plain ones). */
 static void children_bounds_t(const orc_tables *T, int kind, const uint8_t *perm, int d1, int d2,
                               int32_t *lb1, int32_t *lb2)
 {
@@ -354,6 +397,16 @@ static void children_bounds_t(const orc_tables *T, int kind, const uint8_t *perm
             node_unscheduled(n, s1, c1, s2, c2, un);
             orc_front(m, p, s1, c1, f);
             orc_back(m, p, s2, c2, b);
+            if (kind & ORC_MINHT) {
+                int32_t fr[ORC_MAXN], br[ORC_MAXN];
+                for (int k = 0; k < m; ++k) { fr[k] = f[k]; br[k] = b[k]; }
+                refine_heads_tails(n, m, p, un, c1, c2, fr, br);
+                orc_remain(n, m, p, un, r);
+                int32_t v1 = orc_lb1_combine(m, fr, r, br);
+                if (lb1 && (kind & ORC_LB1)) lb1[dir * n + j] = v1;
+                if (lb2 && (kind & ORC_LB2)) lb2[dir * n + j] = imax(lb2_from_parts(T, f, b, un), v1);
+                continue;
+            }
             if (lb1 && (kind & ORC_LB1)) {
                 orc_remain(n, m, p, un, r);
                 lb1[dir * n + j] = orc_lb1_combine(m, f, r, b);
@@ -486,7 +539,7 @@ int orc_branch_rule(int n, const int32_t *lbf, const int32_t *lbb, const uint8_t
 
 typedef struct {
     orc_tables T;
-    int bound;          /* ORC_LB1 or ORC_LB2 */
+    int bound;          /* ORC_LB1 or ORC_LB2, with ORC_MINHT for the refined heads and tails */
     int rule;           /* branching rule, as orc_branch_rule's */
     int32_t cap;        /* the run's initial incumbent */
     int32_t ub;         /* incumbent: only makespans < ub are sought */
@@ -511,7 +564,7 @@ static void bb_dfs(orc_bb *S, const int32_t *perm, int d1, int d2)
     int32_t lb1[2 * ORC_MAXN], lb2[2 * ORC_MAXN];
     for (int i = 0; i < n; ++i) p8[i] = (uint8_t)perm[i];
     children_bounds_t(&S->T, S->bound, p8, d1, d2, lb1, lb2);
-    const int32_t *lb = S->bound == ORC_LB2 ? lb2 : lb1;
+    const int32_t *lb = (S->bound & ORC_LB2) ? lb2 : lb1;
     S->bounded += 2 * u;
     if (u == 1) S->leaves += 2;
     for (int j = 0; j < n; ++j) un[j] = 0;
