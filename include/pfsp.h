@@ -52,6 +52,10 @@ extern "C" {
 /* Bound kinds (bit mask for pfsp_bound_batch; a single value for solves). */
 #define PFSP_LB1 1   /* one-machine bound, Section 2.4 steps 1-4 */
 #define PFSP_LB2 2   /* two-machine Johnson bound over all m(m-1)/2 machine pairs, Section 2.4 */
+#define PFSP_MINHT 4 /* with LB1 or LB2: raise the front of an empty sigma1 (back of an empty sigma2)
+                        to the least work of an unscheduled job on the machines before (after) each
+                        machine -- the heads and tails refinement of LB1, not in the paper, off by
+                        default; LB2 is then the larger of that LB1 and the pair values */
 
 /* Dynamic branching rules: MinMin (Section 2.3) and its capped variant, and
  * readings of MinBranch and MinSum, which Table 4 names for earlier solvers
@@ -92,12 +96,14 @@ void pfsp_free_instance(pfsp_instance *inst);
  * backward child is (sigma1, j sigma2).  Outputs are int32 arrays of
  * num_nodes*2*n entries laid out [node][dir][job] (dir 0 = forward,
  * 1 = backward); entries of scheduled jobs are -1.  kind is a bit mask of
- * PFSP_LB1 | PFSP_LB2; the output of a kind not requested may be NULL and is
- * not touched.  With m = 1 there is no machine pair and LB2 equals LB1.
+ * PFSP_LB1 | PFSP_LB2, optionally with PFSP_MINHT (a separate, generic
+ * kernel); the output of a kind not requested may be NULL and is not
+ * touched.  With m = 1 there is no machine pair and LB2 equals LB1.
  * Bounds are exact int32 values, identical to their definitions.
  * num_nodes = 0 is allowed and does nothing.
  * Errors: PFSP_ERR_INVALID (NULL pointer for a requested output or input,
- * d1 + d2 > n, kind not in 1..3), PFSP_ERR_UNSUPPORTED (LB2 tables too large),
+ * d1 + d2 > n, kind without LB1 or LB2 or with other bits),
+ * PFSP_ERR_UNSUPPORTED (LB2 tables too large),
  * PFSP_ERR_OOM, PFSP_ERR_CUDA.
  */
 int pfsp_bound_batch(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
@@ -216,7 +222,10 @@ typedef struct {
                               incumbent, so node counts then vary from run to run: a
                               finding-mode option.  The optimum found stays exact. */
     int heuristic_seed;   /* seed of the heuristic threads' random choices */
-    int reserved[5];
+    int lb1_minht;        /* 1: LB1 (and the LB1 inside LB2) with the heads and tails refinement of
+                             PFSP_MINHT; pfsp_solve / pfsp_solve_resumable with the plain solver
+                             only (no heuristic threads, no ordering network); 0 (default): off */
+    int reserved[4];
 } pfsp_options;
 
 void pfsp_default_options(pfsp_options *opt);

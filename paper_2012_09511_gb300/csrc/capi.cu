@@ -130,10 +130,20 @@ static int ensure_scratch(pfsp_instance *inst, size_t bytes) {
     return PFSP_OK;
 }
 
+// The bounding kernel of the kind: with PFSP_MINHT the refined one.
+static cudaError_t launch_bounds(const pfsp_instance *inst, int kind, long long num_nodes, const uint8_t *perm,
+                                 const uint8_t *d1, const uint8_t *d2, int32_t *lb1, int32_t *lb2,
+                                 cudaStream_t stream) {
+    if (kind & PFSP_MINHT)
+        return launch_bound_batch_minht(inst, kind & ~PFSP_MINHT, num_nodes, perm, d1, d2, lb1, lb2, stream);
+    return launch_bound_batch(inst, kind, num_nodes, perm, d1, d2, lb1, lb2, stream);
+}
+
 static int check_bound_args(const pfsp_instance *inst, int kind, int64_t num_nodes, const void *perm,
                             const void *d1, const void *d2, const void *lb1, const void *lb2) {
     if (!inst) return set_error(PFSP_ERR_INVALID, "instance is NULL");
-    if (kind < 1 || kind > 3) return set_error(PFSP_ERR_INVALID, "kind must be a non-empty mask of LB1|LB2");
+    if ((kind & (PFSP_LB1 | PFSP_LB2)) == 0 || (kind & ~(PFSP_LB1 | PFSP_LB2 | PFSP_MINHT)) != 0)
+        return set_error(PFSP_ERR_INVALID, "kind must be a non-empty mask of LB1|LB2, optionally with PFSP_MINHT");
     if (num_nodes < 0) return set_error(PFSP_ERR_INVALID, "num_nodes < 0");
     if (num_nodes == 0) return PFSP_OK;
     if (!perm || !d1 || !d2) return set_error(PFSP_ERR_INVALID, "NULL node input");
@@ -280,7 +290,7 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
     g_err[0] = 0;
     int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out);
     if (rc != PFSP_OK || num_nodes == 0) return rc;
-    cudaError_t e = launch_bound_batch(inst, kind, num_nodes, perm, d1, d2, (kind & PFSP_LB1) ? lb1_out : nullptr,
+    cudaError_t e = launch_bounds(inst, kind, num_nodes, perm, d1, d2, (kind & PFSP_LB1) ? lb1_out : nullptr,
                                        (kind & PFSP_LB2) ? lb2_out : nullptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "bound kernel launch");
     return PFSP_OK;
@@ -346,7 +356,7 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
         if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
         if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c], st[q]);
-        if (e == cudaSuccess) e = launch_bound_batch(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
+        if (e == cudaSuccess) e = launch_bounds(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
         if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c + 1], st[q]);
         if (e == cudaSuccess && o1)
             e = cudaMemcpyAsync(lb1_out + (size_t)off * 2 * n, o1, ob, cudaMemcpyDeviceToHost, st[q]);

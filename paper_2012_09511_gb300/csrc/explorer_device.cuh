@@ -8,6 +8,7 @@
 #include <climits>
 
 #include "bound_device.cuh"
+#include "minht_device.cuh"
 #include "pfsp_internal.h"
 #include "solve_internal.h"
 
@@ -58,6 +59,7 @@ template <int NW, int MT, int KIND>
 struct Explorer {
     static constexpr bool LEARNED = KIND == kKindLearned;
     static constexpr bool COOP = KIND == kKindCoop;
+    static constexpr bool MINHT = KIND == kKindMinht;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -406,6 +408,9 @@ struct Explorer {
         ChildBounds<NW> cb;
         const int kind = a.bound == PFSP_LB2 ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
         decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
+        if constexpr (MINHT) {
+            if (d1 == 0 || d2 == 0) refine_minht<NW, MT>(T, W, n, m, d1, d2, cb);
+        }
         tick(counted ? kPhLB1 : kPhInit);
         if ((kind & PFSP_LB2) && m >= 2) {
             const int *order = nullptr;

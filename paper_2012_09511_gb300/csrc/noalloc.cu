@@ -109,6 +109,7 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     a.cap = ub0;
     if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs the plain solver only");
     if (opt->heuristic_threads) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs no heuristic threads");
+    if (opt->lb1_minht) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_noalloc runs the plain bounds only");
     a.warp_words = (warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2) + 7) & ~7;
     a.warp_base = (a.tab_words + 7) & ~7;
     const int per_warp = a.warp_words + kExplorerWords;

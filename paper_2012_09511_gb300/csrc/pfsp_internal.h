@@ -65,6 +65,10 @@ namespace pfsp {
 cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long num_nodes,
                                const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
                                int32_t *lb1, int32_t *lb2, cudaStream_t stream);
+// With the heads and tails refinement of LB1 (bound_minht.cu).
+cudaError_t launch_bound_batch_minht(const pfsp_instance *inst, int kind, long long num_nodes,
+                                     const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
+                                     int32_t *lb1, int32_t *lb2, cudaStream_t stream);
 
 // Error reporting shared by the C-ABI translation units.
 int set_error(int code, const char *fmt, ...);

@@ -309,6 +309,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->learned) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs the plain solver only");
     if (opt->heuristic_threads) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs no heuristic threads");
+    if (opt->lb1_minht) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_solve_batch runs the plain bounds only");
     int dev = 0;
     cudaGetDevice(&dev);
     for (int i = 0; i < count; ++i) {

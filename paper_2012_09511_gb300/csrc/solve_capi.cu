@@ -131,6 +131,9 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         return set_error(PFSP_ERR_INVALID, "heuristic_threads must be in 0..256");
     if (opt->heuristic_threads && (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)))
         return set_error(PFSP_ERR_UNSUPPORTED, "heuristic threads run beside the plain solver only");
+    if (opt->lb1_minht != 0 && opt->lb1_minht != 1) return set_error(PFSP_ERR_INVALID, "lb1_minht must be 0 or 1");
+    if (opt->lb1_minht && (opt->heuristic_threads || (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER))))
+        return set_error(PFSP_ERR_UNSUPPORTED, "lb1_minht runs in the plain solver only");
     const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
     int net_m = 0, net_D0 = 0, net_O = 0;
     if (use_net) {
@@ -153,7 +156,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         memcpy(&rh, rio->resume, sizeof(rh));
         if (memcmp(rh.magic, kCkptMagic, 8) != 0) return set_error(PFSP_ERR_INVALID, "not a pfsp checkpoint");
         if (rh.n != n || rh.m != m) return set_error(PFSP_ERR_INVALID, "checkpoint of a %d x %d instance", rh.n, rh.m);
-        if (rh.bound != opt->bound || rh.branching != opt->branching)
+        // the bound field carries PFSP_MINHT when the refinement was on
+        if (rh.bound != (opt->bound | (opt->lb1_minht ? PFSP_MINHT : 0)) || rh.branching != opt->branching)
             return set_error(PFSP_ERR_INVALID, "checkpoint taken with another bound or branching rule");
         if (rh.count < 0 || rio->resume_bytes != (int64_t)sizeof(CkptHeader) + (int64_t)rh.count * kCkptRecord)
             return set_error(PFSP_ERR_INVALID, "checkpoint size does not match its record count");
@@ -189,6 +193,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.off_ptab = L.off_ptab;
     a.bound = opt->bound;
     a.branching = opt->branching;
+    a.minht = opt->lb1_minht;
     a.cap = resuming ? rh.cap : ub0;
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
     // the network's inference image: every output column when it orders the
@@ -485,7 +490,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         memcpy(h.magic, kCkptMagic, 8);
         h.n = n;
         h.m = m;
-        h.bound = opt->bound;
+        h.bound = opt->bound | (opt->lb1_minht ? PFSP_MINHT : 0);
         h.branching = opt->branching;
         h.cap = a.cap;
         h.ub = best;

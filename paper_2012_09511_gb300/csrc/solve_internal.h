@@ -25,6 +25,7 @@ constexpr unsigned long long kWatchdogNs = 10ull * 1000 * 1000 * 1000;
 constexpr int kKindPlain = 0;    // the paper's solver
 constexpr int kKindLearned = 1;  // with the ordering network
 constexpr int kKindCoop = 2;     // with the host heuristic threads' exchange
+constexpr int kKindMinht = 3;    // with the heads and tails refinement of LB1
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
@@ -122,6 +123,7 @@ struct SolveArgs {
     int learn_depth;      // rows of level < learn_depth are ordered by the network
     CoopShared *coop;     // host heuristic threads' exchange (NULL: none)
     CoopSlot *coop_slots; // [K] the explorers' snapshot slots
+    int minht;            // 1: LB1 with the heads and tails refinement (its own kernel)
     int rows_smem;        // 1: each explorer's rows live in shared memory after its explorer state
 };
 
@@ -140,5 +142,7 @@ int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_coop(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_coop(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+int solve_occupancy_minht(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve_minht(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 
 }  // namespace pfsp

@@ -55,6 +55,7 @@ int mlp_scratch_place(int n, int m, int bound, int D0, int *off) {
 int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
     if (a.net_image) return solve_occupancy_learned(a, warps, smem);
     if (a.coop) return solve_occupancy_coop(a, warps, smem);
+    if (a.minht) return solve_occupancy_minht(a, warps, smem);
     if (a.n <= 32) { PFSP_DISPATCH(1, kKindPlain, occupancy_t, warps, smem) }
     PFSP_DISPATCH(2, kKindPlain, occupancy_t, warps, smem)
 }
@@ -62,6 +63,7 @@ int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
 cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st) {
     if (a.net_image) return launch_solve_learned(a, blocks, warps, smem, st);
     if (a.coop) return launch_solve_coop(a, blocks, warps, smem, st);
+    if (a.minht) return launch_solve_minht(a, blocks, warps, smem, st);
     if (a.n <= 32) { PFSP_DISPATCH(1, kKindPlain, launch_solve_t, a, blocks, warps, smem, st) }
     PFSP_DISPATCH(2, kKindPlain, launch_solve_t, a, blocks, warps, smem, st)
 }

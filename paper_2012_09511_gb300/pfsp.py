@@ -31,6 +31,7 @@ PFSP_LIMIT_NODES = 2
 PFSP_LIMIT_TIME = 3
 PFSP_LB1 = 1
 PFSP_LB2 = 2
+PFSP_MINHT = 4
 PFSP_MINMIN = 0
 PFSP_MINMIN_CAPPED = 1
 PFSP_MINBRANCH = 2
@@ -72,7 +73,8 @@ class pfsp_options(ctypes.Structure):
                 ("bound", ctypes.c_int), ("branching", ctypes.c_int), ("warps_per_sm", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
                 ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("phase_timers", ctypes.c_int),
-                ("heuristic_threads", ctypes.c_int), ("heuristic_seed", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("heuristic_threads", ctypes.c_int), ("heuristic_seed", ctypes.c_int), ("lb1_minht", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 if not os.path.exists(LIB_PATH):

@@ -190,3 +190,33 @@ def test_lb2_over_pair_subsets_bit_exact(pf, n, m, subset):
     assert (full == ofull).all() and (g2 <= full).all()
     with pytest.raises(pf.PfspError):
         pf.pfsp_set_lb2_pairs(inst, [0, 0])
+
+
+@pytest.mark.parametrize("n,m,count", [
+    (20, 10, 3000), (12, 5, 3000), (20, 20, 1500), (36, 4, 800), (64, 3, 300), (9, 1, 500), (5, 7, 400),
+])
+def test_heads_tails_refinement_bit_exact(pf, n, m, count):
+    # PFSP_MINHT: LB1 with the least heads / tails of the unscheduled jobs when
+    # sigma1 / sigma2 is empty (LB2 = max of that LB1 and the pairs).  Small
+    # depths make one side empty on about a third of the nodes; the degenerate
+    # rows (root, one side only, leaf children, no children) are appended.
+    p = inputs.make_instance(n, m, 4000 + n * 64 + m)
+    perm, d1, d2 = inputs.random_nodes(n, count, seed=n * m, dmax=min(3, n))
+    extra_d1 = np.array([0, n, 0, n - 1, 0, 1], dtype=np.uint8) if n >= 2 else np.zeros(6, np.uint8)
+    extra_d2 = np.array([0, 0, n, 0, n - 1, 0], dtype=np.uint8) if n >= 2 else np.zeros(6, np.uint8)
+    perm = np.concatenate([perm, perm[:6]])
+    d1 = np.concatenate([d1, extra_d1])
+    d2 = np.concatenate([d2, extra_d2])
+    inst = pf.pfsp_load_instance(p)
+    for kind in (pf.PFSP_LB1 | pf.PFSP_MINHT, pf.PFSP_LB1 | pf.PFSP_LB2 | pf.PFSP_MINHT):
+        g1, g2 = pf.pfsp_bound_batch(inst, kind, perm, d1, d2)
+        o1, o2 = orc.children_bounds_batch(p, perm, d1, d2, kind=kind, threads=8)
+        bad = np.argwhere(g1 != o1)
+        assert len(bad) == 0, ("LB1 minht mismatch", kind, bad[:5], g1[tuple(bad[0])], o1[tuple(bad[0])])
+        if kind & pf.PFSP_LB2:
+            bad = np.argwhere(g2 != o2)
+            assert len(bad) == 0, ("LB2 minht mismatch", bad[:5], g2[tuple(bad[0])], o2[tuple(bad[0])])
+    plain, _ = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
+    assert (g1 >= plain).all() and (g1 > plain).any() == (m > 1)
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_bound_batch(inst, pf.PFSP_MINHT, perm, d1, d2)

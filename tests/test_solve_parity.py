@@ -98,6 +98,33 @@ def test_other_branching_rules_proof_counts(pf, rule, n, m, bound, seed):
     _check_perm(p, g)
 
 
+@pytest.mark.parametrize("n,m,bound,seed", [(12, 6, 1, 20), (13, 6, 1, 22), (14, 8, 1, 21), (12, 10, 1, 22),
+                                             (12, 8, 2, 42), (36, 3, 1, 4)])
+def test_heads_tails_refinement_proof_counts(pf, n, m, bound, seed):
+    # lb1_minht: the refined LB1 (and LB2 over it); proof trees and counters
+    # equal the oracle's with the same refinement, finding mode its optimum
+    p = inputs.make_instance(n, m, seed)
+    if n > 20:
+        ub = orc.lb1(p, [], [], minht=True) + 4  # a tight incumbent keeps the oracle's tree small
+        want = orc.bb_solve(p, bound=bound, init_ub=ub, minht=True, node_limit=3_000_000)
+        assert want["outcome"] != orc.LIMIT_NODES
+        r = pf.pfsp_solve(pf.pfsp_load_instance(p), bound=bound, init_ub=ub, lb1_minht=1)
+        assert r["outcome"] == want["outcome"] and r["cmax"] == want["cmax"]
+        if want["outcome"] == orc.PROVEN_NO_BETTER:
+            assert (r["decomposed"], r["bounded_children"]) == (want["decomposed"], want["bounded"])
+        return
+    opt = orc.bb_solve(p, bound=bound)["cmax"]
+    proof = orc.bb_solve(p, bound=bound, init_ub=opt, minht=True)
+    inst = pf.pfsp_load_instance(p)
+    r = pf.pfsp_solve(inst, bound=bound, init_ub=opt, lb1_minht=1)
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+    assert (r["decomposed"], r["bounded_children"]) == (proof["decomposed"], proof["bounded"])
+    assert r["leaves"] == proof["leaves"] and r["pruned"] == proof["pruned"]
+    g = pf.pfsp_solve(inst, bound=bound, lb1_minht=1)
+    assert g["outcome"] == pf.PFSP_OPTIMAL and g["cmax"] == opt
+    _check_perm(p, g)
+
+
 def test_fixed_tree_below_optimum(pf):
     # the paper's fixed-tree runs start from an incumbent at or below the optimum
     p = inputs.make_instance(13, 6, 9)
@@ -202,7 +229,7 @@ def test_invalid_options(pf):
     p = inputs.make_instance(8, 4, 1)
     inst = pf.pfsp_load_instance(p)
     for bad in (dict(bound=3), dict(branching=5), dict(branching=-1), dict(node_limit=-1),
-                dict(branching=pf.PFSP_MINSUM, learned=pf.PFSP_EARLY_EXIT)):
+                dict(branching=pf.PFSP_MINSUM, learned=pf.PFSP_EARLY_EXIT), dict(lb1_minht=2)):
         with pytest.raises(pf.PfspError) as e:
             pf.pfsp_solve(inst, **bad)
         assert e.value.code == pf.PFSP_ERR_INVALID
