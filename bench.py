@@ -210,7 +210,30 @@ def solve_leg(pfsp, seeds=range(1, 11)):
             "counts_and_optima_match_oracle": bool(exact), "per_seed": per,
             "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds),
             "branching_rules": rules_leg(pfsp, gold, seeds),
-            "heuristic_threads": heuristic_leg(pfsp, gold, seeds)}
+            "heuristic_threads": heuristic_leg(pfsp, gold, seeds),
+            "lb1_minht": minht_leg(pfsp)}
+
+
+def minht_leg(pfsp):
+    """LB1 proofs at the optimum with and without the heads and tails refinement
+    (pfsp_options.lb1_minht), node counts checked against tests/golden/solve_lb1_minht.json."""
+    from paper_2012_09511_gb300 import inputs
+    with open(os.path.join(ROOT, "tests", "golden", "solve_lb1_minht.json")) as f:
+        cases = json.load(f)["results"]
+    out = {"workload": "LB1 proofs of %d instances (n, m, seed) = %s" % (
+        len(cases), ", ".join("(%d,%d,%d)" % (c["n"], c["m"], c["seed"]) for c in cases))}
+    for name, flag in (("plain", 0), ("minht", 1)):
+        t = 0.0
+        nodes, exact = 0, True
+        for c in cases:
+            inst = pfsp.pfsp_load_instance(inputs.make_instance(c["n"], c["m"], c["seed"]))
+            pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB1, init_ub=c["optimum"], lb1_minht=flag)  # warm
+            r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB1, init_ub=c["optimum"], lb1_minht=flag)
+            exact &= r["decomposed"] == c[name]["decomposed"] and r["outcome"] == pfsp.PFSP_PROVEN_NO_BETTER
+            t += r["kernel_seconds"]
+            nodes += r["decomposed"]
+        out[name] = {"time_to_proof_s": t, "decomposed_nodes": nodes, "counts_match_oracle": bool(exact)}
+    return out
 
 
 def heuristic_leg(pfsp, gold, seeds, threads=4):
