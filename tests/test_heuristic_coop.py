@@ -111,3 +111,14 @@ def test_heuristic_options_validation(pf):
     with pytest.raises(pf.PfspError) as e:
         pf.pfsp_solve_noalloc(p, heuristic_threads=1)
     assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
+    # the heads and tails refinement runs in its own kernel, beside neither
+    for bad in (dict(lb1_minht=1, heuristic_threads=1),):
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_solve(inst, **bad)
+        assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
+    with pytest.raises(pf.PfspError) as e:
+        pf.pfsp_solve_batch([inst], lb1_minht=1)
+    assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
+    with pytest.raises(pf.PfspError) as e:
+        pf.pfsp_solve_noalloc(p, lb1_minht=1)
+    assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
