@@ -41,6 +41,7 @@ WORKLOAD = "pfsp-bound-20x20-4M"
 METRIC = "bounded children/s (LB1 + full-pair LB2)"
 UNIT = "children/s"
 L2_FLUSH_BYTES = 256 << 20
+REDUCE_UB = 1500  # exclusive incumbent of the reduce mode's survivor masks (near the batch's median LB2)
 # INT32 ALU lanes per SM per clock on sm_103a (add, min/max, logic: measured
 # with the microbenchmark whose result is in profiles/int32_alu_peak.md)
 INT32_LANES_PER_SM_CLK = 128
@@ -82,6 +83,18 @@ def algorithmic_ops(n, m, d1, d2):
     lb1 = 2 * m * d + 2 * u * m * 6
     lb2 = P * u * 13
     return int((lb1 + lb2).sum())
+
+
+def survey_equivalent_ops(n, m, d1, d2):
+    """The per-parent work of the bounds evaluated child by child, as the
+    paper's recurrence states them (the scope table's figure): LB2 4 ops per
+    (child, pair, unscheduled job of the child), 2P u (u - 1) such steps; LB1 4m
+    per child and 2m (d1 + d2) per parent.  This design evaluates the same
+    values with the O(P u) composition counted by algorithmic_ops."""
+    d = d1.astype(np.int64) + d2.astype(np.int64)
+    u = n - d
+    P = m * (m - 1) // 2
+    return int((4 * 2 * P * u * np.maximum(u - 1, 0) + 4 * m * 2 * u + 2 * m * d).sum())
 
 
 def kernel_source_hash():
@@ -463,6 +476,46 @@ def run_native(args):
     e2e_s = max(time.perf_counter() - t0, 1e-9)
     e2e_value, _, _ = shard.whole_job_rate(e2e_s, children * args.e2e_steps, device=dev)
 
+    # reduce mode: the same nodes and bounds (LB2, the solver's), one
+    # 48-byte summary per parent instead of the bound arrays
+    ub_reduce = REDUCE_UB
+    so = torch.empty(N * pfsp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+
+    def rstep():
+        pfsp.pfsp_bound_reduce_dev(inst, pfsp.PFSP_LB2, N, tp.data_ptr(), t1.data_ptr(), t2.data_ptr(),
+                                   ub_reduce, so.data_ptr(), sh)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        rstep()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    revs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rstep()
+        e1.record(stream)
+        revs.append((e0, e1))
+    torch.cuda.synchronize()
+    r_ms = sum(a.elapsed_time(b) for a, b in revs)
+    r_value, _, _ = shard.whole_job_rate(r_ms * 1e-3, children * args.steps, device=dev)
+    hs = np.empty(N, dtype=pfsp.SUMMARY_DTYPE)
+    hs_pin = torch.from_numpy(hs.view(np.uint8)).pin_memory()
+    hs = hs_pin.numpy().view(pfsp.SUMMARY_DTYPE)
+    if args.e2e_steps > 0:
+        pfsp.pfsp_bound_reduce(inst, pfsp.PFSP_LB2, *args_np, ub_reduce, out=hs)  # warm
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pfsp.pfsp_bound_reduce(inst, pfsp.PFSP_LB2, *args_np, ub_reduce, out=hs)
+    r_e2e_s = max(time.perf_counter() - t0, 1e-9)
+    r_e2e_value, _, _ = shard.whole_job_rate(r_e2e_s, children * args.e2e_steps, device=dev)
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -474,6 +527,7 @@ def run_native(args):
     achieved = ops / (launch_ms * 1e-3)
     ncu = ncu_summary()
     traffic = ncu.get("dram_bytes_per_launch_full") if ncu else None
+    survey_ops = survey_equivalent_ops(n, m, d1, d2)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": slowest_s * 1e3 / args.steps, "higher_is_better": True,
@@ -487,10 +541,17 @@ def run_native(args):
                      "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
                          nsm, INT32_LANES_PER_SM_CLK, sm_max),
                      "ops_per_launch": ops, "kernel_ms": launch_ms,
+                     "child_by_child_ops_per_launch": survey_ops,
+                     "child_by_child_frac": survey_ops / (launch_ms * 1e-3) / peak_ops,
                      "ncu_utilisation": {k: ncu[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct",
                                                              "lsu_pipe_pct") if k in ncu} if ncu else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
                 "d2h_bytes_per_step": int(2 * N * 2 * n * 4)},
+        "reduce": {"value": r_value, "unit": UNIT, "ms_per_step": r_ms / args.steps,
+                   "mode": "LB2 summarised per parent and direction (least bound, count, sum, survivors "
+                           "below %d), 48 bytes per parent" % REDUCE_UB,
+                   "e2e": {"value": r_e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
+                           "d2h_bytes_per_step": int(N * 48)}},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }

@@ -120,6 +120,37 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
                          const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out,
                          void *stream);
 
+/*
+ * Per-parent summary of the bounds of its children (Sections 2.3-2.4): what
+ * the branching rule and the pruning consume, without the 2n bounds each.
+ * Index 0 is the forward children set, 1 the backward one.
+ */
+typedef struct {
+    int32_t min[2];    /* least bound of the set (INT32_MAX when the node has no child; -1 for
+                          invalid depths on the device entry point) */
+    int32_t count[2];  /* children of the set at that least bound (-1 for invalid depths) */
+    int64_t sum[2];    /* sum of the set's bounds */
+    uint64_t keep[2];  /* bit j: the child of job j has a bound below ub (it survives pruning) */
+} pfsp_node_summary;
+
+/*
+ * Bounding with the children reduced per parent (the "reduce" mode; the
+ * arrays of pfsp_bound_batch are the "materialize" mode): the same nodes,
+ * layout and validation as pfsp_bound_batch; kind is PFSP_LB1 or PFSP_LB2
+ * (one bound: the one summarised).  ub is the exclusive incumbent that keep
+ * tests against.  out (num_nodes entries) receives one summary per node.
+ * MinMin's count of the overall least bound mu is count[d] where min[d] == mu
+ * and 0 elsewhere.  Returns the codes of pfsp_bound_batch.
+ */
+int pfsp_bound_reduce(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                      const uint8_t *d1, const uint8_t *d2, int32_t ub, pfsp_node_summary *out);
+
+/* Same on device buffers, enqueued on `stream` (depths clamped as in
+ * pfsp_bound_batch_dev; invalid ones get min = count = -1). */
+int pfsp_bound_reduce_dev(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                          const uint8_t *d1, const uint8_t *d2, int32_t ub, pfsp_node_summary *out,
+                          void *stream);
+
 /* Counters reported by pfsp_stats, pfsp_solve_batch and pfsp_solve_noalloc. */
 typedef struct {
     uint64_t decomposed;       /* parents whose children were bounded (root counts 1) */

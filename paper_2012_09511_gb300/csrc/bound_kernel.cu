@@ -5,6 +5,9 @@
 // number of CTAs per SM) and walks the batch with a warp-stride loop.  Each
 // CTA stages the instance tables (processing times by machine, machine
 // totals, per-pair Johnson tables) into shared memory once with a bulk copy.
+// The epilogue either writes every child's bounds (materialize) or reduces
+// them per parent and direction to what branching and pruning consume
+// (reduce: least bound, its count, the sum, the survivors).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,12 +27,66 @@ struct BoundArgs {
     int off_pm, off_tot, off_kl, off_rank, off_ptab;
     int warp_words;
     int kind;
+    pfsp_node_summary *summary;  // reduce mode: one per node
+    int ub;                      // reduce mode: exclusive incumbent of the survivor masks
 };
+
+// Reduce-mode epilogue: lane c holds the bounds of the children of compact
+// index c (and c + 32); warp reductions give each direction's least bound,
+// its count, the sum and the job mask of the children below ub.
+template <int NW>
+__device__ __forceinline__ void write_summary(const ChildBounds<NW> &cb, const WarpScratch &W, bool use2, int ub,
+                                              pfsp_node_summary *out) {
+    const int lane = threadIdx.x & 31;
+    int mn[2] = {INT_MAX, INT_MAX}, sm[2] = {0, 0};
+    unsigned klo[2] = {0u, 0u}, khi[2] = {0u, 0u};
+    int v[2][NW];
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        const int c = lane + 32 * h;
+        const bool on = c < cb.u;
+        const int j = on ? W.ul[c] : 0;
+        v[0][h] = use2 ? cb.lb2f[h] : cb.lb1f[h];
+        v[1][h] = use2 ? cb.lb2b[h] : cb.lb1b[h];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            if (on) {
+                mn[d] = min(mn[d], v[d][h]);
+                sm[d] += v[d][h];  // at most 64 bounds below 2^21 each: no overflow
+            }
+            if (on && v[d][h] < ub) {
+                if (j < 32) klo[d] |= 1u << j;
+                else khi[d] |= 1u << (j - 32);
+            }
+        }
+    }
+    int cnt[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        mn[d] = __reduce_min_sync(PFSP_FULL, mn[d]);
+        sm[d] = __reduce_add_sync(PFSP_FULL, sm[d]);
+        klo[d] = __reduce_or_sync(PFSP_FULL, klo[d]);
+        khi[d] = __reduce_or_sync(PFSP_FULL, khi[d]);
+        cnt[d] = 0;
+#pragma unroll
+        for (int h = 0; h < NW; ++h)
+            cnt[d] += __popc(__ballot_sync(PFSP_FULL, lane + 32 * h < cb.u && v[d][h] == mn[d]));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            out->min[d] = mn[d];
+            out->count[d] = cnt[d];
+            out->sum[d] = sm[d];
+            out->keep[d] = ((unsigned long long)khi[d] << 32) | klo[d];
+        }
+    }
+}
 
 // Each CTA owns a contiguous range of nodes; its warps claim them one at a
 // time from a shared counter, so that warps on less busy schedulers of the
 // SM take more nodes.
-template <int NW, int MT, int WALK>
+template <int NW, int MT, int WALK, bool REDUCE>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(BoundArgs a) {
     extern __shared__ __align__(16) int smem[];
     __shared__ uint64_t bar;
@@ -83,6 +140,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
         int32_t *o1 = a.lb1 ? a.lb1 + node * 2 * n : nullptr;
         int32_t *o2 = a.lb2 ? a.lb2 + node * 2 * n : nullptr;
         if (d1 + d2 > n) {
+            if constexpr (REDUCE) {
+                if (lane == 0) {
+                    pfsp_node_summary *s = a.summary + node;
+                    for (int d = 0; d < 2; ++d) {
+                        s->min[d] = -1;
+                        s->count[d] = -1;
+                        s->sum[d] = 0;
+                        s->keep[d] = 0;
+                    }
+                }
+                continue;
+            }
             for (int i = lane; i < 2 * n; i += 32) {
                 if (o1) o1[i] = -1;
                 if (o2) o2[i] = -1;
@@ -91,6 +160,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
         }
         ChildBounds<NW> cb;
         decompose_node<NW, MT, WALK>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
+        if constexpr (REDUCE) {
+            write_summary<NW>(cb, W, (a.kind & PFSP_LB2) != 0, a.ub, a.summary + node);
+            __syncwarp();
+            continue;
+        }
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
             int j = lane + 32 * h;
@@ -149,7 +223,7 @@ static cudaError_t launch_t(const BoundArgs &a, int want_warps, cudaStream_t str
     const int warps = fit_warps(a, want_warps);
     if (warps < 1) return cudaErrorInvalidConfiguration;
     size_t smem = (size_t)(a.tab_words + warps * a.warp_words) * 4;
-    auto kern = bound_batch_kernel<NW, MT, WALK>;
+    auto kern = a.summary ? bound_batch_kernel<NW, MT, WALK, true> : bound_batch_kernel<NW, MT, WALK, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -165,10 +239,12 @@ static cudaError_t launch_t(const BoundArgs &a, int want_warps, cudaStream_t str
 
 cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long num_nodes, const uint8_t *perm,
                                const uint8_t *d1, const uint8_t *d2, int32_t *lb1, int32_t *lb2,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, pfsp_node_summary *summary, int ub) {
     if (num_nodes <= 0) return cudaSuccess;
     const TableLayout &L = inst->lay;
     BoundArgs a;
+    a.summary = summary;
+    a.ub = ub;
     a.perm = perm;
     a.d1 = d1;
     a.d2 = d2;

@@ -296,12 +296,11 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
     return PFSP_OK;
 }
 
-int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, const uint8_t *perm,
-                     const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out) {
-    g_err[0] = 0;
-    pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
-    int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out);
-    if (rc != PFSP_OK) return rc;
+// Host-pointer bounding, shared by both modes: the bound arrays (summary
+// NULL) or one summary per node (reduce mode, survivors below ub).
+static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm, const uint8_t *d1,
+                      const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out, pfsp_node_summary *summary, int ub) {
+    int rc = PFSP_OK;
     auto t0 = std::chrono::steady_clock::now();
     const int n = inst->n;
     // one pass over the depths: validation and the children count (a plain
@@ -331,10 +330,11 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
     const int64_t nchunks = (num_nodes + chunk - 1) / chunk;
     const int nst = nchunks > 1 ? 2 : 1;
     const size_t in_bytes = (size_t)chunk * (n + 2);
-    const size_t out_bytes = (size_t)chunk * 2 * n * sizeof(int32_t);
+    const size_t out_bytes = summary ? (size_t)chunk * sizeof(pfsp_node_summary) : (size_t)chunk * 2 * n * sizeof(int32_t);
+    const bool want1 = !summary && (kind & PFSP_LB1), want2 = !summary && (kind & PFSP_LB2);
     const size_t off_out1 = (in_bytes + 255) & ~(size_t)255;
-    const size_t off_out2 = off_out1 + (((kind & PFSP_LB1) ? out_bytes : 0) + 255) / 256 * 256;
-    const size_t per_stream = (off_out2 + ((kind & PFSP_LB2) ? out_bytes : 0) + 255) / 256 * 256;
+    const size_t off_out2 = off_out1 + (((want1 || summary) ? out_bytes : 0) + 255) / 256 * 256;
+    const size_t per_stream = (off_out2 + (want2 ? out_bytes : 0) + 255) / 256 * 256;
     rc = ensure_scratch(inst, per_stream * nst);
     if (rc != PFSP_OK) return rc;
     cudaStream_t st[2] = {nullptr, nullptr};
@@ -349,15 +349,21 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
         uint8_t *dperm = (uint8_t *)base;
         uint8_t *dd1 = dperm + (size_t)cn * n;
         uint8_t *dd2 = dd1 + cn;
-        int32_t *o1 = (kind & PFSP_LB1) ? (int32_t *)(base + off_out1) : nullptr;
-        int32_t *o2 = (kind & PFSP_LB2) ? (int32_t *)(base + off_out2) : nullptr;
+        int32_t *o1 = want1 ? (int32_t *)(base + off_out1) : nullptr;
+        int32_t *o2 = want2 ? (int32_t *)(base + off_out2) : nullptr;
+        pfsp_node_summary *os = summary ? (pfsp_node_summary *)(base + off_out1) : nullptr;
         const size_t ob = (size_t)cn * 2 * n * sizeof(int32_t);
         e = cudaMemcpyAsync(dperm, perm + (size_t)off * n, (size_t)cn * n, cudaMemcpyHostToDevice, st[q]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
         if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c], st[q]);
-        if (e == cudaSuccess) e = launch_bounds(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
+        if (e == cudaSuccess)
+            e = summary ? launch_bound_batch(inst, kind, cn, dperm, dd1, dd2, nullptr, nullptr, st[q], os, ub)
+                        : launch_bounds(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
         if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c + 1], st[q]);
+        if (e == cudaSuccess && os)
+            e = cudaMemcpyAsync(summary + off, os, (size_t)cn * sizeof(pfsp_node_summary), cudaMemcpyDeviceToHost,
+                                st[q]);
         if (e == cudaSuccess && o1)
             e = cudaMemcpyAsync(lb1_out + (size_t)off * 2 * n, o1, ob, cudaMemcpyDeviceToHost, st[q]);
         if (e == cudaSuccess && o2)
@@ -378,13 +384,51 @@ int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, c
         if (ev) cudaEventDestroy(ev);
     for (int q = 0; q < nst; ++q)
         if (st[q]) cudaStreamDestroy(st[q]);
-    if (e != cudaSuccess) return cuda_fail(e, "pfsp_bound_batch");
+    if (e != cudaSuccess) return cuda_fail(e, summary ? "pfsp_bound_reduce" : "pfsp_bound_batch");
     memset(&inst->stats, 0, sizeof(inst->stats));
     const uint64_t children = 2 * ((uint64_t)num_nodes * (uint64_t)n - depth_sum);
     inst->stats.decomposed = (uint64_t)num_nodes;
     inst->stats.bounded_children = children;
     inst->stats.kernel_seconds = ms * 1e-3;
     inst->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PFSP_OK;
+}
+
+int pfsp_bound_batch(const pfsp_instance *inst_c, int kind, int64_t num_nodes, const uint8_t *perm,
+                     const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out) {
+    g_err[0] = 0;
+    pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
+    int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out);
+    if (rc != PFSP_OK) return rc;
+    return bound_host(inst, kind, num_nodes, perm, d1, d2, lb1_out, lb2_out, nullptr, 0);
+}
+
+static int check_reduce_args(const pfsp_instance *inst, int kind, int64_t num_nodes, const void *perm,
+                             const void *d1, const void *d2, const void *out) {
+    if (kind != PFSP_LB1 && kind != PFSP_LB2) return set_error(PFSP_ERR_INVALID, "kind must be PFSP_LB1 or PFSP_LB2");
+    int rc = check_bound_args(inst, kind, num_nodes, perm, d1, d2, out, out);
+    if (rc != PFSP_OK) return rc;
+    if (num_nodes > 0 && !out) return set_error(PFSP_ERR_INVALID, "out is NULL");
+    return PFSP_OK;
+}
+
+int pfsp_bound_reduce(const pfsp_instance *inst_c, int kind, int64_t num_nodes, const uint8_t *perm,
+                      const uint8_t *d1, const uint8_t *d2, int32_t ub, pfsp_node_summary *out) {
+    g_err[0] = 0;
+    pfsp_instance *inst = const_cast<pfsp_instance *>(inst_c);
+    int rc = check_reduce_args(inst, kind, num_nodes, perm, d1, d2, out);
+    if (rc != PFSP_OK) return rc;
+    return bound_host(inst, kind, num_nodes, perm, d1, d2, nullptr, nullptr, out, ub);
+}
+
+int pfsp_bound_reduce_dev(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
+                          const uint8_t *d1, const uint8_t *d2, int32_t ub, pfsp_node_summary *out, void *stream) {
+    g_err[0] = 0;
+    int rc = check_reduce_args(inst, kind, num_nodes, perm, d1, d2, out);
+    if (rc != PFSP_OK || num_nodes == 0) return rc;
+    cudaError_t e = launch_bound_batch(inst, kind, num_nodes, perm, d1, d2, nullptr, nullptr, (cudaStream_t)stream,
+                                       out, ub);
+    if (e != cudaSuccess) return cuda_fail(e, "bound kernel launch");
     return PFSP_OK;
 }
 

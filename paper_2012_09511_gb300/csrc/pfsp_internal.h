@@ -62,9 +62,12 @@ struct pfsp_instance {
 namespace pfsp {
 
 // Kernel launchers (bound_kernel.cu).  Return cudaError_t of the launch.
+// With summary != NULL the reduce mode: one pfsp_node_summary per node
+// (survivors below ub) instead of the bound arrays.
 cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long num_nodes,
                                const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,
-                               int32_t *lb1, int32_t *lb2, cudaStream_t stream);
+                               int32_t *lb1, int32_t *lb2, cudaStream_t stream,
+                               pfsp_node_summary *summary = nullptr, int ub = 0);
 // With the heads and tails refinement of LB1 (bound_minht.cu).
 cudaError_t launch_bound_batch_minht(const pfsp_instance *inst, int kind, long long num_nodes,
                                      const uint8_t *perm, const uint8_t *d1, const uint8_t *d2,

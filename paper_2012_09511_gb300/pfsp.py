@@ -93,6 +93,10 @@ _lib.pfsp_bound_batch.restype = ctypes.c_int
 _lib.pfsp_bound_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
 _lib.pfsp_bound_batch_dev.restype = ctypes.c_int
 _lib.pfsp_bound_batch_dev.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pfsp_bound_reduce.restype = ctypes.c_int
+_lib.pfsp_bound_reduce.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32, _vp]
+_lib.pfsp_bound_reduce_dev.restype = ctypes.c_int
+_lib.pfsp_bound_reduce_dev.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp]
 _lib.pfsp_default_options.restype = None
 _lib.pfsp_default_options.argtypes = [ctypes.POINTER(pfsp_options)]
 _lib.pfsp_solve.restype = ctypes.c_int
@@ -231,6 +235,30 @@ def pfsp_bound_batch_dev(inst: Instance, kind, num_nodes, perm, d1, d2, lb1_out,
     """Device addresses as ints (0 = NULL); enqueues on `stream` and returns."""
     _check(_lib.pfsp_bound_batch_dev(inst.handle, kind, int(num_nodes), perm or None, d1 or None,
                                      d2 or None, lb1_out or None, lb2_out or None, stream or None))
+
+
+# pfsp_node_summary: per parent and direction (0 forward, 1 backward)
+SUMMARY_DTYPE = np.dtype([("min", "<i4", (2,)), ("count", "<i4", (2,)), ("sum", "<i8", (2,)),
+                          ("keep", "<u8", (2,))])
+assert SUMMARY_DTYPE.itemsize == 48
+
+
+def pfsp_bound_reduce(inst: Instance, kind, perm, d1, d2, ub, out=None) -> np.ndarray:
+    """Reduce mode on host buffers: one SUMMARY_DTYPE record per node (survivors below ub)."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.uint8)
+    d2 = np.ascontiguousarray(d2, dtype=np.uint8)
+    N = len(d1)
+    if out is None:
+        out = np.empty(N, dtype=SUMMARY_DTYPE)
+    _check(_lib.pfsp_bound_reduce(inst.handle, kind, N, _ptr(perm), _ptr(d1), _ptr(d2), int(ub), _ptr(out)))
+    return out
+
+
+def pfsp_bound_reduce_dev(inst: Instance, kind, num_nodes, perm, d1, d2, ub, out, stream=0):
+    """Reduce mode on device addresses (ints); enqueues on `stream` and returns."""
+    _check(_lib.pfsp_bound_reduce_dev(inst.handle, kind, int(num_nodes), perm or None, d1 or None, d2 or None,
+                                      int(ub), out or None, stream or None))
 
 
 def pfsp_stats(inst: Instance) -> dict:

@@ -220,3 +220,64 @@ def test_heads_tails_refinement_bit_exact(pf, n, m, count):
     assert (g1 >= plain).all() and (g1 > plain).any() == (m > 1)
     with pytest.raises(pf.PfspError):
         pf.pfsp_bound_batch(inst, pf.PFSP_MINHT, perm, d1, d2)
+
+
+def _summaries(o, ub):
+    """Reduce-mode summaries from the oracle's bound arrays o [N, 2, n] (-1: scheduled)."""
+    N, _, n = o.shape
+    on = o >= 0
+    big = np.where(on, o, np.iinfo(np.int32).max).astype(np.int64)
+    mn = big.min(axis=2)
+    cnt = (on & (o == mn[:, :, None])).sum(axis=2)
+    sm = np.where(on, o, 0).astype(np.int64).sum(axis=2)
+    bits = (np.uint64(1) << np.arange(n, dtype=np.uint64))
+    keep = np.where(on & (o < ub), bits[None, None, :], np.uint64(0)).sum(axis=2, dtype=np.uint64)
+    return mn.astype(np.int64), cnt, sm, keep
+
+
+@pytest.mark.parametrize("n,m,count", [(20, 20, 4000), (20, 10, 3000), (12, 5, 3000), (50, 5, 800), (64, 4, 300),
+                                       (33, 7, 500), (9, 1, 500), (1, 3, 20)])
+def test_reduce_mode_matches_oracle(pf, n, m, count):
+    # per parent and direction: least bound, its count, the sum and the job
+    # mask of the children below ub, against the oracle's bound arrays
+    p = inputs.make_instance(n, m, 5000 + n * 64 + m)
+    perm, d1, d2 = inputs.random_nodes(n, count, seed=n + 3 * m, dmax=min(10, n))
+    # append a root, a node without children and one with leaf children
+    perm = np.concatenate([perm, perm[:3]])
+    d1 = np.concatenate([d1, np.array([0, n, max(n - 1, 0)], dtype=np.uint8)])
+    d2 = np.concatenate([d2, np.array([0, 0, 0], dtype=np.uint8)])
+    inst = pf.pfsp_load_instance(p)
+    o1, o2 = orc.children_bounds_batch(p, perm, d1, d2, threads=8)
+    for kind, o in ((pf.PFSP_LB1, o1), (pf.PFSP_LB2, o2)):
+        ub = int(np.median(o[o >= 0])) if (o >= 0).any() else 1
+        s = pf.pfsp_bound_reduce(inst, kind, perm, d1, d2, ub)
+        mn, cnt, sm, keep = _summaries(o, ub)
+        assert (s["min"] == mn).all() and (s["count"] == cnt).all()
+        assert (s["sum"] == sm).all() and (s["keep"] == keep).all()
+    assert s["min"][-2].tolist() == [2**31 - 1] * 2 and s["count"][-2].tolist() == [0, 0]
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_bound_reduce(inst, pf.PFSP_LB1 | pf.PFSP_LB2, perm, d1, d2, 10)
+
+
+def test_reduce_mode_device_entry_point(pf):
+    import torch
+    n, m = 20, 20
+    p = inputs.make_instance(n, m, 8)
+    perm, d1, d2 = inputs.random_nodes(n, 5000, seed=3)
+    d1[7], d2[7] = 15, 9  # invalid: d1 + d2 > n, clamped on the device
+    inst = pf.pfsp_load_instance(p)
+    tp = torch.from_numpy(perm).cuda()
+    t1 = torch.from_numpy(d1).cuda()
+    t2 = torch.from_numpy(d2).cuda()
+    out = torch.empty(len(d1) * 48, dtype=torch.uint8, device="cuda")
+    pf.pfsp_bound_reduce_dev(inst, pf.PFSP_LB2, len(d1), tp.data_ptr(), t1.data_ptr(), t2.data_ptr(), 1500,
+                             out.data_ptr())
+    torch.cuda.synchronize()
+    s = out.cpu().numpy().view(pf.SUMMARY_DTYPE)
+    assert s["min"][7].tolist() == [-1, -1] and s["count"][7].tolist() == [-1, -1]
+    ok = np.ones(len(d1), dtype=bool)
+    ok[7] = False
+    d2[7] = 0
+    ref = pf.pfsp_bound_reduce(inst, pf.PFSP_LB2, perm, d1, d2, 1500)
+    for f in ("min", "count", "sum", "keep"):
+        assert (s[f][ok] == ref[f][ok]).all()
