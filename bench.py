@@ -362,7 +362,8 @@ def learned_leg(pfsp):
             key = "%s_%s" % (shape, "proof" if proof else "find")
             out[key] = {k: v[k] for k in ("solved_by_both", "wall_plain_s", "wall_learned_s", "speedup_wall",
                                           "kernel_plain_s", "kernel_learned_s", "speedup_kernel",
-                                          "node_ratio_learned_over_plain", "ablation_wall_s")}
+                                          "node_ratio_learned_over_plain", "ranking_wall_s",
+                                          "mlp_share_of_learned_wall", "ablation_wall_s")}
             out[key]["same_optimum_every_seed"] = all(r["same_optimum"] for r in v["instances"])
             out[key]["per_seed"] = [{"seed": r["seed"], **{k: {kk: r[k][kk] for kk in ("wall_seconds", "decomposed",
                                                                                         "cmax")}

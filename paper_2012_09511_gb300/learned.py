@@ -162,6 +162,7 @@ def compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), train_seeds=ran
             return sum(r[key][field] for r in done)
 
         t_plain, t_learn = tot("plain", "wall_seconds"), tot("learned", "wall_seconds")
+        t_rank = sum(r["ranking_wall_seconds"] for r in done)
         k_plain, k_learn = tot("plain", "seconds"), tot("learned", "seconds")
         n_plain, n_learn = tot("plain", "decomposed"), tot("learned", "decomposed")
         report["%dx%d" % (n, m)] = {
@@ -169,6 +170,10 @@ def compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), train_seeds=ran
             "solved_by_both": len(done),
             "wall_plain_s": t_plain, "wall_learned_s": t_learn,
             "speedup_wall": (t_plain / t_learn) if t_learn > 0 else None,
+            # the network's share of the learned solver's time: it runs once per
+            # instance, on the root's children, to rank the machine pairs
+            "ranking_wall_s": t_rank,
+            "mlp_share_of_learned_wall": (t_rank / t_learn) if t_learn > 0 else None,
             "kernel_plain_s": k_plain, "kernel_learned_s": k_learn,
             "speedup_kernel": (k_plain / k_learn) if k_learn > 0 else None,
             "node_ratio_learned_over_plain": (n_learn / n_plain) if n_plain > 0 else None,
