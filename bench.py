@@ -177,20 +177,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(p, perm, d1, d2, sample, total=None):
+def cpu_baseline(p, perm, d1, d2, sample, total=None, single=0):
     """The oracle as it stands, on the host cores, over a bounded sample of the batch (the
     first `sample` of its `total` nodes; the node generator is counter-based, so a shorter
-    draw is a prefix of the full batch)."""
+    draw is a prefix of the full batch); with single > 0 also on one thread over the first
+    `single` nodes."""
     import oracle as orc
     cores = os.cpu_count() or 1
+
+    def run(k, threads):
+        t = time.perf_counter()
+        orc.children_bounds_batch(p, perm[:k], d1[:k], d2[:k], threads=threads)
+        dt = time.perf_counter() - t
+        children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
+        return children / dt, dt
+
     k = min(sample, len(d1))
-    t = time.perf_counter()
-    orc.children_bounds_batch(p, perm[:k], d1[:k], d2[:k], threads=cores)
-    dt = time.perf_counter() - t
-    children = int(2 * (N_JOBS - d1[:k].astype(np.int64) - d2[:k].astype(np.int64)).sum())
-    return {"value": children / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
-            "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (
-                k, total or len(d1), dt)}
+    value, dt = run(k, cores)
+    out = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+           "sample": "first %d of the %d nodes, LB1 + LB2 from scratch per child, %.1f s" % (
+               k, total or len(d1), dt)}
+    if single > 0:
+        ks = min(single, len(d1))
+        v1, dt1 = run(ks, 1)
+        out["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1,
+                                "sample": "first %d nodes on one thread" % ks}
+    return out
 
 
 def solve_leg(pfsp, seeds=range(1, 11)):
@@ -557,7 +569,7 @@ def run_native(args):
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(p, perm, d1, d2, args.cpu_sample, total=N, single=20000)
     if not args.no_solve and ws == 1:
         out["solve"] = solve_leg(pfsp, seeds=[int(x) for x in args.solve_seeds.split(",") if x])
     if not args.no_solve and ws == 1:
