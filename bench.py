@@ -266,14 +266,17 @@ def heuristic_leg(pfsp, gold, seeds, threads=4):
     device time and wall time to the proven optimum, nodes decomposed, and what the threads
     contributed.  Node counts differ between runs here, so only the optima are checked."""
     from paper_2012_09511_gb300 import inputs
-    out = {"threads": threads}
-    for name, t in (("without", 0), ("with", threads)):
+    out = {"threads": threads, "kinds": "with: iterated greedy; with_beam: beam search below the promoted "
+                                          "explorer nodes; with_both: half the threads each"}
+    for name, t, kind in (("without", 0, 0), ("with", threads, 0), ("with_beam", threads, 1),
+                          ("with_both", threads, 2)):
         kern = wall = 0.0
         nodes, improved, exact = 0, 0, True
         for seed in seeds:
             g = gold[seed]
             inst = pfsp.pfsp_load_instance(inputs.make_instance(20, 10, seed))
-            r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, heuristic_threads=t, heuristic_seed=seed)
+            r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB2, heuristic_threads=t, heuristic_seed=seed,
+                                heuristic_kind=kind)
             exact &= r["cmax"] == g["optimum"] and r["outcome"] == pfsp.PFSP_OPTIMAL
             kern += r["kernel_seconds"]
             wall += r["seconds"]

@@ -256,7 +256,12 @@ typedef struct {
     int lb1_minht;        /* 1: LB1 (and the LB1 inside LB2) with the heads and tails refinement of
                              PFSP_MINHT; pfsp_solve / pfsp_solve_resumable with the plain solver
                              only (no heuristic threads, no ordering network); 0 (default): off */
-    int reserved[4];
+    int heuristic_kind;   /* search of the heuristic threads: 0 (default) the iterated greedy
+                             (pfsp_iterated_greedy) from the promoted schedules, 1 beam search
+                             (pfsp_beam_search) below the promoted explorer nodes with their
+                             prefix and suffix fixed, widths 1, 2, 4, ... 256, 2 both (odd
+                             threads beam search) */
+    int reserved[3];
 } pfsp_options;
 
 void pfsp_default_options(pfsp_options *opt);
@@ -509,6 +514,24 @@ int pfsp_learn_lb2_pairs(pfsp_instance *inst, const pfsp_mlp *mlp, int64_t num_n
  */
 int pfsp_iterated_greedy(const int32_t *p, int n, int m, const int32_t *start, int64_t iterations,
                          uint64_t seed, int32_t *best_perm, int32_t *best_cmax);
+
+/*
+ * Host beam search (the paper's heuristic threads also run the beam search of
+ * Libralesso et al. on partial schedules of the exact search, prefix and
+ * suffix unchanged, Section 4.2): from the node (prefix, suffix) of the
+ * instance p (n x m, job-major), forward branching only, keeping at each
+ * level the `width` partial schedules of least LB1 (Section 2.4; ties: the
+ * smaller sum of the front on all machines, then generation order).  With a
+ * width of at least the number of completions it enumerates them all and
+ * returns the best.  best_perm (n int32, starting with prefix and ending with
+ * suffix) and *best_cmax receive the best complete schedule found.  Host code
+ * only: needs no GPU.
+ * Errors: PFSP_ERR_INVALID (NULL output, n < 1, m < 1, width < 1, d1 + d2 > n,
+ * prefix and suffix not distinct valid jobs, a negative time),
+ * PFSP_ERR_UNSUPPORTED (n > 64).
+ */
+int pfsp_beam_search(const int32_t *p, int n, int m, const int32_t *prefix, int d1, const int32_t *suffix, int d2,
+                     int width, int32_t *best_perm, int32_t *best_cmax);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char *pfsp_last_error(void);

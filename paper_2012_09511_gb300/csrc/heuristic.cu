@@ -155,11 +155,111 @@ int IteratedGreedy::run(int64_t iterations, const std::atomic<int> *stop) {
 }
 
 // ---------------------------------------------------------------------------
+// Beam search between a fixed prefix and suffix
+// ---------------------------------------------------------------------------
+int beam_search(int n, int m, const int32_t *p, const int *seq, int d1, int d2, int width,
+                std::vector<int> &best) {
+    const int u = n - d1 - d2;
+    // back of sigma2: Eq. 1 on the reversed suffix and machines
+    std::vector<int> back(m, 0), front0(m, 0), rem0(m, 0);
+    for (int i = n - 1; i >= n - d2; --i) {
+        const int32_t *pj = p + (size_t)seq[i] * m;
+        int right = 0;
+        for (int k = m - 1; k >= 0; --k) {
+            back[k] = std::max(back[k], right) + pj[k];
+            right = back[k];
+        }
+    }
+    for (int i = 0; i < d1; ++i) {
+        const int32_t *pj = p + (size_t)seq[i] * m;
+        int left = 0;
+        for (int k = 0; k < m; ++k) {
+            front0[k] = std::max(front0[k], left) + pj[k];
+            left = front0[k];
+        }
+    }
+    std::vector<int> mid(seq + d1, seq + (n - d2));
+    for (int j : mid)
+        for (int k = 0; k < m; ++k) rem0[k] += p[(size_t)j * m + k];
+    // beam entries: front [m], remaining work [m], the jobs placed after sigma1
+    struct Entry {
+        std::vector<int> front, rem, placed;
+        uint64_t used;
+    };
+    std::vector<Entry> beam(1, Entry{front0, rem0, {}, 0ull});
+    struct Child {
+        int lb, fsum, parent, job;
+        bool operator<(const Child &o) const {
+            if (lb != o.lb) return lb < o.lb;
+            if (fsum != o.fsum) return fsum < o.fsum;
+            if (parent != o.parent) return parent < o.parent;
+            return job < o.job;
+        }
+    };
+    std::vector<Child> kids;
+    std::vector<int> f(m);
+    for (int step = 0; step < u; ++step) {
+        kids.clear();
+        for (int b = 0; b < (int)beam.size(); ++b) {
+            const Entry &e = beam[b];
+            for (int t = 0; t < u; ++t) {
+                const int j = mid[t];
+                if ((e.used >> t) & 1ull) continue;
+                const int32_t *pj = p + (size_t)j * m;
+                int left = 0, lb = 0, fs = 0;
+                for (int k = 0; k < m; ++k) {
+                    f[k] = std::max(e.front[k], left) + pj[k];
+                    left = f[k];
+                    lb = std::max(lb, f[k] + e.rem[k] - pj[k] + back[k]);
+                    fs += f[k];
+                }
+                kids.push_back(Child{lb, fs, b, t});
+            }
+        }
+        const size_t keep = std::min<size_t>((size_t)width, kids.size());
+        std::partial_sort(kids.begin(), kids.begin() + keep, kids.end());
+        std::vector<Entry> next;
+        next.reserve(keep);
+        for (size_t q = 0; q < keep; ++q) {
+            const Child &c = kids[q];
+            const Entry &e = beam[c.parent];
+            Entry x{e.front, e.rem, e.placed, e.used | (1ull << c.job)};
+            const int j = mid[c.job];
+            const int32_t *pj = p + (size_t)j * m;
+            int left = 0;
+            for (int k = 0; k < m; ++k) {
+                x.front[k] = std::max(x.front[k], left) + pj[k];
+                left = x.front[k];
+                x.rem[k] -= pj[k];
+            }
+            x.placed.push_back(j);
+            next.push_back(std::move(x));
+        }
+        beam.swap(next);
+    }
+    // complete schedules: makespan = max_k front_k + back_k
+    int bc = INT_MAX, bi = 0;
+    for (int b = 0; b < (int)beam.size(); ++b) {
+        int c = 0;
+        for (int k = 0; k < m; ++k) c = std::max(c, beam[b].front[k] + back[k]);
+        if (c < bc) {
+            bc = c;
+            bi = b;
+        }
+    }
+    best.assign(seq, seq + d1);
+    best.insert(best.end(), beam[bi].placed.begin(), beam[bi].placed.end());
+    best.insert(best.end(), seq + (n - d2), seq + n);
+    return bc;
+}
+
+// ---------------------------------------------------------------------------
 // Heuristic threads beside the explorer pool
 // ---------------------------------------------------------------------------
 constexpr double kSnapPeriod = 0.005;  // seconds between snapshot requests
 constexpr double kSnapWait = 0.002;    // seconds to wait for the explorers' answers
 constexpr int kSlice = 16;             // iterated-greedy iterations between offers
+constexpr int kBeamMax = 256;          // widest beam a thread runs from one node
 
 // Page-locked host memory mapped into the device's address space.
 static bool alloc_mapped(size_t bytes, void **host, void **dev) {
@@ -174,8 +274,8 @@ static bool alloc_mapped(size_t bytes, void **host, void **dev) {
     return true;
 }
 
-HeuristicPool::HeuristicPool(int n, int m, const int32_t *p, int threads, uint64_t seed)
-    : n_(n), m_(m), threads_(threads), K_(0), p_(p, p + (size_t)n * m), seed_(seed) {
+HeuristicPool::HeuristicPool(int n, int m, const int32_t *p, int threads, uint64_t seed, int kind)
+    : n_(n), m_(m), threads_(threads), K_(0), p_(p, p + (size_t)n * m), seed_(seed), kind_(kind) {
     void *h, *d;
     if (!alloc_mapped(sizeof(CoopShared), &h, &d)) return;
     shared_ = (CoopShared *)h;
@@ -206,7 +306,7 @@ void HeuristicPool::start(int ub0, const std::vector<int> &start) {
     best_ = start;
     shared_->host_ub = ub0;
     IteratedGreedy probe(n_, m_, p_.data(), 0);
-    starts_.assign(1, {probe.makespan(start.data(), n_), start});
+    starts_.assign(1, Start{probe.makespan(start.data(), n_), start, 0, 0});
     last_snap_ = now_s();
     for (int t = 0; t < threads_; ++t) pool_.emplace_back(&HeuristicPool::worker, this, t);
 }
@@ -238,11 +338,28 @@ void HeuristicPool::offer(const std::vector<int> &seq, int c) {
 
 void HeuristicPool::worker(int id) {
     IteratedGreedy ig(n_, m_, p_.data(), seed_ * 0x100000001b3ull + (uint64_t)id * 0x9e3779b97f4a7c15ull + 1);
-    std::vector<int> s;
+    std::vector<int> s, b;
+    const bool beam = kind_ == 1 || (kind_ == 2 && (id & 1));
     while (!stop_.load()) {
+        int d1 = 0, d2 = 0;
         {
             std::lock_guard<std::mutex> g(mu_);
-            s = starts_.empty() ? best_ : starts_[next_start_++ % starts_.size()].second;
+            if (starts_.empty()) {
+                s = best_;
+            } else {
+                const Start &st = starts_[next_start_++ % starts_.size()];
+                s = st.seq;
+                d1 = st.d1;
+                d2 = st.d2;
+            }
+        }
+        if (beam) {
+            // iterative beam search below this node: widths 1, 2, 4, ... kBeamMax
+            for (int w = 1; w <= kBeamMax && !stop_.load(); w *= 2) {
+                const int c = beam_search(n_, m_, p_.data(), s.data(), d1, d2, w, b);
+                offer(b, c);
+            }
+            continue;
         }
         ig.reset(s.data());
         offer(ig.best_seq(), ig.best());
@@ -312,7 +429,7 @@ void HeuristicPool::collect() {
     std::vector<int> rank(n_, 0);
     for (int i = 0; i < n_; ++i) rank[inc[i]] = i;
     IteratedGreedy ev(n_, m_, p_.data(), 0);
-    std::vector<std::pair<int, std::vector<int>>> cand;
+    std::vector<Start> cand;
     std::vector<int> seq(n_), mid;
     std::vector<char> seen(n_);
     for (int k = 0; k < K_; ++k) {
@@ -333,14 +450,14 @@ void HeuristicPool::collect() {
         for (int i = 0; i < d1; ++i) seq[i] = sl.perm[i];
         for (int i = 0; i < (int)mid.size(); ++i) seq[d1 + i] = mid[i];
         for (int i = n_ - d2; i < n_; ++i) seq[i] = sl.perm[i];
-        cand.emplace_back(ev.makespan(seq.data(), n_), seq);
+        cand.push_back(Start{ev.makespan(seq.data(), n_), seq, d1, d2});
         promoted_ += 1;
     }
     if (cand.empty()) return;
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     if ((int)cand.size() > 2 * threads_) cand.resize((size_t)2 * threads_);
-    offer(cand[0].second, cand[0].first);
+    offer(cand[0].seq, cand[0].c);
     std::lock_guard<std::mutex> g(mu_);
     starts_ = std::move(cand);
 }
@@ -373,5 +490,30 @@ extern "C" int pfsp_iterated_greedy(const int32_t *p, int n, int m, const int32_
     ig.run(iterations, nullptr);
     for (int i = 0; i < n; ++i) best_perm[i] = ig.best_seq()[i];
     *best_cmax = ig.best();
+    return PFSP_OK;
+}
+
+extern "C" int pfsp_beam_search(const int32_t *p, int n, int m, const int32_t *prefix, int d1, const int32_t *suffix,
+                                int d2, int width, int32_t *best_perm, int32_t *best_cmax) {
+    if (!p || !best_perm || !best_cmax || n < 1 || m < 1 || width < 1 || d1 < 0 || d2 < 0 || d1 + d2 > n ||
+        (d1 > 0 && !prefix) || (d2 > 0 && !suffix))
+        return set_error(PFSP_ERR_INVALID, "pfsp_beam_search: bad argument");
+    if (n > 64) return set_error(PFSP_ERR_UNSUPPORTED, "pfsp_beam_search: n > 64");
+    for (int i = 0; i < n * m; ++i)
+        if (p[i] < 0) return set_error(PFSP_ERR_INVALID, "pfsp_beam_search: negative processing time");
+    std::vector<char> seen(n, 0);
+    std::vector<int> seq(n);
+    for (int i = 0; i < d1 + d2; ++i) {
+        const int j = i < d1 ? prefix[i] : suffix[i - d1];
+        if (j < 0 || j >= n || seen[j]) return set_error(PFSP_ERR_INVALID, "pfsp_beam_search: prefix and suffix must be distinct jobs");
+        seen[j] = 1;
+    }
+    for (int i = 0; i < d1; ++i) seq[i] = prefix[i];
+    for (int i = 0; i < d2; ++i) seq[n - d2 + i] = suffix[i];
+    for (int j = 0, at = d1; j < n; ++j)
+        if (!seen[j]) seq[at++] = j;
+    std::vector<int> best;
+    *best_cmax = beam_search(n, m, p, seq.data(), d1, d2, width, best);
+    for (int i = 0; i < n; ++i) best_perm[i] = best[i];
     return PFSP_OK;
 }

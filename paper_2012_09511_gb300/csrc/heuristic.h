@@ -60,6 +60,27 @@ class IteratedGreedy {
     std::vector<int> e_, q_, f_, order_;
 };
 
+// Beam search over forward branching between a fixed prefix sigma1 (seq's
+// first d1 jobs) and a fixed suffix sigma2 (its last d2 jobs): level by level,
+// every partial schedule of the beam is extended by each unscheduled job and
+// the `width` extensions of least LB1 (Section 2.4, the bound as the guide;
+// ties: the smaller sum of the front, then the order of generation) are kept.
+// The paper applies the beam search of Libralesso et al. to partial schedules
+// of the exact search this way, prefix and suffix unchanged (Section 4.2).
+// With a width of at least the number of completions it is exhaustive.
+// Returns the best makespan and writes its schedule to best.
+int beam_search(int n, int m, const int32_t *p, const int *seq, int d1, int d2, int width, std::vector<int> &best);
+
+// A starting point of the threads: a complete schedule, its makespan, and the
+// depths of the explorer node it was promoted from (0, 0 for the initial one).
+struct Start {
+    int c;
+    std::vector<int> seq;
+    int d1, d2;
+    bool operator<(const Start &o) const { return c != o.c ? c < o.c : seq < o.seq; }
+    bool operator==(const Start &o) const { return c == o.c && seq == o.seq; }
+};
+
 // The heuristic threads of one solve.  The calling thread drives snapshots
 // (tick) while the explorer pool runs: the explorers' current nodes are
 // promoted to complete schedules (unscheduled jobs in the incumbent's order),
@@ -67,7 +88,8 @@ class IteratedGreedy {
 // runs the iterated greedy from one of them for a slice of iterations.
 class HeuristicPool {
   public:
-    HeuristicPool(int n, int m, const int32_t *p, int threads, uint64_t seed);
+    // kind: 0 iterated greedy, 1 beam search from the promoted nodes, 2 both (alternate threads)
+    HeuristicPool(int n, int m, const int32_t *p, int threads, uint64_t seed, int kind = 0);
     ~HeuristicPool();
     bool ok() const { return shared_ != nullptr; }
     bool attach(int explorers);  // the explorers' snapshot slots, once their count is known
@@ -104,7 +126,8 @@ class HeuristicPool {
     int own_c_ = 0;     // best makespan the threads found
     int dev_seen_ = INT32_MAX;
     std::vector<int> best_;
-    std::vector<std::pair<int, std::vector<int>>> starts_;  // best promoted schedules
+    std::vector<Start> starts_;  // best promoted schedules
+    int kind_ = 0;
     uint64_t next_start_ = 0;
     std::atomic<uint64_t> improvements_{0};
     uint64_t promoted_ = 0;

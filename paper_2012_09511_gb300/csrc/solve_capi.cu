@@ -129,6 +129,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT keeps the tree of MinMin and MinBranch only");
     if (opt->heuristic_threads < 0 || opt->heuristic_threads > 256)
         return set_error(PFSP_ERR_INVALID, "heuristic_threads must be in 0..256");
+    if (opt->heuristic_kind < 0 || opt->heuristic_kind > 2)
+        return set_error(PFSP_ERR_INVALID, "heuristic_kind must be 0, 1 or 2");
     if (opt->heuristic_threads && (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)))
         return set_error(PFSP_ERR_UNSUPPORTED, "heuristic threads run beside the plain solver only");
     if (opt->lb1_minht != 0 && opt->lb1_minht != 1) return set_error(PFSP_ERR_INVALID, "lb1_minht must be 0 or 1");
@@ -243,7 +245,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     std::unique_ptr<HeuristicPool> hp;
     std::vector<int> h_start;
     if (opt->heuristic_threads > 0) {
-        hp.reset(new HeuristicPool(n, m, inst->p_host, opt->heuristic_threads, (uint64_t)(uint32_t)opt->heuristic_seed));
+        hp.reset(new HeuristicPool(n, m, inst->p_host, opt->heuristic_threads, (uint64_t)(uint32_t)opt->heuristic_seed,
+                                   opt->heuristic_kind));
         if (!hp->ok()) return set_error(PFSP_ERR_OOM, "host-mapped memory for the heuristic threads");
         a.coop = hp->device_shared();
         if ((int)neh_perm.size() == n) h_start = neh_perm;

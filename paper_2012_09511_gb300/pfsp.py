@@ -74,7 +74,7 @@ class pfsp_options(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
                 ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("phase_timers", ctypes.c_int),
                 ("heuristic_threads", ctypes.c_int), ("heuristic_seed", ctypes.c_int), ("lb1_minht", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("heuristic_kind", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -112,6 +112,9 @@ _lib.pfsp_solve_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POIN
 _lib.pfsp_iterated_greedy.restype = ctypes.c_int
 _lib.pfsp_iterated_greedy.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_uint64,
                                       _vp, ctypes.POINTER(ctypes.c_int32)]
+_lib.pfsp_beam_search.restype = ctypes.c_int
+_lib.pfsp_beam_search.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                  _vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.pfsp_autotune_batch.restype = ctypes.c_int
 _lib.pfsp_autotune_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(pfsp_options),
                                      ctypes.c_int, ctypes.POINTER(pfsp_options)]
@@ -302,6 +305,20 @@ def pfsp_iterated_greedy(p, iterations, seed=0, start=None):
     perm = np.full(n, -1, dtype=np.int32)
     c = ctypes.c_int32()
     _check(_lib.pfsp_iterated_greedy(_ptr(p), n, m, _ptr(s), int(iterations), int(seed), _ptr(perm), ctypes.byref(c)))
+    return c.value, perm
+
+
+def pfsp_beam_search(p, width, prefix=(), suffix=()):
+    """Host beam search on p ([n, m] job-major) below the node (prefix, suffix).
+    Returns (cmax, perm)."""
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    n, m = p.shape
+    a = np.ascontiguousarray(list(prefix) or [0], dtype=np.int32)
+    b = np.ascontiguousarray(list(suffix) or [0], dtype=np.int32)
+    perm = np.full(n, -1, dtype=np.int32)
+    c = ctypes.c_int32()
+    _check(_lib.pfsp_beam_search(_ptr(p), n, m, _ptr(a), len(prefix), _ptr(b), len(suffix), int(width), _ptr(perm),
+                                 ctypes.byref(c)))
     return c.value, perm
 
 

@@ -88,3 +88,66 @@ def test_invalid_arguments(pf):
     bad[0, 0] = -1
     with pytest.raises(pf.PfspError):
         pf.pfsp_iterated_greedy(bad, 5)
+
+
+def _best_completion(p, prefix, suffix):
+    import itertools
+    n = p.shape[0]
+    rest = [j for j in range(n) if j not in prefix and j not in suffix]
+    return min(orc.makespan(p, list(prefix) + list(mid) + list(suffix)) for mid in itertools.permutations(rest))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_beam_search_wide_enough_is_exhaustive(pf, seed):
+    # a width of at least the number of partial schedules of every level keeps
+    # them all: the beam search is then an enumeration and returns the optimum
+    n, m = 7, 4
+    p = inputs.make_instance(n, m, 200 + seed)
+    opt, _ = orc.brute_force(p)
+    c, perm = pf.pfsp_beam_search(p, 5040)
+    _valid(p, perm, c)
+    assert c == opt
+
+
+@pytest.mark.parametrize("prefix,suffix", [([3], [5]), ([0, 6], []), ([], [1, 2]), ([4, 2, 0], [6, 1])])
+def test_beam_search_keeps_the_node(pf, prefix, suffix):
+    n, m = 8, 5
+    p = inputs.make_instance(n, m, 31)
+    best = _best_completion(p, prefix, suffix)
+    for width in (1, 3, 40320):
+        c, perm = pf.pfsp_beam_search(p, width, prefix=prefix, suffix=suffix)
+        _valid(p, perm, c)
+        assert perm[:len(prefix)].tolist() == prefix
+        assert perm[n - len(suffix):].tolist() == suffix
+        # never below the best completion, and the bound of the node is below both
+        assert c >= best >= orc.lb1(p, prefix, suffix)
+        if width == 40320:
+            assert c == best
+
+
+def test_beam_search_width_one_is_the_lb1_greedy_dive(pf):
+    # width 1: at each level the extension of least LB1 (ties: smaller front sum)
+    n, m = 9, 4
+    p = inputs.make_instance(n, m, 17)
+    c, perm = pf.pfsp_beam_search(p, 1)
+    seq = []
+    for _ in range(n):
+        cand = []
+        for j in range(n):
+            if j in seq:
+                continue
+            lb = orc.lb1(p, seq + [j], [])
+            fs = int(orc.completion(p, seq + [j]).sum())
+            cand.append((lb, fs, j))
+        seq.append(min(cand)[2])
+    assert perm.tolist() == seq and c == orc.makespan(p, seq)
+
+
+def test_beam_search_invalid_arguments(pf):
+    p = inputs.make_instance(6, 3, 1)
+    for kw in (dict(prefix=[0], suffix=[0]), dict(prefix=[9]), dict(prefix=[0, 1, 2, 3], suffix=[4, 5, 1])):
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_beam_search(p, 4, **kw)
+        assert e.value.code == pf.PFSP_ERR_INVALID
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_beam_search(p, 0)

@@ -65,6 +65,21 @@ def test_proof_mode_tree_is_unchanged(pf, gold):
         assert r["heuristic_improvements"] == 0 and r["heuristic_cmax"] == pf.INT32_MAX
 
 
+@pytest.mark.parametrize("kind", [1, 2])
+def test_beam_search_threads_reach_the_optimum(pf, gold, kind):
+    # heuristic_kind 1: beam search below the promoted explorer nodes; 2: both searches
+    for seed in (1, 4, 7):
+        g = gold[seed]
+        p = inputs.make_instance(20, 10, seed)
+        r = pf.pfsp_solve(pf.pfsp_load_instance(p), bound=pf.PFSP_LB2, heuristic_threads=4, heuristic_kind=kind,
+                          heuristic_seed=seed)
+        assert r["outcome"] == pf.PFSP_OPTIMAL
+        _check(p, r, g["optimum"])
+        assert r["heuristic_cmax"] >= g["optimum"]
+        if seed == 4:
+            assert r["promoted"] > 0 and r["heuristic_improvements"] > 0
+
+
 def test_long_solve_promotes_explorer_nodes(pf, gold):
     # seed 4 takes tens of milliseconds from NEH: several snapshot rounds
     g = gold[4]
@@ -102,9 +117,10 @@ def test_checkpoint_after_heuristic_segment_resumes_exactly(pf, gold):
 def test_heuristic_options_validation(pf):
     p = inputs.make_instance(8, 4, 1)
     inst = pf.pfsp_load_instance(p)
-    with pytest.raises(pf.PfspError) as e:
-        pf.pfsp_solve(inst, heuristic_threads=-1)
-    assert e.value.code == pf.PFSP_ERR_INVALID
+    for bad in (dict(heuristic_threads=-1), dict(heuristic_threads=1, heuristic_kind=3)):
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_solve(inst, **bad)
+        assert e.value.code == pf.PFSP_ERR_INVALID
     with pytest.raises(pf.PfspError) as e:
         pf.pfsp_solve_batch([inst], heuristic_threads=1)
     assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
