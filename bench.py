@@ -236,7 +236,24 @@ def solve_leg(pfsp, seeds=range(1, 11)):
             "oracle_proof_s_single_thread": sum(gold[s]["oracle_proof_seconds"] for s in seeds),
             "branching_rules": rules_leg(pfsp, gold, seeds),
             "heuristic_threads": heuristic_leg(pfsp, gold, seeds),
-            "lb1_minht": minht_leg(pfsp)}
+            "lb1_minht": minht_leg(pfsp),
+            "lb1_30x15_rate": lb1_rate_leg(pfsp)}
+
+
+def lb1_rate_leg(pfsp, seeds=(1, 2, 3), node_limit=20_000_000):
+    """Decomposed nodes per second of the explorer pool with LB1 and MinMin on 30-job,
+    15-machine instances (the size and bound of the paper's single-GPU runs on VFR 30x15
+    instances, which are not available here: seeded uniform [1, 99] stand-ins), from the
+    NEH incumbent, stopped at a node limit."""
+    from paper_2012_09511_gb300 import inputs
+    nodes, secs = 0, 0.0
+    for seed in seeds:
+        inst = pfsp.pfsp_load_instance(inputs.make_instance(30, 15, 3000 + seed))
+        r = pfsp.pfsp_solve(inst, bound=pfsp.PFSP_LB1, node_limit=node_limit)
+        nodes += r["decomposed"]
+        secs += r["kernel_seconds"]
+    return {"workload": "n=30 m=15 uniform[1,99] seeds 3001-3003, LB1 + MinMin from NEH, %d-node limit each" % node_limit,
+            "decomposed_nodes": nodes, "kernel_s": secs, "decomposed_nodes_per_s": nodes / max(secs, 1e-9)}
 
 
 def minht_leg(pfsp):
