@@ -85,6 +85,29 @@ def algorithmic_ops(n, m, d1, d2):
     return int((lb1 + lb2).sum())
 
 
+def pin_to_gpu_cpus(dev_index):
+    """Run the host side on the CPUs next to the GPU, so that the pinned buffers of the
+    end-to-end leg are allocated in the memory of the socket the GPU is attached to.
+    Returns a description, or "default" when the topology is not readable."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return "default"
+        os.sched_setaffinity(0, cpus)
+        return "cpus %s (local to GPU %s)" % (spec, bus)
+    except (OSError, ValueError, AttributeError):
+        return "default"
+
+
 def survey_equivalent_ops(n, m, d1, d2):
     """The per-parent work of the bounds evaluated child by child, as the
     paper's recurrence states them (the scope table's figure): LB2 4 ops per
@@ -183,7 +206,7 @@ def cpu_baseline(p, perm, d1, d2, sample, total=None, single=0):
     draw is a prefix of the full batch); with single > 0 also on one thread over the first
     `single` nodes."""
     import oracle as orc
-    cores = os.cpu_count() or 1
+    cores = len(os.sched_getaffinity(0)) or 1
 
     def run(k, threads):
         t = time.perf_counter()
@@ -440,6 +463,7 @@ def run_native(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    host_cpus = pin_to_gpu_cpus(local)
     from paper_2012_09511_gb300 import build
     build.build()
     from paper_2012_09511_gb300 import inputs, pfsp, shard
@@ -568,7 +592,8 @@ def run_native(args):
         "config": {"workload": WORKLOAD, "n": n, "m": m, "nodes_per_gpu": N, "seed": SEED,
                    "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)",
                    "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU"},
+                   "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU",
+                   "host_cpus": host_cpus},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
