@@ -52,14 +52,16 @@ struct Stats {
 };
 
 // KIND selects the instantiation: kKindPlain, kKindLearned (runs the ordering
-// network) or kKindCoop (exchanges with the host heuristic threads).  The
-// plain solver's kernel carries none of the others' code: the explorer loop is
-// bound by instruction fetch, so even code that never runs slows it down.
+// network), kKindCoop (exchanges with the host heuristic threads), kKindMinht
+// (refined LB1) or kKindLb1 (LB1 solves, without the LB2 sweep).  Each
+// kernel carries only its own code: the explorer loop is bound by
+// instruction fetch, so even code that never runs slows it down.
 template <int NW, int MT, int KIND>
 struct Explorer {
     static constexpr bool LEARNED = KIND == kKindLearned;
     static constexpr bool COOP = KIND == kKindCoop;
     static constexpr bool MINHT = KIND == kKindMinht;
+    static constexpr bool LB1_ONLY = KIND == kKindLb1;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -406,13 +408,13 @@ struct Explorer {
             }
         }
         ChildBounds<NW> cb;
-        const int kind = a.bound == PFSP_LB2 ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
+        const int kind = (!LB1_ONLY && a.bound == PFSP_LB2) ? (PFSP_LB1 | PFSP_LB2) : PFSP_LB1;
         decompose_lb1<NW, MT>(T, W, n, m, kind, job0, job1, d1, d2, cb);
         if constexpr (MINHT) {
             if (d1 == 0 || d2 == 0) refine_minht<NW, MT>(T, W, n, m, d1, d2, cb);
         }
         tick(counted ? kPhLB1 : kPhInit);
-        if ((kind & PFSP_LB2) && m >= 2) {
+        if (!LB1_ONLY && (kind & PFSP_LB2) && m >= 2) {
             const int *order = nullptr;
             if constexpr (LEARNED) {
                 if ((a.learned & PFSP_LEARN_PAIR_ORDER) && net && S >= 2 && cb.u > 0 && I + 1 < a.learn_depth) {
@@ -439,8 +441,8 @@ struct Explorer {
         int mn = INT_MAX;
         for (int h = 0; h < NW; ++h) {
             int c = lane + 32 * h;
-            vf[h] = a.bound == PFSP_LB2 ? cb.lb2f[h] : cb.lb1f[h];
-            vb[h] = a.bound == PFSP_LB2 ? cb.lb2b[h] : cb.lb1b[h];
+            vf[h] = (!LB1_ONLY && a.bound == PFSP_LB2) ? cb.lb2f[h] : cb.lb1f[h];
+            vb[h] = (!LB1_ONLY && a.bound == PFSP_LB2) ? cb.lb2b[h] : cb.lb1b[h];
             if (c < u) {
                 int xf = capped ? min(vf[h], a.cap) : vf[h];
                 int xb = capped ? min(vb[h], a.cap) : vb[h];

@@ -26,6 +26,7 @@ constexpr int kKindPlain = 0;    // the paper's solver
 constexpr int kKindLearned = 1;  // with the ordering network
 constexpr int kKindCoop = 2;     // with the host heuristic threads' exchange
 constexpr int kKindMinht = 3;    // with the heads and tails refinement of LB1
+constexpr int kKindLb1 = 4;      // LB1 solves: the loop carries no LB2 code
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
