@@ -246,7 +246,8 @@ typedef struct {
     int learn_depth;      /* the network orders rows of level < learn_depth only (0 = every level) */
     int phase_timers;     /* 1: fill pfsp_stats_t.phase_cycles (reads the SM clock at every phase
                              boundary, which slows the solve down several times: for relative
-                             profiling only); 0 (default): off */
+                             profiling only; runs in a kernel instantiation of its own, not
+                             beside heuristic threads); 0 (default): off */
     int heuristic_threads; /* pfsp_solve / pfsp_solve_resumable: host threads running the iterated
                               greedy beside the explorer pool (Section 4.2's heuristic threads);
                               0 (default): none.  Their improved schedules lower the explorers'

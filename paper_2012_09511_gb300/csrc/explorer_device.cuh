@@ -53,7 +53,8 @@ struct Stats {
 
 // KIND selects the instantiation: kKindPlain, kKindLearned (runs the ordering
 // network), kKindCoop (exchanges with the host heuristic threads), kKindMinht
-// (refined LB1) or kKindLb1 (LB1 solves, without the LB2 sweep).  Each
+// (refined LB1), kKindLb1 (LB1 solves, without the LB2 sweep) or kKindDiag
+// (phase timers and traces).  Each
 // kernel carries only its own code: the explorer loop is bound by
 // instruction fetch, so even code that never runs slows it down.
 template <int NW, int MT, int KIND>
@@ -62,6 +63,10 @@ struct Explorer {
     static constexpr bool COOP = KIND == kKindCoop;
     static constexpr bool MINHT = KIND == kKindMinht;
     static constexpr bool LB1_ONLY = KIND == kKindLb1;
+    // phase timers and decomposition traces: compiled out of the fast kernels
+    // (plain LB2, LB1-only, and the one beside the heuristic threads), which
+    // run solves that ask for neither
+    static constexpr bool DIAG = KIND != kKindPlain && KIND != kKindLb1 && KIND != kKindCoop;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -115,7 +120,7 @@ struct Explorer {
     // Charge the cycles since the last mark to phase p (lane 0; the sums are
     // reported per solve).  A uniform test when the timers are off.
     __device__ __forceinline__ void tick(int p) {
-        if (timed && lane == 0) {
+        if (DIAG && timed && lane == 0) {
             const long long t = clock64();
             X.ph[p] += (unsigned long long)(t - t_mark);
             t_mark = t;
@@ -395,7 +400,7 @@ struct Explorer {
         const int job0 = lane < n ? X.perm[lane] : 0;
         const int job1 = (NW == 2 && lane + 32 < n) ? X.perm[lane + 32] : 0;
         tick(counted ? kPhDecode : kPhInit);
-        if (counted && a.trace_cap > 0 && (st.decomposed % (unsigned long long)a.trace_stride) == 0) {
+        if (DIAG && counted && a.trace_cap > 0 && (st.decomposed % (unsigned long long)a.trace_stride) == 0) {
             unsigned long long slot = 0;
             if (lane == 0) slot = atomicAdd(a.trace_count, 1ull);
             slot = __shfl_sync(PFSP_FULL, slot, 0);

@@ -134,6 +134,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (opt->heuristic_threads && (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)))
         return set_error(PFSP_ERR_UNSUPPORTED, "heuristic threads run beside the plain solver only");
     if (opt->lb1_minht != 0 && opt->lb1_minht != 1) return set_error(PFSP_ERR_INVALID, "lb1_minht must be 0 or 1");
+    if (opt->heuristic_threads && (opt->phase_timers || tr))
+        return set_error(PFSP_ERR_UNSUPPORTED, "phase timers and traces are not taken beside heuristic threads");
     if (opt->lb1_minht && (opt->heuristic_threads || (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER))))
         return set_error(PFSP_ERR_UNSUPPORTED, "lb1_minht runs in the plain solver only");
     const bool use_net = (opt->learned & (PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER)) != 0;
@@ -196,6 +198,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.bound = opt->bound;
     a.branching = opt->branching;
     a.minht = opt->lb1_minht;
+    a.diag = (opt->phase_timers || tr) ? 1 : 0;
     a.cap = resuming ? rh.cap : ub0;
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
     // the network's inference image: every output column when it orders the

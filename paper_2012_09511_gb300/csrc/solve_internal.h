@@ -27,6 +27,7 @@ constexpr int kKindLearned = 1;  // with the ordering network
 constexpr int kKindCoop = 2;     // with the host heuristic threads' exchange
 constexpr int kKindMinht = 3;    // with the heads and tails refinement of LB1
 constexpr int kKindLb1 = 4;      // LB1 solves: the loop carries no LB2 code
+constexpr int kKindDiag = 5;     // with phase timers and decomposition traces (both bounds)
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
@@ -125,6 +126,7 @@ struct SolveArgs {
     CoopShared *coop;     // host heuristic threads' exchange (NULL: none)
     CoopSlot *coop_slots; // [K] the explorers' snapshot slots
     int minht;            // 1: LB1 with the heads and tails refinement (its own kernel)
+    int diag;             // 1: phase timers or a trace requested (the kernel that carries them)
     int rows_smem;        // 1: each explorer's rows live in shared memory after its explorer state
 };
 
@@ -143,6 +145,8 @@ int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_coop(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_coop(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+int solve_occupancy_diag(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve_diag(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_minht(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_minht(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 
