@@ -53,8 +53,8 @@ struct Stats {
 
 // KIND selects the instantiation: kKindPlain, kKindLearned (runs the ordering
 // network), kKindCoop (exchanges with the host heuristic threads), kKindMinht
-// (refined LB1), kKindLb1 (LB1 solves, without the LB2 sweep) or kKindDiag
-// (phase timers and traces).  Each
+// (refined LB1), kKindLb1 (LB1 solves, without the LB2 sweep), kKindDiag
+// (phase timers and traces) or kKindEE (early exit of the LB2 sweep).  Each
 // kernel carries only its own code: the explorer loop is bound by
 // instruction fetch, so even code that never runs slows it down.
 template <int NW, int MT, int KIND>
@@ -66,7 +66,9 @@ struct Explorer {
     // phase timers and decomposition traces: compiled out of the fast kernels
     // (plain LB2, LB1-only, and the one beside the heuristic threads), which
     // run solves that ask for neither
-    static constexpr bool DIAG = KIND != kKindPlain && KIND != kKindLb1 && KIND != kKindCoop;
+    static constexpr bool DIAG = KIND != kKindPlain && KIND != kKindLb1 && KIND != kKindCoop && KIND != kKindEE;
+    // early exit of the LB2 sweep: compiled out of the plain kernel
+    static constexpr bool EARLY = KIND != kKindPlain && KIND != kKindLb1;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -427,9 +429,10 @@ struct Explorer {
                     order = X.sorder;
                 }
             }
-            const int swept = decompose_lb2<NW, MT>(T, W, n, m, S, cb,
-                                                    (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
-                                                    (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order);
+            const int swept = EARLY ? decompose_lb2<NW, MT>(T, W, n, m, S, cb,
+                                                            (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
+                                                            (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order)
+                                    : decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
             if (counted) st.slots += swept;
         }
         tick(counted ? kPhLB2 : kPhInit);

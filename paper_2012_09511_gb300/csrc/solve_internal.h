@@ -28,6 +28,7 @@ constexpr int kKindCoop = 2;     // with the host heuristic threads' exchange
 constexpr int kKindMinht = 3;    // with the heads and tails refinement of LB1
 constexpr int kKindLb1 = 4;      // LB1 solves: the loop carries no LB2 code
 constexpr int kKindDiag = 5;     // with phase timers and decomposition traces (both bounds)
+constexpr int kKindEE = 6;       // with the early exit of the LB2 sweep (PFSP_EARLY_EXIT)
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
@@ -145,6 +146,8 @@ int solve_occupancy_learned(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_learned(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_coop(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_coop(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
+int solve_occupancy_ee(const SolveArgs &a, int warps, size_t smem);
+cudaError_t launch_solve_ee(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_diag(const SolveArgs &a, int warps, size_t smem);
 cudaError_t launch_solve_diag(const SolveArgs &a, int blocks, int warps, size_t smem, cudaStream_t st);
 int solve_occupancy_minht(const SolveArgs &a, int warps, size_t smem);

@@ -57,6 +57,7 @@ int solve_occupancy(const SolveArgs &a, int warps, size_t smem) {
     if (a.coop) return solve_occupancy_coop(a, warps, smem);
     if (a.minht) return solve_occupancy_minht(a, warps, smem);
     if (a.diag) return solve_occupancy_diag(a, warps, smem);
+    if (a.bound == PFSP_LB2 && (a.learned & PFSP_EARLY_EXIT)) return solve_occupancy_ee(a, warps, smem);
     if (a.bound == PFSP_LB1) {
         if (a.n <= 32) { PFSP_DISPATCH(1, kKindLb1, occupancy_t, warps, smem) }
         PFSP_DISPATCH(2, kKindLb1, occupancy_t, warps, smem)
@@ -70,6 +71,7 @@ cudaError_t launch_solve(const SolveArgs &a, int blocks, int warps, size_t smem,
     if (a.coop) return launch_solve_coop(a, blocks, warps, smem, st);
     if (a.minht) return launch_solve_minht(a, blocks, warps, smem, st);
     if (a.diag) return launch_solve_diag(a, blocks, warps, smem, st);
+    if (a.bound == PFSP_LB2 && (a.learned & PFSP_EARLY_EXIT)) return launch_solve_ee(a, blocks, warps, smem, st);
     if (a.bound == PFSP_LB1) {
         if (a.n <= 32) { PFSP_DISPATCH(1, kKindLb1, launch_solve_t, a, blocks, warps, smem, st) }
         PFSP_DISPATCH(2, kKindLb1, launch_solve_t, a, blocks, warps, smem, st)
