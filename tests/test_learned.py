@@ -270,6 +270,12 @@ def test_learned_lb2_pair_subset_keeps_the_solve_exact(pf):
     assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (want["decomposed"], want["bounded"],
                                                                       want["pruned"])
     assert r["lb2_slots"] <= r["decomposed"]
+    # the learned solver's own options (the subset in the plain kernel)
+    from paper_2012_09511_gb300 import learned
+    r0 = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, **learned.learned_options(pf))
+    assert (r0["decomposed"], r0["bounded_children"], r0["pruned"]) == (want["decomposed"], want["bounded"],
+                                                                         want["pruned"])
+    assert r0["lb2_slots"] == r0["decomposed"]  # one 32-pair slot per decomposition
     f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2)
     assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
     assert len(pf.pfsp_learn_lb2_pairs(inst, mlp, keep=100)) == P  # keep >= P: every pair
