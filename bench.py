@@ -108,12 +108,12 @@ def pin_to_gpu_cpus(dev_index):
         return "default"
 
 
-def survey_equivalent_ops(n, m, d1, d2):
+def child_by_child_ops(n, m, d1, d2):
     """The per-parent work of the bounds evaluated child by child, as the
-    paper's recurrence states them (the scope table's figure): LB2 4 ops per
-    (child, pair, unscheduled job of the child), 2P u (u - 1) such steps; LB1 4m
-    per child and 2m (d1 + d2) per parent.  This design evaluates the same
-    values with the O(P u) composition counted by algorithmic_ops."""
+    paper's recurrence states them: LB2 4 ops per (child, pair, unscheduled job
+    of the child), 2P u (u - 1) such steps; LB1 4m per child and 2m (d1 + d2)
+    per parent.  This design evaluates the same values with the O(P u)
+    composition counted by algorithmic_ops."""
     d = d1.astype(np.int64) + d2.astype(np.int64)
     u = n - d
     P = m * (m - 1) // 2
@@ -592,7 +592,7 @@ def run_native(args):
     achieved = ops / (launch_ms * 1e-3)
     ncu = ncu_summary()
     traffic = ncu.get("dram_bytes_per_launch_full") if ncu else None
-    survey_ops = survey_equivalent_ops(n, m, d1, d2)
+    cbc_ops = child_by_child_ops(n, m, d1, d2)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": slowest_s * 1e3 / args.steps, "higher_is_better": True,
@@ -607,8 +607,8 @@ def run_native(args):
                      "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
                          nsm, INT32_LANES_PER_SM_CLK, sm_max),
                      "ops_per_launch": ops, "kernel_ms": launch_ms,
-                     "child_by_child_ops_per_launch": survey_ops,
-                     "child_by_child_frac": survey_ops / (launch_ms * 1e-3) / peak_ops,
+                     "child_by_child_ops_per_launch": cbc_ops,
+                     "child_by_child_frac": cbc_ops / (launch_ms * 1e-3) / peak_ops,
                      "ncu_utilisation": {k: ncu[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct",
                                                              "lsu_pipe_pct") if k in ncu} if ncu else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
