@@ -8,14 +8,13 @@ pfsp_solve runs the plain and the learned solvers.
 
 The learned solver restricts LB2 to the machine pairs that the network
 predicts most often give a child's LB2 (scored on the root's children; half
-of the 32-pair slots: one of two at m = 10, three of six at m = 20), and
-skips a node's LB2 sweep when
-every child of one direction already has an LB1 at or above the incumbent.
-Both keep the search exact (a subset LB2 is still a lower bound; a skipped
-node has no child below the incumbent), so its optimum is always the plain
-solver's; the comparison reports the time to the proven optimum (wall time,
-ranking included) and the decomposed-node counts of both.  The network's row
-order is reported as an ablation.
+of the 32-pair slots: one of two at m = 10, three of six at m = 20).  A
+subset LB2 is still a lower bound, so the search stays exact and its optimum
+is always the plain solver's; the comparison reports the time to the proven
+optimum (wall time, ranking included) and the decomposed-node counts of both.
+The early exit of the LB2 sweep (a node one of whose directions has every
+child at or above the incumbent needs no sweep) and the network's row order
+are reported as ablations.
 """
 from __future__ import annotations
 
