@@ -65,3 +65,21 @@ def test_host_side_validation_without_gpu():
     with pytest.raises(pfsp.PfspError) as e:
         pfsp.pfsp_load_instance(np.full((5, 3), 1 << 23, dtype=np.int32))
     assert e.value.code == pfsp.PFSP_ERR_UNSUPPORTED
+
+
+def test_entry_points_reject_null_instances_without_gpu():
+    # the instance check runs before any device work, for every entry point
+    # that takes one
+    from paper_2012_09511_gb300 import pfsp
+    import ctypes
+    lib = pfsp._lib
+    buf = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    assert lib.pfsp_bound_batch(None, 3, 1, buf, buf, buf, out, out) == pfsp.PFSP_ERR_INVALID
+    assert lib.pfsp_bound_reduce(None, 2, 1, buf, buf, buf, 100, out) == pfsp.PFSP_ERR_INVALID
+    assert lib.pfsp_bound_reduce_dev(None, 2, 1, buf, buf, buf, 100, out, None) == pfsp.PFSP_ERR_INVALID
+    o = pfsp.pfsp_default_options()
+    best = ctypes.c_int32()
+    oc = ctypes.c_int()
+    assert lib.pfsp_solve(None, ctypes.byref(o), ctypes.byref(best), out, ctypes.byref(oc)) == pfsp.PFSP_ERR_INVALID
+    assert pfsp.SUMMARY_DTYPE.itemsize == 48
