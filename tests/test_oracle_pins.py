@@ -417,6 +417,24 @@ def test_minmin_picks_a_fully_pruned_direction(capped):
             assert all(v >= ub for v in chosen), (lbf, lbb, d)
 
 
+def test_minbranch_picks_a_fully_pruned_direction():
+    # the same dead-end property for MinBranch (counting against the initial
+    # incumbent): a direction with every child at or above it has no survivor,
+    # so MinBranch picks it unless the other has none either, and then no child
+    # of either direction survives (the early exit stays exact under MinBranch)
+    rng = np.random.default_rng(11)
+    ub = 10
+    for _ in range(4000):
+        u = int(rng.integers(1, 5))
+        jobs = list(range(u))
+        full = rng.integers(ub, ub + 4, size=u)
+        other = rng.integers(ub - 3, ub + 3, size=u)
+        for lbf, lbb in ((full, other), (other, full)):
+            d = orc.branch_rule(lbf, lbb, jobs, orc.MINBRANCH, cap=ub)
+            chosen = lbf if d == orc.FWD else lbb
+            assert all(v >= ub for v in chosen), (lbf, lbb, d)
+
+
 # ---------------------------------------------------------------- search ---
 
 @pytest.mark.parametrize("seed", range(1, 11))
