@@ -435,6 +435,15 @@ def test_minbranch_picks_a_fully_pruned_direction():
             assert all(v >= ub for v in chosen), (lbf, lbb, d)
 
 
+def test_minsum_may_branch_away_from_a_fully_pruned_direction():
+    # why the early exit is refused with MinSum: forward is entirely at or
+    # above the incumbent 10, yet backward's larger sum (39 > 20) wins, and
+    # backward keeps a child (9) below the incumbent; an early exit would have
+    # replaced backward's LB2 by lower LB1 values and could flip the decision
+    assert orc.branch_rule([10, 10], [9, 30], [0, 1], orc.MINSUM, cap=10) == orc.BWD
+    assert orc.branch_rule([10, 10], [9, 30], [0, 1], orc.MINBRANCH, cap=10) == orc.FWD
+
+
 # ---------------------------------------------------------------- search ---
 
 @pytest.mark.parametrize("seed", range(1, 11))
