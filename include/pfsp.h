@@ -396,14 +396,18 @@ int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);
  * not allowed: a service that reserves its memory at start-up, an application
  * whose device memory belongs to another allocator, or a caller that cannot
  * afford the device synchronisation an allocation implies.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture begins.
+ *   - Every call looks up the array's device address on the current device
+ *     (a query that allocates nothing); the first call on a device also loads
+ *     the library's module there, and the array with it, so make that first
+ *     call before any stream capture begins.
  *   - Every call shares the array and overwrites what the previous call left;
  *     calls that overlap on the GPU (other threads or streams) race and must
  *     be serialised by the caller.
- *   - When the tables plus even a one-explorer-per-SM pool exceed 8 MiB (large
- *     n), the call fails with PFSP_ERR_UNSUPPORTED; fewer explorers per SM are
- *     used automatically when that makes the pool fit.
+ *   - The pool takes as many explorers per SM as fit in the array beside the
+ *     tables (the largest pool first, down to one explorer per SM); only when
+ *     the tables plus a one-explorer-per-SM pool exceed 8 MiB does the call
+ *     fail with PFSP_ERR_UNSUPPORTED.  On a 152-SM GPU every instance the
+ *     library accepts (n, m <= 64) fits: at n = 64 that pool takes 3.1 MB.
  *   - stats may be NULL; otherwise it receives the solve's counters.
  * Returns the same codes as pfsp_solve.
  */

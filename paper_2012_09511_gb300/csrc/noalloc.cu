@@ -31,24 +31,18 @@ namespace pfsp {
 constexpr size_t kNoAllocBytes = 8u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the array, looked up once per device.  In host code the
+// Device address of the array on the current device.  In host code the
 // symbol g_noalloc_scratch is only a host-side stand-in, not a device address.
-constexpr int kMaxDevices = 64;
-static void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
+// The address is looked up on every call (a cheap query that allocates
+// nothing): a cached address could go stale when the primary context is
+// reset and the module is loaded again.  The first call on a device loads the
+// library's module there, and the array with it.
 static int scratch_for_current_device(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_error(PFSP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(PFSP_ERR_UNSUPPORTED, "device index %d too large", dev);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(PFSP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(PFSP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+    *out = p;
     return PFSP_OK;
 }
 
@@ -143,23 +137,36 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
         offs[10] = take(64);
         return off;
     };
+    // explorers per SM are chosen directly: a cooperative launch may use
+    // fewer CTAs per SM than can be resident, so the pool can shrink to one
+    // explorer per SM (one single-warp CTA on each SM); the largest pool that
+    // fits is used (ties: more warps per CTA)
     size_t offs[11];
-    int warps = want, blocks = 0, K = 0;
-    size_t smem = 0, need = 0;
-    for (; warps >= 1; --warps) {
-        smem = (size_t)(a.warp_base + warps * per_warp) * 4;
-        int per_sm = solve_occupancy(a, warps, smem);
-        if (per_sm < 1) continue;
-        blocks = nsm * per_sm;
-        K = blocks * warps;
-        need = layout_bytes(K, offs);
-        if (need <= kNoAllocBytes) break;
+    int warps = 0, blocks = 0, K = 0;
+    size_t smem = 0;
+    for (int w = want; w >= 1; --w) {
+        const size_t sm_w = (size_t)(a.warp_base + w * per_warp) * 4;
+        const int per_sm = solve_occupancy(a, w, sm_w);
+        for (int c = per_sm; c >= 1; --c) {
+            const int Kc = nsm * c * w;
+            if (Kc <= K) break;
+            if (layout_bytes(Kc, offs) <= kNoAllocBytes) {
+                warps = w;
+                blocks = nsm * c;
+                K = Kc;
+                smem = sm_w;
+                break;
+            }
+        }
     }
-    if (warps < 1 || K < 1)
+    if (K < 1) {
+        const size_t need = layout_bytes(nsm, offs);
         return set_error(PFSP_ERR_UNSUPPORTED,
                          "instance %dx%d needs more than the %zu-byte static scratch of pfsp_solve_noalloc "
                          "(%zu bytes with one explorer per SM)",
                          n, m, kNoAllocBytes, need);
+    }
+    layout_bytes(K, offs);
     a.K = K;
     a.row_stride = n * n;
     a.inst_of = nullptr;

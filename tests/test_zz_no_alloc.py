@@ -63,3 +63,40 @@ def test_noalloc_matches_allocating_solve_twice(pf):
     assert got2["cmax"] == ref2["cmax"] == opt
     assert (got2["decomposed"], got2["bounded_children"]) == (ref2["decomposed"], ref2["bounded_children"])
     assert got2["decomposed"] > 1
+
+
+def test_noalloc_large_n_shrinks_pool(pf):
+    # at n = 50 the 12-warp-per-SM pool needs about 23 MB: the call must shrink
+    # the pool (down to one explorer per SM if needed) and still solve
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    p = inputs.make_instance(50, 5, 101)
+    got = pf.pfsp_solve_noalloc(p, bound=pf.PFSP_LB1, node_limit=20000)
+    assert got["outcome"] in (pf.PFSP_OPTIMAL, pf.PFSP_LIMIT_NODES)
+    assert sorted(got["perm"].tolist()) == list(range(50))
+    assert _makespan(p, got["perm"]) == got["cmax"]
+    # the pool holds at least one explorer per SM and fits the 8 MiB array
+    # (rows of n x n jobs and bounds, 5 bytes a cell, plus 209 bytes of state)
+    assert nsm <= got["explorers"]
+    assert got["explorers"] * (50 * 50 * 5 + 209) < 8 << 20
+    # the search starts from NEH, so its incumbent is never worse (oracle's NEH)
+    import oracle
+    assert got["cmax"] <= oracle.neh(p)[0]
+
+
+def test_noalloc_largest_n_and_rejections(pf):
+    # n = 64, the library's largest instance, is accepted
+    p = inputs.make_instance(64, 5, 7)
+    got = pf.pfsp_solve_noalloc(p, bound=pf.PFSP_LB1, node_limit=5000)
+    assert sorted(got["perm"].tolist()) == list(range(64))
+    assert _makespan(p, got["perm"]) == got["cmax"]
+    # LB2 tables that exceed shared memory (m = 64: 2,016 pairs) are refused
+    # with PFSP_ERR_UNSUPPORTED before any device work
+    with pytest.raises(pf.PfspError) as e:
+        pf.pfsp_solve_noalloc(inputs.make_instance(20, 64, 1), bound=pf.PFSP_LB2)
+    assert e.value.code == pf.PFSP_ERR_UNSUPPORTED
+    # a third solve after the refusal still agrees with the allocating one
+    p3 = inputs.make_instance(10, 5, 4)
+    ref = pf.pfsp_solve(pf.pfsp_load_instance(p3), bound=pf.PFSP_LB1)
+    got3 = pf.pfsp_solve_noalloc(p3, bound=pf.PFSP_LB1)
+    assert (got3["cmax"], got3["outcome"]) == (ref["cmax"], ref["outcome"])
