@@ -14,6 +14,15 @@ def rank_seed(base: int, rank: int) -> int:
     return base + rank
 
 
+def node_range(count: int, rank: int, world: int) -> tuple[int, int]:
+    """Half-open range [lo, hi) of the nodes of one batch that rank `rank` of
+    `world` bounds when a single batch is split across ranks: contiguous,
+    disjoint, covering [0, count), sizes differing by at most one."""
+    if world < 1 or not 0 <= rank < world or count < 0:
+        raise ValueError("need 0 <= rank < world and count >= 0")
+    return count * rank // world, count * (rank + 1) // world
+
+
 def whole_job_rate(local_seconds: float, local_units: float, device=None):
     """(units per second over all ranks, slowest rank's seconds, total units).
 
