@@ -566,35 +566,48 @@ struct Explorer {
     // stolen or initial interval), or the node at level X.lvl (a resumed
     // checkpoint, whose ancestors on the path were decomposed before it even
     // when they share its leftmost leaf).  Ancestors are not counted.
-    __device__ bool init_at_start() {
-        I = -1;
-        bool zero = true;
-        for (int h = 0; h < NW; ++h) {
-            int i = lane + 32 * h;
-            zero &= __all_sync(PFSP_FULL, i >= n || X.D[i] == 0);
-        }
-        const int lvl = X.lvl;
-        ub_seen = ub();
-        expand(zero && lvl < 0);  // the root; counted only by the explorer starting at 0
-        while (true) {
-            // I is the level whose row has just been built; follow the digit D[I]
-            const int d = X.D[I];
-            if (lane == 0) X.V[I] = d;
-            __syncwarp();
-            bool alive = rl[I * n + d] < ub_seen;
-            if (!alive) {
-                if (lane == 0) X.V[I] = d + 1;
-                __syncwarp();
-                return select();
-            }
-            bool rest_zero = true;
+    // One step of rebuilding the path to the start digits D after a new
+    // interval arrived (init_phase 0: the root is next; 1: the row of level I
+    // was just built).  Returns 1 when the next node on the path must be
+    // decomposed (*counted says whether it counts), 0 when the explorer stands
+    // on the first node of its interval (have_node), -1 when no node of the
+    // interval is left on this path and selection took over (have_node as
+    // select() returned).  The decompositions happen at the loop's single
+    // expand call site, so that the kernel carries one copy of it.
+    __device__ int init_step(int &init_phase, bool &counted, bool &have_node) {
+        if (init_phase == 0) {
+            I = -1;
+            bool zero = true;
             for (int h = 0; h < NW; ++h) {
                 int i = lane + 32 * h;
-                rest_zero &= __all_sync(PFSP_FULL, i >= n || i <= I || X.D[i] == 0);
+                zero &= __all_sync(PFSP_FULL, i >= n || X.D[i] == 0);
             }
-            if ((lvl < 0 ? rest_zero : I >= lvl) || I >= n - 2) return true;  // this node starts the interval
-            expand(false);
+            init_phase = 1;
+            counted = zero && X.lvl < 0;  // the root; counted only by the explorer starting at 0
+            return 1;
         }
+        // I is the level whose row has just been built; follow the digit D[I]
+        const int d = X.D[I];
+        if (lane == 0) X.V[I] = d;
+        __syncwarp();
+        if (!(rl[I * n + d] < ub_seen)) {
+            if (lane == 0) X.V[I] = d + 1;
+            __syncwarp();
+            have_node = select();
+            return -1;
+        }
+        bool rest_zero = true;
+        for (int h = 0; h < NW; ++h) {
+            int i = lane + 32 * h;
+            rest_zero &= __all_sync(PFSP_FULL, i >= n || i <= I || X.D[i] == 0);
+        }
+        const int lvl = X.lvl;
+        if ((lvl < 0 ? rest_zero : I >= lvl) || I >= n - 2) {  // this node starts the interval
+            have_node = true;
+            return 0;
+        }
+        counted = false;
+        return 1;
     }
 
     // Answer a steal request if one is waiting (victim side).  A request
@@ -609,20 +622,27 @@ struct Explorer {
     }
 
     // The stop flag, this explorer's mailbox and the incumbent, read together
-    // (one round trip); returns the stop flag, *req receives the request and
-    // ub_seen the incumbent that this iteration's selection and pruning use
-    // (never below the current one, which only decreases).
-    __device__ int poll(unsigned long long *req) {
-        int s = 0, u = 0;
-        unsigned long long r = 0;
+    // (one L2 round trip) one iteration ahead: prefetch_poll issues the loads
+    // (lane 0) and take_poll consumes them at the top of the next iteration,
+    // so that the round trip overlaps the decomposition in between.
+    // take_poll returns the stop flag, *req receives the request and ub_seen
+    // the incumbent that this iteration's selection and pruning use.  The
+    // values are at most one iteration old: a request or a stop is seen one
+    // iteration later, and the incumbent is never below the current one (it
+    // only decreases), so it prunes no more than the current one would.
+    int pf_stop = 0, pf_ub = INT_MAX;
+    unsigned long long pf_req = kNoRequest;
+    __device__ __forceinline__ void prefetch_poll() {
         if (lane == 0) {
-            s = ld_volatile(a.stop);
-            r = *(volatile unsigned long long *)(a.mailbox + me);
-            u = ld_volatile(a.ub);
+            pf_stop = ld_volatile(a.stop);
+            pf_req = *(volatile unsigned long long *)(a.mailbox + me);
+            pf_ub = ld_volatile(a.ub);
         }
-        *req = __shfl_sync(PFSP_FULL, r, 0);
-        ub_seen = __shfl_sync(PFSP_FULL, u, 0);
-        return __shfl_sync(PFSP_FULL, s, 0);
+    }
+    __device__ __forceinline__ int take_poll(unsigned long long *req) {
+        *req = __shfl_sync(PFSP_FULL, pf_req, 0);
+        ub_seen = __shfl_sync(PFSP_FULL, pf_ub, 0);
+        return __shfl_sync(PFSP_FULL, pf_stop, 0);
     }
 
     __device__ void service_req(unsigned long long req, bool active) {
@@ -852,12 +872,14 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
             }
         }
     }
-    int state = nonempty ? 1 : 0;  // 0 empty, 1 needs init, 2 active
+    int state = nonempty ? 1 : 0;  // 0 empty, 1 rebuilding the path to a new interval, 2 active
+    int init_phase = 0;
     bool have_node = false;
     unsigned iter = 0;
     // watchdog of idle explorers: the global decomposition count must keep
     // moving while some explorer holds work
     unsigned long long seen = ~0ull, seen_at = global_ns();
+    ex.prefetch_poll();
     while (true) {
         ++iter;
         if ((iter & (a.check_every - 1)) == 0) {
@@ -865,32 +887,47 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
             ex.publish_length(state == 2);
         }
         unsigned long long req;
-        if (ex.poll(&req)) break;
+        // a stop is taken between nodes of the interval, never in the middle
+        // of a path rebuild (at most n decompositions): a checkpoint then
+        // records the interval's start, and the root, counted when it starts
+        // an interval, is never decomposed twice
+        if (ex.take_poll(&req) && state != 1) break;
         ex.service_req(req, state == 2);
         ex.tick(kPhService);
+        bool counted = false, go = false;
         if (state == 1) {
-            have_node = ex.init_at_start();
-            state = 2;
-            ex.publish_length(true);
+            const int r = ex.init_step(init_phase, counted, have_node);
+            if (r == 1) go = true;
+            else {
+                state = 2;
+                ex.publish_length(true);
+            }
             ex.tick(kPhInit);
         }
-        if (state == 2) {
+        if (state == 2 && !go) {
             ex.st.iters += 1;
             if (!have_node) have_node = ex.select();
-            const bool go = have_node && ex.pos_before_end();
+            go = have_node && ex.pos_before_end();
+            counted = true;
             ex.tick(kPhSelect);
-            if (go) {
-                ex.expand(true);
+            if (!go) {
+                // interval exhausted
+                state = 0;
                 have_node = false;
-                continue;
+                ex.publish_length(false);
+                if (lane == 0) atomicSub(a.active, 1);
+                __syncwarp();
             }
-            // interval exhausted
-            state = 0;
-            have_node = false;
-            ex.publish_length(false);
-            if (lane == 0) atomicSub(a.active, 1);
-            __syncwarp();
         }
+        if (go) {
+            // the next iteration's poll is issued now: its L2 round trip
+            // overlaps the decomposition
+            ex.prefetch_poll();
+            ex.expand(counted);
+            have_node = false;
+            continue;
+        }
+        ex.prefetch_poll();
         // idle
         if (ex.active_count() == 0) break;
         {
@@ -914,9 +951,12 @@ __device__ void run_explorer(const SolveArgs &a, const SmemTables &T, const Warp
         if (r < 0) break;
         if (r == 1) {
             state = 1;
+            init_phase = 0;
+            ex.prefetch_poll();
             continue;
         }
         __nanosleep(500);
+        ex.prefetch_poll();
         ex.tick(kPhIdle);
     }
     ex.flush_limits();

@@ -257,6 +257,9 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     }
     int per_sm = solve_occupancy(a, warps, smem);
     if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "solve kernel cannot be resident (occupancy 0)");
+    // explorers per SM as asked: a cooperative launch may use fewer CTAs per
+    // SM than can be resident (default: every resident CTA)
+    if (opt->warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, opt->warps_per_sm / warps));
     const int blocks = nsm * per_sm;
     const int K = blocks * warps;
     a.K = K;
