@@ -229,8 +229,16 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
                                      32-pair slot at which every child of one direction has a pair
                                      term at least the incumbent (same exactness argument); pairs in
                                      the instance's order (pfsp_learn_pair_order puts the pairs most
-                                     likely to decide first).  The check after each slot costs
-                                     about as much as it saves on the pools measured so far. */
+                                     likely to decide first). */
+#define PFSP_EARLY_EXIT_CHILDREN 16 /* with PFSP_EARLY_EXIT: the sweep evaluates only the jobs one of
+                                     whose children has an LB1 below the solve's initial incumbent c;
+                                     a child left out keeps its LB1, a lower bound of its LB2 that is
+                                     at least c.  It is pruned as with the full sweep, and
+                                     min(bound, c) is unchanged, so under PFSP_MINMIN_CAPPED the
+                                     search tree and every counter are those of the full sweep.
+                                     Under PFSP_MINMIN and PFSP_MINBRANCH the sums of bounds that
+                                     break ties may differ, so trees may differ too; pruning and the
+                                     optimum stay exact (not in the paper) */
 
 typedef struct {
     int32_t init_ub;
@@ -381,6 +389,20 @@ int pfsp_set_lb2_pairs(pfsp_instance *inst, const int32_t *pairs, int count);
 /* The pairs LB2 uses, in sweep order, in the first entries of `order`
  * (m(m-1)/2 int32); entries past the pairs in use are -1. */
 int pfsp_get_pair_order(const pfsp_instance *inst, int32_t *order);
+
+/*
+ * Test hook (no counterpart in the paper): the number of polls a thief makes
+ * while it waits for a victim's answer in pfsp_solve and pfsp_solve_resumable
+ * (the steal handshake of Section 3.4; each poll also answers requests sent to
+ * the waiting thief and sleeps about 200 ns).  0 restores the default
+ * (2^21 polls, about half a second).  When a wait runs out, the kernel records
+ * the error, stops every explorer and the call returns PFSP_ERR_TIMEOUT with
+ * nothing written; the context stays usable.  A small limit makes that
+ * happen on purpose, so that callers can test their handling of the error.
+ * Process-wide; read when a solve starts.  Errors: PFSP_ERR_INVALID
+ * (polls < 0).
+ */
+int pfsp_set_steal_wait_limit(int polls);
 
 /* Counters of the last pfsp_bound_batch or pfsp_solve call on `inst`. */
 int pfsp_stats(const pfsp_instance *inst, pfsp_stats_t *out);

@@ -381,12 +381,36 @@ __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *
     }
 }
 
+template <int NW>
+__device__ __forceinline__ umask_t<NW> warp_or(umask_t<NW> x) {
+    if constexpr (NW == 1) {
+        return __reduce_or_sync(PFSP_FULL, (unsigned)x);
+    } else {
+        const unsigned lo = __reduce_or_sync(PFSP_FULL, (unsigned)(x & 0xffffffffull));
+        const unsigned hi = __reduce_or_sync(PFSP_FULL, (unsigned)(x >> 32));
+        return ((umask_t<NW>)hi << 32) | lo;
+    }
+}
+
 // LB2 sweep over the slots.  NC > 0: the children's accumulators are NC
 // registers per direction (u <= NC); NC = 0: they live in W.Acc.  RW: the
 // walks keep their records in registers (u <= kRegWalk).
-template <int NW, int MT, int NC, bool RW>
+//
+// SURV with live_only (the early exit per child, cap < INT_MAX): a job both
+// of whose children have an LB1 at or above cap is not evaluated (a
+// warp-uniform test per job); the other jobs are, in both directions.  Such
+// children keep their LB1, a lower bound of their LB2 at or above cap, so
+// they are pruned as with the full sweep and min(bound, cap) is unchanged:
+// capped MinMin decides every node as with full LB2.  The walks over the
+// unscheduled jobs are those of the full sweep (every job is in every
+// child's sequence).  With slot checks, a job whose children are both
+// decided after a slot (a pair term or its LB1 at or above cap) is not
+// evaluated in the later slots either.  Without live_only every child is
+// evaluated, as in the full sweep.
+template <int NW, int MT, int NC, bool RW, bool SURV = false>
 __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                         ChildBounds<NW> &out, int cap, bool slot_checks, const int *order) {
+                                         ChildBounds<NW> &out, int cap, bool slot_checks, const int *order,
+                                         bool live_only = false) {
     using mask_t = umask_t<NW>;
     constexpr bool REGACC = NC > 0;
     const int m = MT ? MT : m_rt;
@@ -397,8 +421,8 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     const int u = out.u;
     __syncwarp();
     const mask_t all = (u >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << u) - 1);
-    // children already decided by LB1 (only used with a cap); when every
-    // child of one direction is, the node is a dead end and no pair is needed
+    // children already decided (only with a cap); when every child of one
+    // direction is, the node is a dead end and no pair is needed
     mask_t done_f = 0, done_b = 0;
     if (cap != INT_MAX) {
 #pragma unroll
@@ -410,6 +434,15 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         }
         if ((done_f & all) == all || (done_b & all) == all) return 0;
     }
+    // jobs evaluated (warp-uniform): every job, or (SURV, live_only) those
+    // with a child still below cap
+    mask_t ev = all;
+    if constexpr (SURV) {
+        if (live_only) ev = all & ~(done_f & done_b);
+    }
+    // jobs evaluated in at least one slot: their accumulators are reduced
+    // at the end (a job dropped at a slot check holds terms >= cap)
+    const mask_t ev0 = ev;
     int accf[REGACC ? NC : 1], accb[REGACC ? NC : 1];
     if constexpr (REGACC) {
 #pragma unroll
@@ -426,28 +459,28 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     mask_t UposAll[SC];
     if constexpr (MT > 0) {
 #pragma unroll
-        for (int s = 0; s < SC; ++s) UposAll[s] = 0;
+        for (int q = 0; q < SC; ++q) UposAll[q] = 0;
         for (mask_t um = U; um; um &= um - 1) {
             const uint8_t *rj = T.rank + (size_t)lowest_bit<NW>(um) * SC * 32 + lane;
 #pragma unroll
-            for (int s = 0; s < SC; ++s) UposAll[s] |= mask_t(1) << rj[s * 32];
+            for (int q = 0; q < SC; ++q) UposAll[q] |= mask_t(1) << rj[q * 32];
         }
     }
     int swept = 0;
 #pragma unroll 1
     for (int si = 0; si < S; ++si) {
         swept = si + 1;
-        const int s = order ? order[si] : si;
-        const int klw = T.kl[s * 32 + lane];
+        const int sl = order ? order[si] : si;
+        const int klw = T.kl[sl * 32 + lane];
         const int k = klw & 0xff, l = klw >> 8;
         const int Bl = W.FRB[l].z;
-        const int2 *pt = T.ptab + (size_t)s * n * 32 + lane;
+        const int2 *pt = T.ptab + (size_t)sl * n * 32 + lane;
         mask_t Upos;
         if constexpr (MT > 0) {
             if (order) {
                 Upos = 0;
 #pragma unroll
-                for (int q = 0; q < SC; ++q) Upos = q == s ? UposAll[q] : Upos;
+                for (int q = 0; q < SC; ++q) Upos = q == sl ? UposAll[q] : Upos;
             } else {
                 Upos = UposAll[0];
 #pragma unroll
@@ -456,11 +489,11 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         } else {
             Upos = 0;
             for (mask_t um = U; um; um &= um - 1)
-                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + s) * 32 + lane];
+                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + sl) * 32 + lane];
         }
         if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane);
         else scan_slot<NW>(W, pt, E, Upos, u, lane);
-        // evaluation: the third pair term of every child of this parent
+        // evaluation: the third pair term of every evaluated child
         const int2 *gk = W.G + k;
         const int *bb = W.Bb + l;
         const int *cb = W.Cb + lane;
@@ -470,6 +503,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
                 if (c0 >= u4) break;
 #pragma unroll
                 for (int c = c0; c < c0 + 4; ++c) {
+                    if (SURV && !((ev >> c) & 1)) continue;  // warp-uniform
                     const int C = cb[c * 32];
                     const int2 g = gk[c * mp];
                     accf[c] = max(accf[c], g.x + C + Bl);
@@ -478,6 +512,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
             }
         } else {
             for (int c = 0; c < u; ++c) {
+                if (SURV && !((ev >> c) & 1)) continue;  // warp-uniform
                 const int C = cb[c * 32];
                 const int2 g = gk[c * mp];
                 int2 v = W.Acc[c * 32 + lane];
@@ -504,31 +539,24 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
                     mb |= (mask_t)(v.y >= cap) << c;
                 }
             }
-            if constexpr (NW == 1) {
-                mf = __reduce_or_sync(PFSP_FULL, (unsigned)mf);
-                mb = __reduce_or_sync(PFSP_FULL, (unsigned)mb);
-            } else {
-                unsigned fl = __reduce_or_sync(PFSP_FULL, (unsigned)(mf & 0xffffffffull));
-                unsigned fh = __reduce_or_sync(PFSP_FULL, (unsigned)(mf >> 32));
-                unsigned bl = __reduce_or_sync(PFSP_FULL, (unsigned)(mb & 0xffffffffull));
-                unsigned bh = __reduce_or_sync(PFSP_FULL, (unsigned)(mb >> 32));
-                mf = ((mask_t)fh << 32) | fl;
-                mb = ((mask_t)bh << 32) | bl;
-            }
-            done_f |= mf;
-            done_b |= mb;
+            done_f |= warp_or<NW>(mf);
+            done_b |= warp_or<NW>(mb);
             if ((done_f & all) == all || (done_b & all) == all) break;
+            if constexpr (SURV) {
+                if (live_only) ev &= ~(done_f & done_b);
+            }
         }
     }
     // ---- max over lanes (pairs) per child -------------------------------------
     if constexpr (REGACC) {
-        // register accumulators (u <= 32): one warp max-reduction per child
-        // and direction, kept by the child's lane
+        // register accumulators (u <= 32): one warp max-reduction per
+        // evaluated child and direction, kept by the child's lane
         static_assert(NW == 1, "register accumulators hold at most 32 children");
         int mf = kNegInf, mb = kNegInf;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             if (c >= u) break;
+            if (SURV && !((ev0 >> c) & 1)) continue;  // warp-uniform
             const int xf = __reduce_max_sync(PFSP_FULL, accf[c]);
             const int xb = __reduce_max_sync(PFSP_FULL, accb[c]);
             mf = lane == c ? xf : mf;
@@ -540,7 +568,8 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         }
         return swept;
     }
-    // shared accumulators: transpose through padded rows
+    // shared accumulators: transpose through padded rows (rows of children
+    // never evaluated stay at kNegInf)
     __syncwarp();
     int2 *X = W.X;  // [u][33], aliases the walk records and Cb
     for (int c = 0; c < u; ++c) X[c * 33 + lane] = W.Acc[c * 32 + lane];
@@ -578,14 +607,18 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
 // WALK = 0: walks through shared memory (any n).  Fixed per kernel, so that
 // a kernel carries the register demand of one path only.
 // Returns the number of 32-pair slots swept (fewer than S after an early exit).
-template <int NW, int MT, int WALK = 0>
+template <int NW, int MT, int WALK = 0, bool SURV = false>
 __device__ __forceinline__ int decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
-                                             ChildBounds<NW> &out, int cap, bool slot_checks, const int *order) {
+                                             ChildBounds<NW> &out, int cap, bool slot_checks, const int *order,
+                                             bool live_only = false) {
     if (out.u == 0 || (MT ? MT : m_rt) < 2) return 0;
     static_assert(WALK == 0 || NW == 1, "register walks need n <= 32");
     if constexpr (WALK == 1)
-        return lb2_sweep<NW, MT, kRegWalk, true>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order);
-    else return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order);
+        return lb2_sweep<NW, MT, kRegWalk, true, SURV>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order,
+                                                         live_only);
+    else
+        return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false, SURV>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order,
+                                                                  live_only);
 }
 
 // Both phases: the bounds of all 2u children of the node.

@@ -429,10 +429,11 @@ struct Explorer {
                     order = X.sorder;
                 }
             }
-            const int swept = EARLY ? decompose_lb2<NW, MT>(T, W, n, m, S, cb,
-                                                            (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
-                                                            (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order)
-                                    : decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
+            const int swept =
+                EARLY ? decompose_lb2<NW, MT, 0, true>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
+                                                       (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order,
+                                                       (a.learned & PFSP_EARLY_EXIT_CHILDREN) != 0)
+                      : decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
             if (counted) st.slots += swept;
         }
         tick(counted ? kPhLB2 : kPhInit);
@@ -794,7 +795,8 @@ struct Explorer {
         myseq = __shfl_sync(PFSP_FULL, myseq, 0);
         if (!posted) return 0;
         int r = 0;
-        for (int it = 0; it < kWaitLimit; ++it) {
+        const int wait_limit = a.wait_limit > 0 ? a.wait_limit : kWaitLimit;
+        for (int it = 0; it < wait_limit; ++it) {
             if (lane == 0) {
                 unsigned long long v = *(volatile unsigned long long *)(a.response + me);
                 r = (v >> 2) == myseq ? (int)(v & 3ull) : 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cstring>
@@ -73,7 +74,17 @@ struct DeviceSolveState {
 
 using namespace pfsp;
 
+// Polls of a thief's answer wait in pfsp_solve (0: the default kWaitLimit);
+// set only through the test hook pfsp_set_steal_wait_limit.
+static std::atomic<int> g_steal_wait_limit{0};
+
 extern "C" {
+
+int pfsp_set_steal_wait_limit(int polls) {
+    if (polls < 0) return set_error(PFSP_ERR_INVALID, "polls must be >= 0");
+    g_steal_wait_limit.store(polls);
+    return PFSP_OK;
+}
 
 void pfsp_default_options(pfsp_options *o) {
     if (!o) return;
@@ -121,10 +132,13 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (opt->node_limit < 0 || opt->time_limit_s < 0) return set_error(PFSP_ERR_INVALID, "negative limit");
     if (opt->bound == PFSP_LB2 && !inst->lb2_ok)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
-    if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT | PFSP_EARLY_EXIT_SLOTS))
+    if (opt->learned & ~(PFSP_LEARN_CHILD_ORDER | PFSP_LEARN_PAIR_ORDER | PFSP_EARLY_EXIT | PFSP_EARLY_EXIT_SLOTS |
+                         PFSP_EARLY_EXIT_CHILDREN))
         return set_error(PFSP_ERR_INVALID, "unknown bits in learned");
     if ((opt->learned & PFSP_EARLY_EXIT_SLOTS) && !(opt->learned & PFSP_EARLY_EXIT))
         return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT_SLOTS needs PFSP_EARLY_EXIT");
+    if ((opt->learned & PFSP_EARLY_EXIT_CHILDREN) && !(opt->learned & PFSP_EARLY_EXIT))
+        return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT_CHILDREN needs PFSP_EARLY_EXIT");
     if ((opt->learned & PFSP_EARLY_EXIT) && opt->branching == PFSP_MINSUM)
         return set_error(PFSP_ERR_INVALID, "PFSP_EARLY_EXIT keeps the tree of MinMin and MinBranch only");
     if (opt->heuristic_threads < 0 || opt->heuristic_threads > 256)
@@ -200,6 +214,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.minht = opt->lb1_minht;
     a.diag = (opt->phase_timers || tr) ? 1 : 0;
     a.cap = resuming ? rh.cap : ub0;
+    a.wait_limit = g_steal_wait_limit.load();
     a.warp_words = warp_words(n, m, n > 32, opt->bound == PFSP_LB2 && m >= 2);
     // the network's inference image: every output column when it orders the
     // LB2 slots, else only the descend-first column (one 16-column tile)

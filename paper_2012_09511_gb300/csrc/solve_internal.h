@@ -129,6 +129,7 @@ struct SolveArgs {
     int minht;            // 1: LB1 with the heads and tails refinement (its own kernel)
     int diag;             // 1: phase timers or a trace requested (the kernel that carries them)
     int rows_smem;        // 1: each explorer's rows live in shared memory after its explorer state
+    int wait_limit;       // polls of a thief's answer wait (0: kWaitLimit; lowered only by a test hook)
 };
 
 // Words of one explorer's rows in shared memory: bounds [n][n] int32, then

@@ -66,6 +66,7 @@ PFSP_LEARN_CHILD_ORDER = 1
 PFSP_LEARN_PAIR_ORDER = 2
 PFSP_EARLY_EXIT = 4
 PFSP_EARLY_EXIT_SLOTS = 8
+PFSP_EARLY_EXIT_CHILDREN = 16
 
 
 class pfsp_options(ctypes.Structure):
@@ -152,6 +153,8 @@ _lib.pfsp_free_checkpoint.restype = None
 _lib.pfsp_free_checkpoint.argtypes = [_vp]
 _lib.pfsp_set_pair_order.restype = ctypes.c_int
 _lib.pfsp_set_pair_order.argtypes = [_vp, _vp]
+_lib.pfsp_set_steal_wait_limit.restype = ctypes.c_int
+_lib.pfsp_set_steal_wait_limit.argtypes = [ctypes.c_int]
 _lib.pfsp_learn_lb2_pairs.restype = ctypes.c_int
 _lib.pfsp_learn_lb2_pairs.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.pfsp_set_lb2_pairs.restype = ctypes.c_int
@@ -484,6 +487,11 @@ def pfsp_mlp_rows(inst: Instance, mlp: Mlp, perm, d1, d2):
     _check(_lib.pfsp_mlp_rows(inst.handle, mlp.handle, k, _ptr(perm), _ptr(d1), _ptr(d2), _ptr(X), _ptr(T),
                               _ptr(M)))
     return X, T, M
+
+
+def pfsp_set_steal_wait_limit(polls: int = 0) -> None:
+    """Test hook: polls of a thief's answer wait in pfsp_solve (0 = the default)."""
+    _check(_lib.pfsp_set_steal_wait_limit(int(polls)))
 
 
 def pfsp_set_pair_order(inst: Instance, order=None) -> None:

@@ -140,6 +140,53 @@ def test_early_exit_keeps_the_tree(pf, n, m, seed):
         assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
 
 
+@pytest.mark.parametrize("n,m,seed", [(12, 10, 17), (11, 20, 3), (13, 5, 8), (12, 8, 6), (33, 10, 4), (34, 5, 1)])
+def test_early_exit_children_keeps_the_capped_tree(pf, n, m, seed):
+    # PFSP_EARLY_EXIT_CHILDREN leaves out the jobs both of whose children
+    # have an LB1 at or above the initial incumbent c; those children keep a
+    # bound >= c, so min(bound, c) and the pruning are those of the full
+    # sweep: capped MinMin builds the oracle's tree, whatever the pair order
+    # (n = 34 runs the 64-bit-mask kernels, accumulators in shared memory)
+    p = inputs.make_instance(n, m, seed)
+    inst = pf.pfsp_load_instance(p)
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, branching=orc.MINMIN_CAPPED)
+    base = pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_CHILDREN
+    rng = np.random.default_rng(seed)
+    for order in (None, rng.permutation(m * (m - 1) // 2)):
+        pf.pfsp_set_pair_order(inst, order)
+        for flags in (base, base | pf.PFSP_EARLY_EXIT_SLOTS):
+            r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=flags,
+                              branching=pf.PFSP_MINMIN_CAPPED)
+            assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+            got = (r["decomposed"], r["bounded_children"], r["pruned"])
+            assert got == (want["decomposed"], want["bounded"], want["pruned"]), (order, flags)
+        # under the other rules the tree may differ (tie-breaking sums), the
+        # proof and the optimum may not
+        for rule in (pf.PFSP_MINMIN, pf.PFSP_MINBRANCH):
+            r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, learned=base | pf.PFSP_EARLY_EXIT_SLOTS,
+                              branching=rule)
+            assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+            f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, learned=base | pf.PFSP_EARLY_EXIT_SLOTS, branching=rule)
+            assert f["outcome"] == pf.PFSP_OPTIMAL and f["cmax"] == opt
+            assert orc.makespan(p, f["perm"]) == opt
+    pf.pfsp_set_pair_order(inst, None)
+
+
+def test_early_exit_children_capped_proof_counts_20x10(pf):
+    for g in json_golden():
+        if g["proof_capped_decomposed"] > 300000:
+            continue
+        inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, g["seed"]))
+        flags = pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_CHILDREN | pf.PFSP_EARLY_EXIT_SLOTS
+        r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"], learned=flags,
+                          branching=pf.PFSP_MINMIN_CAPPED)
+        assert r["decomposed"] == g["proof_capped_decomposed"], g["seed"]
+        full = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"], branching=pf.PFSP_MINMIN_CAPPED)
+        assert full["decomposed"] == r["decomposed"]
+        assert r["lb2_slots"] <= full["lb2_slots"]
+
+
 def test_early_exit_proof_counts_20x10(pf):
     import json
     import os
@@ -216,6 +263,11 @@ def test_learned_options_are_validated(pf):
     inst = pf.pfsp_load_instance(p)
     with pytest.raises(pf.PfspError):  # slot checks without the early exit
         pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT_SLOTS)
+    with pytest.raises(pf.PfspError):  # live-children sweep without the early exit
+        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT_CHILDREN)
+    with pytest.raises(pf.PfspError):  # refused with MinSum
+        pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_EARLY_EXIT | pf.PFSP_EARLY_EXIT_CHILDREN,
+                      branching=pf.PFSP_MINSUM)
     with pytest.raises(pf.PfspError):  # no network
         pf.pfsp_solve(inst, bound=2, learned=pf.PFSP_LEARN_CHILD_ORDER)
     other = pf.pfsp_mlp_create(10, seed=1)
@@ -270,12 +322,37 @@ def test_learned_lb2_pair_subset_keeps_the_solve_exact(pf):
     assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (want["decomposed"], want["bounded"],
                                                                       want["pruned"])
     assert r["lb2_slots"] <= r["decomposed"]
-    # the learned solver's own options (the subset in the plain kernel)
-    from paper_2012_09511_gb300 import learned
-    r0 = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, **learned.learned_options(pf))
+    # the subset in the plain kernel: one 32-pair slot per decomposition
+    r0 = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt)
     assert (r0["decomposed"], r0["bounded_children"], r0["pruned"]) == (want["decomposed"], want["bounded"],
                                                                          want["pruned"])
-    assert r0["lb2_slots"] == r0["decomposed"]  # one 32-pair slot per decomposition
+    assert r0["lb2_slots"] == r0["decomposed"]
     f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2)
     assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt
     assert len(pf.pfsp_learn_lb2_pairs(inst, mlp, keep=100)) == P  # keep >= P: every pair
+
+
+def test_learned_solver_workflow_keeps_the_capped_tree(pf):
+    # the learned solver of the comparison: the network orders the pairs
+    # (scores on the root's children), the sweep exits early per child; under
+    # capped MinMin its tree is the oracle's, under MinMin the optimum is
+    from paper_2012_09511_gb300 import learned
+    n, m = 13, 10
+    p = inputs.make_instance(n, m, 45)
+    inst = pf.pfsp_load_instance(p)
+    mlp = pf.pfsp_mlp_create(m, seed=4)
+    order = learned.order_pairs(pf, inst, mlp)
+    assert sorted(order.tolist()) == list(range(m * (m - 1) // 2))
+    assert (pf.pfsp_get_pair_order(inst) == order).all()
+    perm, d1, d2 = learned.root_children(n)
+    score = pf.pfsp_mlp_pair_scores(inst, mlp, perm, d1, d2)
+    assert (np.diff(score[order]) <= 0).all()
+    opt = orc.bb_solve(p, bound=orc.LB2)["cmax"]
+    want = orc.bb_solve(p, bound=orc.LB2, init_ub=opt, branching=orc.MINMIN_CAPPED)
+    for slots in (False, True):
+        r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=opt, branching=pf.PFSP_MINMIN_CAPPED,
+                          **learned.learned_options(pf, slot_checks=slots))
+        assert (r["decomposed"], r["bounded_children"], r["pruned"]) == (want["decomposed"], want["bounded"],
+                                                                         want["pruned"])
+        f = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, **learned.learned_options(pf, slot_checks=slots))
+        assert f["cmax"] == opt and orc.makespan(p, f["perm"]) == opt

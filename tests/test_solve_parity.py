@@ -255,3 +255,25 @@ def test_n20_m10_lb2_optimum_and_proof_counts(pf, seed):
     f = pf.pfsp_solve(inst, bound=2)
     assert f["outcome"] == pf.PFSP_OPTIMAL and f["cmax"] == g["optimum"]
     _check_perm(p, f)
+
+
+def test_steal_wait_expiry_returns_timeout(pf):
+    # a thief's bounded wait for a victim's answer (the steal handshake of
+    # Section 3.4) made to run out on purpose: with one poll allowed, the first
+    # request that the victim does not answer at once ends the solve with
+    # PFSP_ERR_TIMEOUT and nothing written; nothing faults or hangs, and the
+    # next solve, with the default limit, runs normally on the same context
+    path = os.path.join(os.path.dirname(__file__), "golden", "solve_20x10_lb2.json")
+    g = {r["seed"]: r for r in json.load(open(path))["results"]}[7]
+    inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, 7))
+    try:
+        pf.pfsp_set_steal_wait_limit(1)
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"])
+        assert e.value.code == pf.PFSP_ERR_TIMEOUT
+    finally:
+        pf.pfsp_set_steal_wait_limit(0)
+    r = pf.pfsp_solve(inst, bound=pf.PFSP_LB2, init_ub=g["optimum"])
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER and r["decomposed"] == g["proof_decomposed"]
+    with pytest.raises(pf.PfspError):
+        pf.pfsp_set_steal_wait_limit(-1)
