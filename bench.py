@@ -41,6 +41,7 @@ WORKLOAD = "pfsp-bound-20x20-4M"
 METRIC = "bounded children/s (LB1 + full-pair LB2)"
 UNIT = "children/s"
 L2_FLUSH_BYTES = 256 << 20
+LEARNED_SLOT_CHECKS = False  # learned solver: check after every 32-pair slot
 REDUCE_UB = 1500  # exclusive incumbent of the reduce mode's survivor masks (near the batch's median LB2)
 # INT32 ALU lanes per SM per clock on sm_103a (add, min/max, logic; measured
 # at 127.9 IMNMX thread-instructions per SM per clock)
@@ -54,14 +55,26 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nodes", type=int, default=N_NODES)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="timed end-to-end steps (default: --steps; 0 skips the end-to-end legs)")
     ap.add_argument("--cpu-sample", type=int, default=1000000, help="nodes in the oracle's timed sample")
+    ap.add_argument("--ref-sample", type=int, default=400000,
+                    help="nodes the reference arm (the oracle) bounds per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-proof leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-ordering comparison")
     ap.add_argument("--solve-seeds", default="1,2,3,4,5,6,7,8,9,10",
                     help="seeds of the time-to-proof leg (comma separated)")
     return ap.parse_args()
+
+
+def workload_config(nodes, ws):
+    """The workload both arms name in their JSON line (identical dicts)."""
+    return {"workload": WORKLOAD, "n": N_JOBS, "m": M_MACH, "nodes_per_gpu": nodes, "seed": SEED,
+            "depths": "d1, d2 uniform in 0..%d" % DMAX, "bounds": "LB1+LB2 (190 pairs)",
+            "l2": "GPU arm: flushed before every step (256 MiB write, outside the timed events); "
+                  "oracle arm: host only",
+            "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU"}
 
 
 def dist_env():
@@ -394,12 +407,15 @@ def batch_leg(pfsp):
 
 
 def learned_leg(pfsp):
-    """Learned solver vs the plain full-pair LB2 solver on n = 50, m = 5 and
-    n = 30, m = 10 (5 seeds each), from NEH to the proven optimum and proving a
-    known optimum (fixed tree), plus proofs of 16 x 20 and 18 x 20 instances.
-    The m-machine networks are trained on the GPU on the solver's own traces of
-    other instances with the same m; identical optima required; wall times
-    (pair ranking included) and decomposed nodes reported."""
+    """Learned solver vs the plain full-pair LB2 solver, proving known optima:
+    n = 30, m = 10 (the ten seeds of learned.SEEDS_30X10, whose plain proofs
+    take at least 50 ms each), n = 50, m = 5 (seeds 101-110; these proofs take
+    well under a millisecond) and n = 18, m = 20 (seeds 101-103, where the
+    pairs fill six 32-pair slots).  Both under capped MinMin (identical trees,
+    counts checked equal) and under the paper's MinMin (node inflation
+    reported); kernel and wall times are the median of three solves.  The
+    m-machine networks are trained on the GPU on the solver's own traces of
+    other instances with the same m."""
     from paper_2012_09511_gb300 import inputs, learned
     mlps, training = {}, {}
     for m in (5, 10, 20):
@@ -409,22 +425,20 @@ def learned_leg(pfsp):
                                               nodes_per_instance=3000 if m == 20 else 4000)
         info["seconds"] = time.perf_counter() - t
         training["m=%d" % m] = info
-    out = {"training": training}
-    for shapes, proof in ((((50, 5), (30, 10)), False), (((50, 5), (30, 10), (16, 20), (18, 20)), True)):
-        rep = learned.compare(pfsp, shapes=shapes, seeds=range(1, 6), time_limit_s=20.0,
-                              depth_fracs=(4,), proof=proof, mlps=mlps)
-        for shape, v in rep.items():
-            key = "%s_%s" % (shape, "proof" if proof else "find")
-            out[key] = {k: v[k] for k in ("solved_by_both", "wall_plain_s", "wall_learned_s", "speedup_wall",
-                                          "kernel_plain_s", "kernel_learned_s", "speedup_kernel",
-                                          "node_ratio_learned_over_plain", "ranking_wall_s",
-                                          "mlp_share_of_learned_wall", "ablation_wall_s")}
-            out[key]["same_optimum_every_seed"] = all(r["same_optimum"] for r in v["instances"])
-            out[key]["per_seed"] = [{"seed": r["seed"], **{k: {kk: r[k][kk] for kk in ("wall_seconds", "decomposed",
-                                                                                        "cmax")}
-                                                            for k in ("plain", "learned")}}
-                                    for r in v["instances"]]
-    return out
+    cases = {"30x10": (30, 10, learned.SEEDS_30X10), "50x5": (50, 5, range(101, 111)),
+             "18x20": (18, 20, range(101, 104))}
+    rules = (("minmin_capped", pfsp.PFSP_MINMIN_CAPPED), ("minmin", pfsp.PFSP_MINMIN))
+    rep = learned.compare_proofs(pfsp, cases, mlps, rules=rules, reps=3, slot_checks=LEARNED_SLOT_CHECKS)
+    for name, r in rep.items():
+        c = r.get("minmin_capped")
+        if c:
+            c["counts_equal_plain"] = c["decomposed"]["learned"] == c["decomposed"]["plain"]
+    return {"training": training,
+            "learned_solver": "network pair order (root's children) + early exit per child%s" % (
+                " + slot checks" if LEARNED_SLOT_CHECKS else ""),
+            "ablations": "early_exit_index_order: the same early exit, pairs in index order; "
+                         "pair_subset: LB2 over the network's top half of the 32-pair slots (weaker bound)",
+            "proofs": rep}
 
 
 def run_reference(args):
@@ -433,21 +447,21 @@ def run_reference(args):
         return
     from paper_2012_09511_gb300 import inputs
     p = inputs.make_instance(N_JOBS, M_MACH, SEED)
-    sample = min(args.cpu_sample, args.nodes)
+    sample = min(args.ref_sample, args.nodes)
     perm, d1, d2 = inputs.random_nodes(N_JOBS, sample, seed=SEED)
     for _ in range(args.warmup):
         cpu_baseline(p, perm, d1, d2, min(2000, sample))
-    times, children = [], 0
+    times = []
     for _ in range(args.steps):
         r = cpu_baseline(p, perm, d1, d2, sample, total=args.nodes)
         times.append(r)
-    value = statistics.median([t["value"] for t in times])
-    step_ms = statistics.median([t["seconds"] for t in times]) * 1e3
+    # the rate over all steps: children bounded / seconds, summed
+    value = sum(t["value"] * t["seconds"] for t in times) / max(sum(t["seconds"] for t in times), 1e-9)
+    step_ms = statistics.mean([t["seconds"] for t in times]) * 1e3
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": N_JOBS, "m": M_MACH, "nodes": args.nodes,
-                      "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)"},
+           "config": workload_config(args.nodes, 1),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": times[0]["cores"], "kind": "oracle",
                             "sample": times[0]["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -523,25 +537,32 @@ def run_native(args):
     h1 = torch.empty((N, 2, n), dtype=torch.int32).pin_memory()
     h2 = torch.empty((N, 2, n), dtype=torch.int32).pin_memory()
     args_np = (hp.numpy(), hd1.numpy(), hd2.numpy())
-    if args.e2e_steps > 0:
-        pfsp.pfsp_bound_batch(inst, 3, *args_np, lb1_out=h1.numpy(), lb2_out=h2.numpy())  # warm (scratch)
-    if ws > 1:
-        dist.barrier()
+    e2e_steps = args.steps if args.e2e_steps < 0 else args.e2e_steps
+
     def timed_steps(call):
-        # per-step wall times; the rate is taken at the median step, which a
-        # transient slowdown of the shared host (copies compete with other
-        # jobs' traffic) moves less than the mean
+        # W untimed calls (the first allocates the library's staging scratch),
+        # then the same number of timed steps as the device leg; per-step wall
+        # times are kept, the rate is taken over their sum (the mean step)
+        if e2e_steps > 0:
+            for _ in range(max(args.warmup, 1)):
+                call()
+        if ws > 1:
+            dist.barrier()
         ts = []
-        for _ in range(args.e2e_steps):
+        for _ in range(e2e_steps):
             t0 = time.perf_counter()
             call()
             ts.append(time.perf_counter() - t0)
         return ts
 
+    def rates(ts):
+        mean, _, _ = shard.whole_job_rate(max(sum(ts), 1e-9), children * len(ts), device=dev)
+        med, _, _ = shard.whole_job_rate(max(statistics.median(ts), 1e-9) if ts else 1e-9, children if ts else 0,
+                                         device=dev)
+        return mean, med
+
     e2e_ts = timed_steps(lambda: pfsp.pfsp_bound_batch(inst, 3, *args_np, lb1_out=h1.numpy(), lb2_out=h2.numpy()))
-    e2e_s = max(statistics.median(e2e_ts), 1e-9) if e2e_ts else 1e-9
-    e2e_value, _, _ = shard.whole_job_rate(e2e_s, children if e2e_ts else 0, device=dev)
-    e2e_mean, _, _ = shard.whole_job_rate(max(sum(e2e_ts), 1e-9), children * max(len(e2e_ts), 1), device=dev)
+    e2e_value, e2e_median = rates(e2e_ts)
 
     # reduce mode: the same nodes and bounds (LB2, the solver's), one
     # 48-byte summary per parent instead of the bound arrays
@@ -573,13 +594,8 @@ def run_native(args):
     hs = np.empty(N, dtype=pfsp.SUMMARY_DTYPE)
     hs_pin = torch.from_numpy(hs.view(np.uint8)).pin_memory()
     hs = hs_pin.numpy().view(pfsp.SUMMARY_DTYPE)
-    if args.e2e_steps > 0:
-        pfsp.pfsp_bound_reduce(inst, pfsp.PFSP_LB2, *args_np, ub_reduce, out=hs)  # warm
-    if ws > 1:
-        dist.barrier()
     r_ts = timed_steps(lambda: pfsp.pfsp_bound_reduce(inst, pfsp.PFSP_LB2, *args_np, ub_reduce, out=hs))
-    r_e2e_s = max(statistics.median(r_ts), 1e-9) if r_ts else 1e-9
-    r_e2e_value, _, _ = shard.whole_job_rate(r_e2e_s, children if r_ts else 0, device=dev)
+    r_e2e_value, r_e2e_median = rates(r_ts)
 
     if rank != 0:
         if ws > 1:
@@ -597,11 +613,8 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": slowest_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "nodes_per_gpu": N, "seed": SEED,
-                   "depths": "d1, d2 uniform in 0..10", "bounds": "LB1+LB2 (190 pairs)",
-                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
-                   "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU",
-                   "host_cpus": host_cpus},
+        "config": workload_config(N, ws),
+        "host_cpus": host_cpus,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": "%d SMs x %d INT32 lanes/clk x %.0f MHz (max SM clock)" % (
@@ -613,13 +626,15 @@ def run_native(args):
                                                              "lsu_pipe_pct") if k in ncu} if ncu else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
                 "d2h_bytes_per_step": int(2 * N * 2 * n * 4),
-                "statistic": "median of %d steps through pfsp_bound_batch" % len(e2e_ts), "mean_value": e2e_mean,
+                "statistic": "mean of %d steps through pfsp_bound_batch (after %d untimed)" % (
+                    len(e2e_ts), max(args.warmup, 1)), "median_value": e2e_median,
                 "step_ms": [round(t * 1e3, 2) for t in e2e_ts]},
         "reduce": {"value": r_value, "unit": UNIT, "ms_per_step": r_ms / args.steps,
                    "mode": "LB2 summarised per parent and direction (least bound, count, sum, survivors "
                            "below %d), 48 bytes per parent" % REDUCE_UB,
                    "e2e": {"value": r_e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
-                           "d2h_bytes_per_step": int(N * 48)}},
+                           "d2h_bytes_per_step": int(N * 48), "median_value": r_e2e_median,
+                           "step_ms": [round(t * 1e3, 2) for t in r_ts]}},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }

@@ -3,21 +3,31 @@
 Orchestration only; every step runs in the library's kernels:
 pfsp_solve_trace records nodes the solver decomposes, pfsp_mlp_rows builds
 the training rows on the GPU, pfsp_mlp_train trains the network on the GPU,
-pfsp_learn_lb2_pairs scores the machine pairs with the network, and
+pfsp_learn_pair_order ranks the machine pairs with the network, and
 pfsp_solve runs the plain and the learned solvers.
 
-The learned solver restricts LB2 to the machine pairs that the network
-predicts most often give a child's LB2 (scored on the root's children; half
-of the 32-pair slots: one of two at m = 10, three of six at m = 20).  A
-subset LB2 is still a lower bound, so the search stays exact and its optimum
-is always the plain solver's; the comparison reports the time to the proven
-optimum (wall time, ranking included) and the decomposed-node counts of both.
-The early exit of the LB2 sweep (a node one of whose directions has every
-child at or above the incumbent needs no sweep) and the network's row order
-are reported as ablations.
+The learned solver (not in the paper) orders the LB2 sweep and exits it early:
+  * order: the network scores every machine pair on the root's 2n children
+    (its mean probability that the pair gives a child's LB2) and the instance's
+    pairs are swept best first (pfsp_learn_pair_order);
+  * early exit: a node one of whose directions has every child at or above
+    the incumbent needs no sweep (reading R14); otherwise only the jobs with a
+    child still below it are evaluated (PFSP_EARLY_EXIT_CHILDREN), and, with
+    slot checks, the sweep stops after the 32-pair slot at which one direction
+    is decided.
+Every child that can survive gets its exact full-pair LB2, so pruning stays
+exact and the plain full-pair LB2 solver is the judge: under capped MinMin the
+two build the same tree (node counts equal, checked), under the paper's
+MinMin the tie-breaking sums of decided children may differ and the node
+inflation is reported.  The comparison proves a known optimum (incumbent at
+the optimum, a fixed tree) and reports the median of repeated solves.
+Ablations: the same early exit with the pairs in index order (what the
+network's order adds) and LB2 restricted to the network's top pairs (a weaker
+bound, the learned pair subset).
 """
 from __future__ import annotations
 
+import statistics
 import time
 
 import numpy as np
@@ -25,6 +35,12 @@ import numpy as np
 from . import inputs
 
 LEARNED_ALL = 1 | 2 | 4  # child order | pair order | early exit
+EARLY_EXIT, EARLY_EXIT_SLOTS, EARLY_EXIT_CHILDREN = 4, 8, 16
+
+# The 30 x 10 instances of the comparison: seeds 101 upwards, the first ten
+# whose proof of the optimum takes the plain solver at least 50 ms of kernel
+# time on one GB300 (most 30 x 10 proofs take a few milliseconds).
+SEEDS_30X10 = (135, 232, 370, 415, 421, 457, 564, 583, 642, 672)
 
 
 def collect_rows(pfsp, instances, mlp, nodes_per_instance=4000, stride=2, bound=2, time_limit_s=5.0):
@@ -52,19 +68,49 @@ def train_network(pfsp, m, train_instances, seed=0, epochs=8, batch=4096, lr=2e-
     return mlp, {"rows": int(len(X)), "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
 
 
-def _run(pfsp, inst, **kw):
-    t = time.perf_counter()
-    r = pfsp.pfsp_solve(inst, **kw)
-    return r, time.perf_counter() - t
+def root_children(n):
+    """The root's 2n children in the layout of pfsp_bound_batch: job j first
+    (forward, d1 = 1) and job j last (backward, d2 = 1)."""
+    perm = np.empty((2 * n, n), dtype=np.uint8)
+    d1 = np.zeros(2 * n, dtype=np.uint8)
+    d2 = np.zeros(2 * n, dtype=np.uint8)
+    for j in range(n):
+        rest = [q for q in range(n) if q != j]
+        perm[j] = [j] + rest
+        d1[j] = 1
+        perm[n + j] = rest + [j]
+        d2[n + j] = 1
+    return perm, d1, d2
+
+
+def order_pairs(pfsp, inst, mlp):
+    """Sweep the instance's pairs in the network's order (mean pair probability
+    over the root's children, best first); returns the order, or None when
+    every pair fits one 32-pair slot (m <= 8): the sweep then evaluates all of
+    them at once and no order can change its work, so the network is not run."""
+    if inst.m * (inst.m - 1) // 2 <= 32:
+        pfsp.pfsp_set_pair_order(inst, None)
+        return None
+    perm, d1, d2 = root_children(inst.n)
+    return pfsp.pfsp_learn_pair_order(inst, mlp, perm, d1, d2)
+
+
+def learned_options(pfsp, slot_checks=False):
+    """pfsp_solve options of the learned solver (the pair order is set on the
+    instance by order_pairs): the early exit per child, and optionally the
+    check after every 32-pair slot."""
+    flags = pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_EARLY_EXIT_CHILDREN
+    if slot_checks:
+        flags |= pfsp.PFSP_EARLY_EXIT_SLOTS
+    return {"learned": flags}
 
 
 def learned_pairs(pfsp, inst, mlp, keep=None):
     """LB2 of `inst` restricted to the `keep` machine pairs the network scores
-    highest on the root's children (pfsp_learn_lb2_pairs).  By default half of
-    the 32-pair slots, rounded up, are kept: 32 of 45 pairs at m = 10 (one slot
-    of two), 96 of 190 at m = 20 (three of six); measured on proofs, fewer
-    pairs weaken the bound more than they save.  Nothing changes when the
-    instance has at most `keep` pairs.  Returns the pairs kept, or None."""
+    highest on the root's children (pfsp_learn_lb2_pairs; the learned pair
+    subset, a weaker bound).  By default half of the 32-pair slots, rounded up.
+    Nothing changes when the instance has at most `keep` pairs.  Returns the
+    pairs kept, or None."""
     P = inst.m * (inst.m - 1) // 2
     if keep is None:
         keep = 32 * (((P + 31) // 32 + 1) // 2)
@@ -74,112 +120,84 @@ def learned_pairs(pfsp, inst, mlp, keep=None):
     return pfsp.pfsp_learn_lb2_pairs(inst, mlp, keep=keep)
 
 
-def learned_options(pfsp):
-    """pfsp_solve options of the learned solver (the LB2 pair subset is set on
-    the instance by learned_pairs): none beyond the subset.  The early exit of
-    the sweep runs in a kernel of its own whose checks cost instruction fetch;
-    with the subset it is 1.0x at m = 10 and 0.9x at m = 20, so it stays an
-    ablation."""
-    return {}
+def _median_solve(pfsp, inst, reps, **kw):
+    """Median kernel and wall seconds of `reps` solves (after one untimed)."""
+    pfsp.pfsp_solve(inst, **kw)
+    ks, ws, r = [], [], None
+    for _ in range(reps):
+        t = time.perf_counter()
+        r = pfsp.pfsp_solve(inst, **kw)
+        ws.append(time.perf_counter() - t)
+        ks.append(r["kernel_seconds"])
+    return r, statistics.median(ks), statistics.median(ws)
 
 
-def solve_variants(pfsp, p, mlp, time_limit_s=30.0, depths=None, init_ub=None):
-    """Plain and learned solves of one instance (LB2), from its NEH schedule or,
-    with init_ub, in proof mode.
-
-    plain: the full-pair LB2 solver, pairs in index order.
-    learned: LB2 over the network's top pairs (learned_pairs: half of the
-    32-pair slots); its wall time includes the ranking.
-    Ablations: early exit alone, and in finding mode the network's row order
-    at each depth of `depths` (with early exit, all pairs)."""
-    n = p.shape[0]
-    depths = depths or [max(1, n // 4)]
+def proof_variants(pfsp, p, opt, mlp, rule, reps=3, slot_checks=False, subset=True):
+    """Proofs of the optimum `opt` of instance p (LB2, branching `rule`) by the
+    plain full-pair solver, the learned solver and the ablations."""
     inst = pfsp.pfsp_load_instance(p)
-    base = dict(bound=2, time_limit_s=time_limit_s)
-    if init_ub is not None:
-        base["init_ub"] = int(init_ub)
+    base = dict(bound=2, init_ub=int(opt), branching=rule)
     out = {}
 
-    def record(name, r, wall, extra_wall=0.0):
-        out[name] = {"cmax": r["cmax"], "outcome": r["outcome"], "seconds": r["kernel_seconds"],
-                     "wall_seconds": wall + extra_wall, "decomposed": r["decomposed"],
-                     "bounded": r["bounded_children"], "lb2_slots": r["lb2_slots"]}
+    def record(name, r, k, w, extra_wall=0.0):
+        assert r["outcome"] == pfsp.PFSP_PROVEN_NO_BETTER, (name, r["outcome"])
+        out[name] = {"kernel_s": k, "wall_s": w + extra_wall, "decomposed": int(r["decomposed"]),
+                     "lb2_slots": int(r["lb2_slots"])}
 
     pfsp.pfsp_set_lb2_pairs(inst, None)
-    record("plain", *_run(pfsp, inst, **base))
-    record("early_exit", *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT, **base))
-    if init_ub is None:
-        for d in depths:
-            record("child_order_depth_%d" % d,
-                   *_run(pfsp, inst, learned=pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_LEARN_CHILD_ORDER, mlp=mlp,
-                         learn_depth=d, **base))
+    record("plain", *_median_solve(pfsp, inst, reps, **base))
+    record("early_exit_index_order", *_median_solve(pfsp, inst, reps, **learned_options(pfsp, slot_checks), **base))
     t = time.perf_counter()
-    kept = learned_pairs(pfsp, inst, mlp)
+    order_pairs(pfsp, inst, mlp)
     t_rank = time.perf_counter() - t
-    record("learned", *_run(pfsp, inst, **learned_options(pfsp), **base), extra_wall=t_rank)
-    out["ranking_wall_seconds"] = t_rank
-    out["pairs_kept"] = None if kept is None else [int(q) for q in kept]
-    pfsp.pfsp_set_lb2_pairs(inst, None)
+    record("learned", *_median_solve(pfsp, inst, reps, **learned_options(pfsp, slot_checks), **base),
+           extra_wall=t_rank)
+    out["ranking_wall_s"] = t_rank
+    if subset:
+        pfsp.pfsp_set_pair_order(inst, None)
+        t = time.perf_counter()
+        kept = learned_pairs(pfsp, inst, mlp)
+        t_sub = time.perf_counter() - t
+        if kept is not None:
+            record("pair_subset", *_median_solve(pfsp, inst, reps, **base), extra_wall=t_sub)
+        pfsp.pfsp_set_lb2_pairs(inst, None)
     return out
 
 
-def compare(pfsp, shapes=((50, 5), (30, 10)), seeds=range(1, 6), train_seeds=range(1, 11), time_limit_s=30.0,
-            depth_fracs=(4,), proof=False, mlps=None):
-    """Time to the proven optimum, plain vs learned, on the given shapes.
+def compare_proofs(pfsp, cases, mlps, rules=(("minmin", 0),), reps=3, slot_checks=False, subset_rules=("minmin",)):
+    """Time-to-proof of the plain full-pair LB2 solver and of the learned solver.
 
-    The m-machine network is trained on traces of 20-job instances with the same
-    m (seeds train_seeds), unless mlps maps m to a trained network; the
-    evaluation instances are n x m with seeds 100 + s, disjoint from training.
-    proof=False solves from NEH (find and prove); proof=True first finds the
-    optimum with the plain solver, then times both solvers proving it (incumbent
-    at the optimum, a fixed tree)."""
+    cases: {name: (n, m, seeds)}; the optimum of each instance is found first
+    by the plain solver from NEH, then each variant proves it `reps` times
+    (median).  rules: (name, PFSP branching rule) pairs."""
     report = {}
-    for n, m in shapes:
-        if mlps and m in mlps:
-            mlp, info = mlps[m], {"reused": True}
-        else:
-            t = time.perf_counter()
-            train = [inputs.make_instance(20, m, s) for s in train_seeds]
-            mlp, info = train_network(pfsp, m, train)
-            info["seconds"] = time.perf_counter() - t
+    for name, (n, m, seeds) in cases.items():
         rows = []
         for s in seeds:
-            p = inputs.make_instance(n, m, 100 + s)
-            ub = None
-            if proof:
-                inst = pfsp.pfsp_load_instance(p)
-                f = pfsp.pfsp_solve(inst, bound=2, time_limit_s=time_limit_s)
-                if f["outcome"] != pfsp.PFSP_OPTIMAL:
-                    continue
-                ub = f["cmax"]
-            r = solve_variants(pfsp, p, mlp, time_limit_s=time_limit_s,
-                               depths=[max(1, n // f) for f in depth_fracs], init_ub=ub)
-            r["seed"] = 100 + s
-            r["same_optimum"] = len({v["cmax"] for v in r.values() if isinstance(v, dict)}) == 1
-            rows.append(r)
-        want = pfsp.PFSP_PROVEN_NO_BETTER if proof else pfsp.PFSP_OPTIMAL
-        done = [r for r in rows if all(r[k]["outcome"] == want for k in ("plain", "learned"))]
-
-        def tot(key, field):
-            return sum(r[key][field] for r in done)
-
-        t_plain, t_learn = tot("plain", "wall_seconds"), tot("learned", "wall_seconds")
-        t_rank = sum(r["ranking_wall_seconds"] for r in done)
-        k_plain, k_learn = tot("plain", "seconds"), tot("learned", "seconds")
-        n_plain, n_learn = tot("plain", "decomposed"), tot("learned", "decomposed")
-        report["%dx%d" % (n, m)] = {
-            "mode": "proof" if proof else "find", "training": info, "instances": rows,
-            "solved_by_both": len(done),
-            "wall_plain_s": t_plain, "wall_learned_s": t_learn,
-            "speedup_wall": (t_plain / t_learn) if t_learn > 0 else None,
-            # the network's share of the learned solver's time: it runs once per
-            # instance, on the root's children, to rank the machine pairs
-            "ranking_wall_s": t_rank,
-            "mlp_share_of_learned_wall": (t_rank / t_learn) if t_learn > 0 else None,
-            "kernel_plain_s": k_plain, "kernel_learned_s": k_learn,
-            "speedup_kernel": (k_plain / k_learn) if k_learn > 0 else None,
-            "node_ratio_learned_over_plain": (n_learn / n_plain) if n_plain > 0 else None,
-            "ablation_wall_s": {key: tot(key, "wall_seconds") for key in done[0] if isinstance(done[0][key], dict)}
-            if done else {},
-        }
+            p = inputs.make_instance(n, m, s)
+            f = pfsp.pfsp_solve(pfsp.pfsp_load_instance(p), bound=2, time_limit_s=30.0)
+            if f["outcome"] != pfsp.PFSP_OPTIMAL:
+                continue
+            row = {"seed": s, "optimum": int(f["cmax"])}
+            for rname, rule in rules:
+                row[rname] = proof_variants(pfsp, p, f["cmax"], mlps[m], rule, reps=reps, slot_checks=slot_checks,
+                                            subset=rname in subset_rules)
+            rows.append(row)
+        rep = {"instances": len(rows), "seeds": [r["seed"] for r in rows]}
+        for rname, _ in rules:
+            keys = [k for k, v in rows[0][rname].items() if isinstance(v, dict)] if rows else []
+            tot = {k: sum(r[rname][k]["kernel_s"] for r in rows) for k in keys}
+            wall = {k: sum(r[rname][k]["wall_s"] for r in rows) for k in keys}
+            nodes = {k: sum(r[rname][k]["decomposed"] for r in rows) for k in keys}
+            per = [r[rname]["plain"]["kernel_s"] / r[rname]["learned"]["kernel_s"] for r in rows]
+            rep[rname] = {
+                "kernel_s": tot, "wall_s": wall, "decomposed": nodes,
+                "speedup_kernel": tot["plain"] / tot["learned"] if rows else None,
+                "speedup_wall": wall["plain"] / wall["learned"] if rows else None,
+                "speedup_kernel_per_seed_median": statistics.median(per) if per else None,
+                "seeds_faster": int(sum(x > 1.0 for x in per)),
+                "node_ratio_learned_over_plain": nodes["learned"] / nodes["plain"] if rows else None,
+                "ranking_wall_s": sum(r[rname]["ranking_wall_s"] for r in rows),
+            }
+        report[name] = rep
     return report
