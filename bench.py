@@ -402,7 +402,9 @@ def batch_leg(pfsp):
             "decomposed_nodes_per_s": st["decomposed"] / max(st["kernel_seconds"], 1e-9),
             "all_optimal": bool((r["outcomes"] == pfsp.PFSP_OPTIMAL).all()),
             "optima_checked_against_oracle": len(checked), "optima_match_oracle": bool(match),
-            "autotuned": {"warps_per_sm": tuned.warps_per_sm, "check_every": tuned.check_every,
+            "autotuned": {"warps_per_sm": tuned.warps_per_sm, "slot_warps": tuned.slot_warps,
+                          "instance_slots": st["explorers"] // max(tuned.slot_warps, 1),
+                          "check_every": tuned.check_every,
                           "min_steal": tuned.min_steal, "tuning_s": tune_s}}
 
 

@@ -218,7 +218,9 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
 #define PFSP_LEARN_CHILD_ORDER 1  /* order each new row by the network's descend-first logits */
 #define PFSP_LEARN_PAIR_ORDER 2   /* sweep LB2's 32-pair slots in the order of the network's pair logits */
 #define PFSP_EARLY_EXIT 4         /* skip the LB2 sweep of a node when every child of one direction
-                                     has an LB1 at least the solve's initial incumbent: such a node
+                                     has an LB1 at least the incumbent c (the incumbent the explorer
+                                     read for this node, never above the initial one and equal to it
+                                     in proof mode; under PFSP_MINBRANCH the initial one): such a node
                                      has no child below the incumbent under either MinMin rule (the
                                      decided direction holds no minimum below it, so MinMin picks
                                      it) nor under MinBranch (it has no child below the incumbent, so
@@ -231,9 +233,10 @@ typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
                                      the instance's order (pfsp_learn_pair_order puts the pairs most
                                      likely to decide first). */
 #define PFSP_EARLY_EXIT_CHILDREN 16 /* with PFSP_EARLY_EXIT: the sweep evaluates only the jobs one of
-                                     whose children has an LB1 below the solve's initial incumbent c;
-                                     a child left out keeps its LB1, a lower bound of its LB2 that is
-                                     at least c.  It is pruned as with the full sweep, and
+                                     whose children has an LB1 below the incumbent c of
+                                     PFSP_EARLY_EXIT; a child left out keeps its LB1, a lower bound of
+                                     its LB2 that is at least c.  It is pruned as with the full
+                                     sweep, and in proof mode (c fixed at the initial incumbent)
                                      min(bound, c) is unchanged, so under PFSP_MINMIN_CAPPED the
                                      search tree and every counter are those of the full sweep.
                                      Under PFSP_MINMIN and PFSP_MINBRANCH the sums of bounds that
@@ -270,7 +273,13 @@ typedef struct {
                              (pfsp_beam_search) below the promoted explorer nodes with their
                              prefix and suffix fixed, widths 1, 2, 4, ... 256, 2 both (odd
                              threads beam search) */
-    int reserved[3];
+    int slot_warps;       /* pfsp_solve_batch only: explorers per instance slot.  A slot is one CTA
+                             that claims an instance and explores it with its warps (then joins
+                             the busiest running instance); with warps_per_sm explorers per SM,
+                             warps_per_sm / slot_warps slots run on each SM, so this sets how many
+                             instances are in flight at once.  0 (default): one slot per SM of
+                             warps_per_sm explorers (12 when that is 0 too) */
+    int reserved[2];
 } pfsp_options;
 
 void pfsp_default_options(pfsp_options *opt);

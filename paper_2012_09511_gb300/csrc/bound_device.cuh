@@ -84,13 +84,15 @@ constexpr int kWarpHead = 256;
 constexpr int kRegWalk = 20;
 
 // reg_walk: the layout of kernels whose LB2 walks keep their records in
-// registers (n <= kRegWalk): no E region.
+// registers (n <= kRegWalk, register accumulators): no E region and no
+// transpose buffer.
 __host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2, bool reg_walk = false) {
     if (!lb2) return kWarpHead;
     int nr = round4(n);
     int g = round4(nr * (m | 1));
-    // G takes 2g words; then E + Cb (96 nr), or Cb + X (66 nr) without E
-    const int walk = reg_walk ? 66 * nr : 96 * nr;
+    // G takes 2g words; then E + Cb (96 nr: the transpose buffer aliases E
+    // and Cb), or Cb alone (32 nr) with register walks
+    const int walk = reg_walk ? 32 * nr : 96 * nr;
     return kWarpHead + 3 * g + walk + (smem_acc ? 64 * nr : 0);
 }
 
@@ -104,10 +106,12 @@ __device__ inline WarpScratch carve_warp(int *base, int n, int m, bool reg_walk 
     w.G = reinterpret_cast<int2 *>(base + kWarpHead);
     w.Bb = base + kWarpHead + 2 * g;
     if (reg_walk) {
+        // register walks come with register accumulators: neither the
+        // transpose buffer nor shared accumulators are used
         w.E = nullptr;
         w.Cb = w.Bb + g;
-        w.X = reinterpret_cast<int2 *>(w.Cb);
-        w.Acc = reinterpret_cast<int2 *>(w.Cb + 66 * nr);
+        w.X = nullptr;
+        w.Acc = nullptr;
     } else {
         w.E = reinterpret_cast<int2 *>(w.Bb + g);
         w.Cb = w.Bb + g + 64 * nr;
@@ -498,9 +502,12 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         const int *bb = W.Bb + l;
         const int *cb = W.Cb + lane;
         if constexpr (REGACC) {
+            // children past the last evaluated one cost nothing (ev is a
+            // 32-bit mask here: register accumulators hold u <= 32)
+            const int cend = SURV ? ((ev ? 32 - __clz((unsigned)ev) : 0) + 3) & ~3 : u4;
 #pragma unroll
             for (int c0 = 0; c0 < NC; c0 += 4) {
-                if (c0 >= u4) break;
+                if (c0 >= cend) break;
 #pragma unroll
                 for (int c = c0; c < c0 + 4; ++c) {
                     if (SURV && !((ev >> c) & 1)) continue;  // warp-uniform

@@ -429,8 +429,14 @@ struct Explorer {
                     order = X.sorder;
                 }
             }
+            // early-exit threshold: the incumbent of this iteration (never
+            // above the initial one, equal to it in proof mode); MinBranch
+            // counts children against the initial incumbent, so it keeps that
+            const int ee_cap = !(a.learned & PFSP_EARLY_EXIT) ? INT_MAX
+                               : a.branching == PFSP_MINBRANCH ? a.cap
+                                                               : min(a.cap, ub_seen);
             const int swept =
-                EARLY ? decompose_lb2<NW, MT, 0, true>(T, W, n, m, S, cb, (a.learned & PFSP_EARLY_EXIT) ? a.cap : INT_MAX,
+                EARLY ? decompose_lb2<NW, MT, 0, true>(T, W, n, m, S, cb, ee_cap,
                                                        (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order,
                                                        (a.learned & PFSP_EARLY_EXIT_CHILDREN) != 0)
                       : decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);

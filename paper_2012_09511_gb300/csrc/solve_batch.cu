@@ -280,13 +280,19 @@ static int plan_batch(const pfsp_instance *const *insts, int count, const pfsp_o
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int warps = opt->warps_per_sm > 0 ? std::min(opt->warps_per_sm, kSolveWarps) : kSolveWarps;
+    // a slot (CTA) of `warps` explorers per instance in flight; explorers
+    // per SM as asked (a cooperative launch may use fewer CTAs per SM than
+    // can be resident), else every resident slot
+    const int per_sm_want = opt->warps_per_sm > 0 ? opt->warps_per_sm : 0;
+    int warps = opt->slot_warps > 0 ? opt->slot_warps : (per_sm_want > 0 ? per_sm_want : kSolveWarps);
+    warps = std::min(warps, kSolveWarps);
     long long fit = ((long long)optin - 256 - (long long)P.max_tab * 4) / ((long long)P.warp_stride * 4);
     warps = (int)std::min<long long>(warps, fit);
     if (warps < 1) return set_error(PFSP_ERR_UNSUPPORTED, "batch explorer state does not fit in shared memory");
     P.smem = (size_t)(P.max_tab + warps * P.warp_stride) * 4;
     int per_sm = P.nw == 1 ? batch_occupancy<1>(warps, P.smem) : batch_occupancy<2>(warps, P.smem);
     if (per_sm < 1) return set_error(PFSP_ERR_CUDA, "batch solve kernel cannot be resident");
+    if (per_sm_want > 0) per_sm = std::max(1, std::min(per_sm, per_sm_want / warps));
     P.warps = warps;
     P.blocks = nsm * per_sm;
     P.K = P.blocks * warps;
@@ -507,7 +513,8 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
 }
 
 // Autotuner: time the batch solve on a sample of the instances for a small
-// grid of pool parameters (explorers per SM, iterations between publications,
+// grid of pool parameters (explorers per SM, explorers per instance slot --
+// hence instances in flight per SM --, iterations between publications,
 // smallest interval a victim splits) and keep the fastest.
 extern "C" int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp_options *base,
                                    int sample, pfsp_options *best) {
@@ -515,26 +522,30 @@ extern "C" int pfsp_autotune_batch(const pfsp_instance *const *insts, int count,
     const int k = sample > 0 ? std::min(sample, count) : std::min(count, 32);
     std::vector<int32_t> cm(k), perms;
     std::vector<int> out(k);
-    const int warps_grid[] = {4, 8, 12};
+    const int per_sm_grid[] = {8, 12};
+    const int slot_grid[] = {4, 6, 12};
     const int check_grid[] = {8, 32};
     const double steal_grid[] = {2.0, 720.0};
     double best_t = 1e300;
     pfsp_options bo = *base;
-    for (int w : warps_grid)
-        for (int c : check_grid)
-            for (double s : steal_grid) {
-                pfsp_options o = *base;
-                o.warps_per_sm = w;
-                o.check_every = c;
-                o.min_steal = s;
-                pfsp_stats_t stt;
-                int rc = pfsp_solve_batch(insts, k, &o, nullptr, cm.data(), nullptr, out.data(), &stt);
-                if (rc != PFSP_OK) return rc;
-                if (stt.kernel_seconds < best_t) {
-                    best_t = stt.kernel_seconds;
-                    bo = o;
+    for (int e : per_sm_grid)
+        for (int w : slot_grid)
+            for (int c : check_grid)
+                for (double st : steal_grid) {
+                    if (w > e) continue;
+                    pfsp_options o = *base;
+                    o.warps_per_sm = e;
+                    o.slot_warps = w;
+                    o.check_every = c;
+                    o.min_steal = st;
+                    pfsp_stats_t stt;
+                    int rc = pfsp_solve_batch(insts, k, &o, nullptr, cm.data(), nullptr, out.data(), &stt);
+                    if (rc != PFSP_OK) return rc;
+                    if (stt.kernel_seconds < best_t) {
+                        best_t = stt.kernel_seconds;
+                        bo = o;
+                    }
                 }
-            }
     *best = bo;
     return PFSP_OK;
 }

@@ -75,7 +75,8 @@ class pfsp_options(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("min_steal", ctypes.c_double), ("mlp", ctypes.c_void_p),
                 ("learned", ctypes.c_int), ("learn_depth", ctypes.c_int), ("phase_timers", ctypes.c_int),
                 ("heuristic_threads", ctypes.c_int), ("heuristic_seed", ctypes.c_int), ("lb1_minht", ctypes.c_int),
-                ("heuristic_kind", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("heuristic_kind", ctypes.c_int), ("slot_warps", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 if not os.path.exists(LIB_PATH):
