@@ -29,6 +29,9 @@ struct pfsp_mlp {
 
 namespace pfsp {
 
+cudaError_t mlp_forward_tc(const MlpDev &P, const float *dX, long long rows, float *dY, cudaStream_t st,
+                           bool *timed_out);
+
 static inline int round16(int x) { return (x + 15) & ~15; }
 
 MlpDev mlp_view(const pfsp_mlp *M) {
@@ -119,51 +122,6 @@ cudaError_t mlp_build_image(const pfsp_mlp *M, int O3, void *dst, cudaStream_t s
     const int total = mlp_image_bytes(M->D0, O3) / 2;
     mlp_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(mlp_view(M), O3, (unsigned char *)dst);
     return cudaGetLastError();
-}
-
-// Forward pass with the fused inference path that the solver uses: the
-// weights are read from the image in global memory, each warp runs 16-row
-// tiles with its activations in its own shared-memory scratch.
-template <int KT1>
-__global__ void mlp_forward_kernel(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
-                                   float *Y) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int D0 = 16 * KT1, ldx = D0 + 8;
-    (void)img_bytes;
-    const MlpImage P = mlp_image_view(img, D0, O);
-    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(sm + wib * mlp_scratch_bytes(D0));
-    const int g = lane >> 2, t = lane & 3;
-    const long long tiles = (rows + 15) / 16;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + wib; tile < tiles; tile += nw) {
-        for (int e = lane; e < 16 * D0; e += 32) {
-            const long long r = tile * 16 + e / D0;
-            Xs[(e / D0) * ldx + e % D0] = __float2bfloat16_rn(r < rows ? X[r * D0 + e % D0] : 0.0f);
-        }
-        __syncwarp();
-        __nv_bfloat16 *H1 = Xs + 16 * ldx, *H2 = H1 + 16 * (kMlpHidden + 8);
-        mlp_fused_hidden<KT1>(P, Xs, H1, MlpPark{H2});
-        for (int p = 0; p < O / 16; ++p) {
-            float c0[4], c1[4];
-            mlp_tile_cols<kMlpHidden / 16>(H2, kMlpHidden + 8, P.W3t, kMlpHidden + 8, p, c0, c1);
-            const long long r0 = tile * 16 + g, r1 = r0 + 8;
-            const int ca = 16 * p + 2 * t, cb = ca + 8;
-            if (r0 < rows) {
-                Y[r0 * O + ca] = c0[0] + P.b3[ca];
-                Y[r0 * O + ca + 1] = c0[1] + P.b3[ca + 1];
-                Y[r0 * O + cb] = c1[0] + P.b3[cb];
-                Y[r0 * O + cb + 1] = c1[1] + P.b3[cb + 1];
-            }
-            if (r1 < rows) {
-                Y[r1 * O + ca] = c0[2] + P.b3[ca];
-                Y[r1 * O + ca + 1] = c0[3] + P.b3[ca + 1];
-                Y[r1 * O + cb] = c1[2] + P.b3[cb];
-                Y[r1 * O + cb + 1] = c1[3] + P.b3[cb + 1];
-            }
-        }
-        __syncwarp();
-    }
 }
 
 // Gradients of the masked mean BCE over the batch rows idx[row0 .. row0+n)
@@ -365,21 +323,6 @@ using namespace pfsp;
 
 namespace pfsp {
 
-template <int KT1>
-static cudaError_t forward_t(const unsigned char *img, int img_bytes, int O, const float *X, long long rows,
-                             float *Y) {
-    const int warps = 4;
-    const size_t smem = (size_t)warps * mlp_scratch_bytes(16 * KT1);
-    void (*kern)(const unsigned char *, int, int, const float *, long long, float *) = mlp_forward_kernel<KT1>;
-    cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    kern<<<nsm, warps * 32, smem>>>(img, img_bytes, O, X, rows, Y);
-    return cudaGetLastError();
-}
-
 }  // namespace pfsp
 
 extern "C" {
@@ -483,22 +426,13 @@ int pfsp_mlp_set_params(pfsp_mlp *M, const float *in) {
 
 namespace pfsp {
 
-// Logits dY [rows][O] of device inputs dX [rows][D0] (synchronous).
+// Logits dY [rows][O] of device inputs dX [rows][D0] (synchronous): the
+// tcgen05 kernel of mlp_tc.cu; cudaErrorTimeout when one of its bounded
+// waits expired.
 cudaError_t mlp_forward_dev(const pfsp_mlp *M, const float *dX, long long rows, float *dY) {
-    unsigned char *img = nullptr;
-    const int img_bytes = mlp_image_bytes(M->D0, M->O);
-    cudaError_t e = cudaMalloc(&img, img_bytes);
-    if (e == cudaSuccess) e = mlp_build_image(M, M->O, img, 0);
-    if (e == cudaSuccess) {
-        switch (M->D0 / 16) {
-            case 1: e = forward_t<1>(img, img_bytes, M->O, dX, rows, dY); break;
-            case 2: e = forward_t<2>(img, img_bytes, M->O, dX, rows, dY); break;
-            case 3: e = forward_t<3>(img, img_bytes, M->O, dX, rows, dY); break;
-            default: e = forward_t<4>(img, img_bytes, M->O, dX, rows, dY); break;
-        }
-    }
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(img);
+    bool timed_out = false;
+    cudaError_t e = mlp_forward_tc(mlp_view(M), dX, rows, dY, 0, &timed_out);
+    if (e == cudaSuccess && timed_out) e = cudaErrorTimeout;
     return e;
 }
 
@@ -517,6 +451,7 @@ int pfsp_mlp_forward(const pfsp_mlp *M, int64_t rows, const float *X, float *Y) 
     if (e == cudaSuccess) e = cudaMemcpy(Y, dY, rows * M->O * 4, cudaMemcpyDeviceToHost);
     cudaFree(dX);
     cudaFree(dY);
+    if (e == cudaErrorTimeout) return set_error(PFSP_ERR_TIMEOUT, "pfsp_mlp_forward: a bounded device wait expired");
     return e == cudaSuccess ? PFSP_OK : set_error(PFSP_ERR_CUDA, "pfsp_mlp_forward: %s", cudaGetErrorString(e));
 }
 

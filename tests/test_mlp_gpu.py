@@ -72,3 +72,29 @@ def test_training_reduces_loss(pf):
     Y = pf.pfsp_mlp_forward(mlp, X)
     acc = ((Y[:, 1:11] > 0) == (T[:, 1:11] > 0.5)).mean()
     assert acc > 0.9, acc
+
+
+@pytest.mark.parametrize("m", [5, 10, 20])
+def test_batched_forward_many_tiles(pf, m):
+    # the batched forward (tcgen05 kernel, 128-row tiles, TMEM accumulators)
+    # on more rows than one pass of the grid covers, with a ragged last tile:
+    # every row against the reference with the same bf16 roundings
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mlp = pf.pfsp_mlp_create(m, seed=21)
+    flat = pf.pfsp_mlp_get_params(mlp)
+    rng = np.random.default_rng(100 + m)
+    flat = flat + rng.normal(0, 0.02, flat.size).astype(np.float32)
+    pf.pfsp_mlp_set_params(mlp, flat)
+    params = mlp.split(flat)
+    rows = 128 * nsm * 2 + 77
+    X, _, _ = _data(mlp, rows, 7 + m)
+    Y = pf.pfsp_mlp_forward(mlp, X)
+    Yr, _ = mlp_ref.forward(params, X)
+    assert Y.shape == Yr.shape
+    assert np.isfinite(Y).all()
+    assert np.linalg.norm(Y - Yr) <= REL_TOL * np.linalg.norm(Yr)
+    # row by row too: no tile or row is misplaced
+    err = np.linalg.norm(Y - Yr, axis=1)
+    ref = np.linalg.norm(Yr, axis=1)
+    assert (err <= 5e-2 * ref + 1e-3).all(), (int(np.argmax(err - 5e-2 * ref)), float(err.max()))
