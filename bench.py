@@ -431,6 +431,7 @@ def learned_leg(pfsp):
              "18x20": (18, 20, range(101, 104))}
     rules = (("minmin_capped", pfsp.PFSP_MINMIN_CAPPED), ("minmin", pfsp.PFSP_MINMIN))
     rep = learned.compare_proofs(pfsp, cases, mlps, rules=rules, reps=3, slot_checks=LEARNED_SLOT_CHECKS)
+    find = learned.compare_finding(pfsp, 30, 10, learned.SEEDS_30X10, mlps[10], rule=pfsp.PFSP_MINMIN)
     for name, r in rep.items():
         c = r.get("minmin_capped")
         if c:
@@ -440,7 +441,9 @@ def learned_leg(pfsp):
                 " + slot checks" if LEARNED_SLOT_CHECKS else ""),
             "ablations": "early_exit_index_order: the same early exit, pairs in index order; "
                          "pair_subset: LB2 over the network's top half of the 32-pair slots (weaker bound)",
-            "proofs": rep}
+            "proofs": rep,
+            "finding_30x10": dict(find, workload="30 x 10 seeds of the proofs, from NEH to the proven optimum, "
+                                                 "MinMin, one solve each")}
 
 
 def run_reference(args):
@@ -624,8 +627,9 @@ def run_native(args):
                      "ops_per_launch": ops, "kernel_ms": launch_ms,
                      "child_by_child_ops_per_launch": cbc_ops,
                      "child_by_child_frac": cbc_ops / (launch_ms * 1e-3) / peak_ops,
-                     "ncu_utilisation": {k: ncu[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct",
-                                                             "lsu_pipe_pct") if k in ncu} if ncu else None},
+                     "ncu_utilisation": {k: ncu[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_inst_pct",
+                                                             "fmaheavy_cycles_pct", "lsu_pipe_pct") if k in ncu}
+                     if ncu else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * (n + 2)),
                 "d2h_bytes_per_step": int(2 * N * 2 * n * 4),
                 "statistic": "mean of %d steps through pfsp_bound_batch (after %d untimed)" % (

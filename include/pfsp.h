@@ -208,9 +208,12 @@ typedef struct {
  *   warps_per_sm explorers per SM; 0 = as many as fit in shared memory (at
  *                most 12).
  *   check_every  iterations between limit checks and length publications
- *                (rounded up to a power of two); 0 = default (16).
+ *                (rounded up to a power of two); 0 = default (8).
  *   min_steal    smallest remaining interval (in leaves) a victim splits;
- *                0 = default (2, i.e. any splittable interval).
+ *                0 = default: pfsp_solve and pfsp_solve_noalloc take the
+ *                leaves of a subtree with min(floor(2n/5), 9) jobs left (8!
+ *                at n = 20), pfsp_solve_batch takes 2 (any splittable
+ *                interval; pfsp_autotune_batch chooses between 2 and 8!).
  */
 typedef struct pfsp_mlp pfsp_mlp; /* ordering network, see pfsp_mlp_create */
 

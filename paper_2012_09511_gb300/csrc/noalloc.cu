@@ -193,8 +193,8 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     a.best_key = (unsigned long long *)(sc + 4);
     a.node_limit = opt->node_limit;
     a.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
-    a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
-    int ce = opt->check_every > 0 ? opt->check_every : 16, pw = 1;
+    a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : default_min_steal(n);
+    int ce = opt->check_every > 0 ? opt->check_every : kDefaultCheckEvery, pw = 1;
     while (pw < ce) pw <<= 1;
     a.check_every = pw;
 

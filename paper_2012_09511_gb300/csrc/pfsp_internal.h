@@ -18,6 +18,20 @@ constexpr int kMaxTime = (1 << 22) - 1;     // largest accepted processing time
 constexpr long long kMaxTotal = 1LL << 28;  // largest accepted sum of all times
 constexpr int kMaxTableBytes = 160 * 1024;  // LB2 tables must fit in shared memory
 constexpr long long kBoundChunk = 1 << 18;  // nodes per chunk of the host-pointer bounding pipeline
+constexpr int kDefaultCheckEvery = 8;      // explorer iterations between limit checks and length publications
+
+// Default smallest interval (in leaves) a victim splits for a thief: the
+// leaves of a subtree with min(floor(2n/5), 9) jobs left (8! at n = 20, 9!
+// from n = 23 on).  Smaller intervals cost the thief more to rebuild (a path
+// of decompositions down to the interval's start) than the work they hold;
+// much larger ones leave thieves idle (12! was slower than 8!-10! on 30-job
+// proofs).
+inline float default_min_steal(int n) {
+    double f = 1.0;
+    const int jobs = (2 * n) / 5 < 9 ? (2 * n) / 5 : 9;
+    for (int k = 2; k <= jobs; ++k) f *= k;
+    return (float)f;
+}
 
 // Instance tables, one contiguous int32 blob in device memory that every CTA
 // copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):

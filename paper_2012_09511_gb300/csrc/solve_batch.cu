@@ -413,7 +413,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     b.node_limit = opt->node_limit;
     b.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
     b.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
-    int ce = opt->check_every > 0 ? opt->check_every : 16, pw = 1;
+    int ce = opt->check_every > 0 ? opt->check_every : kDefaultCheckEvery, pw = 1;
     while (pw < ce) pw <<= 1;
     b.check_every = pw;
 
@@ -525,7 +525,7 @@ extern "C" int pfsp_autotune_batch(const pfsp_instance *const *insts, int count,
     const int per_sm_grid[] = {8, 12};
     const int slot_grid[] = {4, 6, 12};
     const int check_grid[] = {8, 32};
-    const double steal_grid[] = {2.0, 720.0};
+    const double steal_grid[] = {2.0, 40320.0};
     double best_t = 1e300;
     pfsp_options bo = *base;
     for (int e : per_sm_grid)

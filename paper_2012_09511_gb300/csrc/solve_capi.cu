@@ -384,7 +384,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (use_net) a.net_image = (const unsigned char *)(b + o_img);
     a.node_limit = opt->node_limit;
     a.time_limit_ns = opt->time_limit_s > 0 ? (unsigned long long)(opt->time_limit_s * 1e9) : 0ull;
-    a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : 2.0f;
+    a.min_steal = opt->min_steal > 0 ? (float)opt->min_steal : default_min_steal(n);
     if (tcap > 0) {
         a.trace_perm = (uint8_t *)(b + o_tp);
         a.trace_d1 = (uint8_t *)(b + o_t1);
@@ -393,7 +393,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
         a.trace_cap = tcap;
         a.trace_stride = tr->stride > 0 ? tr->stride : 1;
     }
-    int ce = opt->check_every > 0 ? opt->check_every : 16;
+    int ce = opt->check_every > 0 ? opt->check_every : kDefaultCheckEvery;
     int pw = 1;
     while (pw < ce) pw <<= 1;
     a.check_every = pw;
