@@ -201,3 +201,25 @@ def compare_proofs(pfsp, cases, mlps, rules=(("minmin", 0),), reps=3, slot_check
             }
         report[name] = rep
     return report
+
+
+def compare_finding(pfsp, n, m, seeds, mlp, rule=0):
+    """Time to the proven optimum from the NEH schedule (finding mode), plain
+    full-pair LB2 against the learned solver, one solve each per instance
+    (finding-mode trees depend on when each explorer meets the incumbents, so
+    they vary from run to run); optima must agree."""
+    tot = {"plain": 0.0, "learned": 0.0}
+    nodes = {"plain": 0, "learned": 0}
+    same = True
+    for s in seeds:
+        inst = pfsp.pfsp_load_instance(inputs.make_instance(n, m, s))
+        pfsp.pfsp_set_pair_order(inst, None)
+        a = pfsp.pfsp_solve(inst, bound=2, branching=rule, time_limit_s=30.0)
+        order_pairs(pfsp, inst, mlp)
+        b = pfsp.pfsp_solve(inst, bound=2, branching=rule, time_limit_s=30.0, **learned_options(pfsp))
+        same &= a["cmax"] == b["cmax"] and a["outcome"] == b["outcome"] == pfsp.PFSP_OPTIMAL
+        for k, r in (("plain", a), ("learned", b)):
+            tot[k] += r["kernel_seconds"]
+            nodes[k] += int(r["decomposed"])
+    return {"kernel_s": tot, "decomposed": nodes, "same_optima": bool(same),
+            "speedup_kernel": tot["plain"] / tot["learned"] if tot["learned"] > 0 else None}
