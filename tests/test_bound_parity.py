@@ -83,6 +83,24 @@ def test_empty_batch_and_invalid_depths(pf):
         pf.pfsp_bound_batch(inst, 0, np.arange(8)[None], [1], [1])
 
 
+def test_invalid_depths_found_in_large_batches(pf):
+    # batches of a million nodes and more validate their depths on several host
+    # threads before any work: an invalid node in the last thread's range is
+    # refused, and so is one in the first
+    n, m, N = 12, 5, (1 << 20) + 333
+    inst = pf.pfsp_load_instance(inputs.make_instance(n, m, 2))
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=3, dmax=5)
+    for bad in (N - 1, 7):
+        e1, e2 = d1.copy(), d2.copy()
+        e1[bad], e2[bad] = 7, 6  # 13 > n
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_bound_batch(inst, 3, perm, e1, e2)
+        assert e.value.code == pf.PFSP_ERR_INVALID and ("node %d" % bad) in str(e.value)
+    g1, _ = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
+    assert pf.pfsp_stats(inst)["bounded_children"] == int(2 * (n - d1.astype(np.int64) - d2).sum())
+    assert ((g1 >= 0).sum(axis=2) == (n - d1.astype(np.int64) - d2)[:, None]).all()
+
+
 def test_lb1_only_and_lb2_only(pf):
     n, m = 20, 20
     p = inputs.make_instance(n, m, 9)
