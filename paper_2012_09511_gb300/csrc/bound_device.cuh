@@ -55,7 +55,8 @@ struct SmemTables {
     const int *pm;        // [m][nj]
     const int *tot;       // [32]
     const int *kl;        // [S*32]
-    const uint8_t *rank;  // [S][n][32] position of job j in the lane's pair order
+    const int *pq;        // [2][m][nj] per job: P_k = sum of its times on machines 0..k, then Q_k = on k..m-1
+    const uint8_t *rank;  // [n][S][32] bit of job j in the lane's position masks (see pos_of_bit)
     const int2 *ptab;     // [S][n][32]
     int S;                // slots of the table layout (stride of rank); the sweep may use fewer
 };
@@ -70,9 +71,9 @@ struct WarpScratch {
     int *ul;          // [64] compact list: ul[c] = c-th unscheduled job
     int *cidx;        // [64] cidx[j] = compact index of job j
     int2 *G;          // [nr][mp] {forward child: F'_k + R_k - p_jk, backward child: F_k + R_k - p_jk}
-    int *Bb;          // [nr][mp] backward child back B'_k
+    int *Bb;          // [nr][mp] backward child back B'_k minus the parent's B_k
     int2 *E;          // [nr][32] prefix pass records {PB, t | c << 8} (per lane); NULL for register walks
-    int *Cb;          // [nr][32] C of child c (per lane)
+    int *Cb;          // [nr][32] C of child c plus the parent's B_l (per lane)
     int2 *X;          // [u][33] transpose buffer, aliasing E and Cb (or Cb and the words after it)
     int2 *Acc;        // [nr][32] accumulators (only when not kept in registers)
 };
@@ -138,6 +139,57 @@ __device__ __forceinline__ int lowest_bit(umask_t<NW> x) {
     else return __ffsll((long long)x) - 1;
 }
 
+// Bit walks.  32-bit masks are walked from the highest set bit (bfind, one
+// instruction, -1 for an empty mask) and 64-bit masks from the lowest (a
+// 64-bit bfind and variable shift cost more than the 64-bit ffs and
+// x & (x - 1)).  The position masks of a pair's Johnson order follow the walk:
+// position t sits in bit 31 - t (n <= 32) or t (n > 32), so that every walk
+// meets the positions in ascending order.
+template <int NW>
+__device__ __forceinline__ int next_bit(umask_t<NW> x) {
+    if constexpr (NW == 1) {
+        int r;
+        asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+        return r;
+    } else {
+        return lowest_bit<NW>(x);
+    }
+}
+
+// x without bit t = next_bit(x).  shl clamps shift amounts past the width,
+// so t = -1 (an empty mask) leaves x = 0 unchanged.
+template <int NW>
+__device__ __forceinline__ umask_t<NW> drop_bit(umask_t<NW> x, int t) {
+    if constexpr (NW == 1) {
+        uint32_t b;
+        asm("shl.b32 %0, 1, %1;" : "=r"(b) : "r"(t));
+        return x & ~b;
+    } else {
+        return x & (x - 1);
+    }
+}
+
+// Position of bit b of a position mask (its own inverse).
+template <int NW>
+__device__ __forceinline__ int pos_of_bit(int b) {
+    return NW == 1 ? 31 - b : b;
+}
+
+// The mask of positions 0..n-1.
+template <int NW>
+__device__ __forceinline__ umask_t<NW> all_positions(int n) {
+    if constexpr (NW == 1) return ~0u << (32 - n);  // 1 <= n <= 32
+    else return n >= 64 ? ~0ull : ((1ull << n) - 1);
+}
+
+// __shfl_down_sync with the source lane clamped to max_lane: lanes whose
+// source lies above it keep their own value.
+__device__ __forceinline__ int shfl_down_clamped(int v, int delta, int max_lane) {
+    int r;
+    asm volatile("shfl.sync.down.b32 %0, %1, %2, %3, 0xffffffff;" : "=r"(r) : "r"(v), "r"(delta), "r"(max_lane));
+    return r;
+}
+
 // max(a + b, c): the step of every max-plus recurrence below, one DPX
 // add-max instruction on sm_90 and later.
 __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
@@ -145,8 +197,12 @@ __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s
 // Decompose the node whose permutation entries are held one per lane
 // (job0 = position lane, job1 = position lane + 32) with depths d1, d2.
 // kind: bit 0 = LB1 wanted, bit 1 = LB2 wanted.  MT is the machine count
-// when known at compile time (0: take m_rt).  All 32 lanes must call.
-template <int NW, int MT>
+// when known at compile time (0: take m_rt).  SCAN: fronts and backs by
+// max-scans over the machines, one per scheduled job (needs T.pq), when there
+// are at least 16 machines; otherwise, and below 16 machines, by the
+// wavefront (its m - 1 fill steps cost less than log2 m shuffles per job
+// there).  All 32 lanes must call.
+template <int NW, int MT, bool SCAN = false>
 __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int kind,
                                               int job0, int job1, int d1, int d2, ChildBounds<NW> &out) {
     using mask_t = umask_t<NW>;
@@ -180,10 +236,50 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
     }
 
     // ---- steps 1 and 3: front (Eq. 1 over sigma1) and back (Eq. 1 over the
-    // reversed sigma2 on reversed machines) as two wavefronts over machines,
-    // run in the same loop so that their shuffle chains overlap -------------
+    // reversed sigma2 on reversed machines), lane = machine -------------------
     int Fk = 0, Bk = 0, Sk = 0;
-    {
+    if (SCAN && (MT ? MT >= 16 : m >= 16)) {
+        // Appending job j to the front, F'_k = max(F_k, F'_{k-1}) + p_jk,
+        // unrolls to F'_k = P_k + max_{k' <= k} (F_k' - P_k' + p_jk') with P the
+        // job's prefix sums over machines: one inclusive max-scan over lanes.
+        // Prepending it to the back is the mirror image with the suffix sums
+        // Q: B'_k = Q_k + max_{k' >= k} (B_k' - Q_k' + p_jk').  The front's
+        // scan reads lower lanes only; the back's is clamped to the last
+        // machine, so lanes past it (rows of machine 0) feed no machine.
+        constexpr int LG = MT == 0 ? 5 : MT <= 2 ? 1 : MT <= 4 ? 2 : MT <= 8 ? 3 : MT <= 16 ? 4 : 5;
+        const int kk = lane < m ? lane : 0;
+        const int *prow = T.pm + kk * nj, *Prow = T.pq + kk * nj, *Qrow = T.pq + (m + kk) * nj;
+        const int steps = max(d1, d2);
+        for (int s = 0; s < steps; ++s) {
+            const int pos = n - 1 - s;
+            int jf = __shfl_sync(PFSP_FULL, job0, s);
+            int jb = __shfl_sync(PFSP_FULL, job0, pos);
+            if constexpr (NW == 2) {
+                const int jf1 = __shfl_sync(PFSP_FULL, job1, s);
+                const int jb1 = __shfl_sync(PFSP_FULL, job1, pos);
+                jf = s >= 32 ? jf1 : jf;
+                jb = pos >= 32 ? jb1 : jb;
+            }
+            if (s < d1) {
+                const int p = prow[jf];
+                const int Pk = Prow[jf];
+                int x = Fk - Pk + p;
+#pragma unroll
+                for (int o = 0; o < LG; ++o) x = max(x, __shfl_up_sync(PFSP_FULL, x, 1 << o));
+                Fk = Pk + x;
+                Sk += p;
+            }
+            if (s < d2) {
+                const int p = prow[jb];
+                const int Qk = Qrow[jb];
+                int x = Bk - Qk + p;
+#pragma unroll
+                for (int o = 0; o < LG; ++o) x = max(x, shfl_down_clamped(x, 1 << o, m - 1));
+                Bk = Qk + x;
+                Sk += p;
+            }
+        }
+    } else {
         const int stepsF = d1 > 0 ? d1 + m - 1 : 0;
         const int stepsB = d2 > 0 ? d2 + m - 1 : 0;
         const int steps = max(stepsF, stepsB);
@@ -254,7 +350,7 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
                 if (want2) {
                     W.G[c * mp + kf].x = gf;
                     W.G[c * mp + kb].y = gb;
-                    W.Bb[c * mp + kb] = b;
+                    W.Bb[c * mp + kb] = b - Pb.z;
                 }
             }
             out.lb1f[h] = lf;
@@ -268,27 +364,30 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
 }
 
 // One slot of the LB2 sweep for this lane's pair: walk the unscheduled jobs
-// (bit mask Upos of their positions in the pair's Johnson order, lowest bit
-// first) recording the prefix constant PB before each job, then backwards
-// composing the suffix maps, leaving C of every child (compact index c) in
-// W.Cb[c][lane].  Both walks take four jobs per round: the next positions
-// come off the mask by clearing its lowest bit (a two-operation chain), so
-// the table loads of the four jobs issue together instead of each waiting
-// for the previous job's.
+// (bit mask Upos of their positions in the pair's Johnson order, walked in
+// ascending position order by next_bit) recording the prefix constant PB
+// before each job, then backwards composing the suffix maps, leaving C of
+// every child (compact index c) plus Bl in W.Cb[c][lane].  The suffix walk
+// starts from the map (Bl, -inf) instead of the identity (0, -inf): every
+// constant it builds, and so C, comes out shifted by Bl (the parent's B_l),
+// which saves the evaluation an addition.  Both walks take four jobs per
+// round: the next positions come off the mask by dropping the walked bit (a
+// short chain), so the table loads of the four jobs issue together
+// instead of each waiting for the previous job's.
 template <int NW>
 __device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, int2 *E, umask_t<NW> Upos, int u,
-                                          int lane) {
+                                          int lane, int Bl) {
     int PB = kNegInf;
     for (int i = 0; i < u; i += 4) {
         int t[4];
         int2 e[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            t[q] = lowest_bit<NW>(Upos);  // -1 once the mask is empty
-            Upos &= Upos - 1;
+            t[q] = next_bit<NW>(Upos);  // -1 once the mask is empty
+            Upos = drop_bit<NW>(Upos, t[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = (i + q < u) ? pt[t[q] * 32] : make_int2(0, kNegInf);
+        for (int q = 0; q < 4; ++q) e[q] = (i + q < u) ? pt[pos_of_bit<NW>(t[q]) * 32] : make_int2(0, kNegInf);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             // rows u..round4(u)-1 get a record that the backward walk never reads
@@ -297,13 +396,13 @@ __device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, 
             PB = addmax(PB, e[q].x >> 8, e[q].y);  // identity for a padding step
         }
     }
-    int SA = 0, SB = kNegInf;
+    int SA = Bl, SB = kNegInf;
     for (int i = u - 1; i >= 0; i -= 4) {
         int2 q[4], e[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) q[r] = (i - r >= 0) ? E[(i - r) * 32] : make_int2(0, 0);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) e[r] = (i - r >= 0) ? pt[(q[r].y & 0xff) * 32] : make_int2(0, kNegInf);
+        for (int r = 0; r < 4; ++r) e[r] = (i - r >= 0) ? pt[pos_of_bit<NW>(q[r].y & 0xff) * 32] : make_int2(0, kNegInf);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (i - r >= 0) {
@@ -319,7 +418,8 @@ __device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, 
 // constant of step i in PBr[i] and the position of its job in byte i % 4 of
 // tb[i / 4].  All indices below are compile-time constants.
 
-// Backward steps 4G+3 .. 4G (those below u) of scan_slot_reg.
+// Backward steps 4G+3 .. 4G (those below u) of scan_slot_reg (n <= 32:
+// masks of 32 bits).
 template <int G>
 __device__ __forceinline__ void scan_back_group(const WarpScratch &W, const int2 *pt, const int (&PBr)[kRegWalk],
                                                 const unsigned (&tb)[kRegWalk / 4], int u, int lane, int &SA,
@@ -329,7 +429,7 @@ __device__ __forceinline__ void scan_back_group(const WarpScratch &W, const int2
 #pragma unroll
     for (int r = 3; r >= 0; --r) {
         const int t = (tb[G] >> (8 * r)) & 0xff;
-        e[r] = (4 * G + r < u) ? pt[t * 32] : make_int2(0, kNegInf);
+        e[r] = (4 * G + r < u) ? pt[pos_of_bit<1>(t) * 32] : make_int2(0, kNegInf);
     }
 #pragma unroll
     for (int r = 3; r >= 0; --r) c[r] = W.cidx[e[r].x & 0xff];
@@ -349,7 +449,8 @@ __device__ __forceinline__ void scan_back_group(const WarpScratch &W, const int2
 // entered at the group holding step u - 1.
 template <int NW>
 __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *pt, umask_t<NW> Upos, int u,
-                                              int lane) {
+                                              int lane, int Bl) {
+    static_assert(NW == 1, "register walks need n <= 32");
     int PBr[kRegWalk];
     unsigned tb[kRegWalk / 4];
     int PB = kNegInf;
@@ -360,11 +461,11 @@ __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *
         int2 e[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            t[q] = lowest_bit<NW>(Upos);  // -1 once the mask is empty
-            Upos &= Upos - 1;
+            t[q] = next_bit<NW>(Upos);  // -1 once the mask is empty
+            Upos = drop_bit<NW>(Upos, t[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = (4 * g + q < u) ? pt[t[q] * 32] : make_int2(0, kNegInf);
+        for (int q = 0; q < 4; ++q) e[q] = (4 * g + q < u) ? pt[pos_of_bit<NW>(t[q]) * 32] : make_int2(0, kNegInf);
         tb[g] = (unsigned)(t[0] & 0xff) | ((unsigned)(t[1] & 0xff) << 8) | ((unsigned)(t[2] & 0xff) << 16) |
                 ((unsigned)(t[3] & 0xff) << 24);
 #pragma unroll
@@ -373,7 +474,7 @@ __device__ __forceinline__ void scan_slot_reg(const WarpScratch &W, const int2 *
             PB = addmax(PB, e[q].x >> 8, e[q].y);  // identity for a padding step
         }
     }
-    int SA = 0, SB = kNegInf;
+    int SA = Bl, SB = kNegInf;  // shifted by Bl, as in scan_slot
     static_assert(kRegWalk == 20, "the entry switch below lists kRegWalk / 4 groups");
     switch ((u + 3) >> 2) {
         case 5: scan_back_group<4>(W, pt, PBr, tb, u, lane, SA, SB); [[fallthrough]];
@@ -458,16 +559,27 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     int2 *E = RW ? nullptr : W.E + lane;
     // positions of the unscheduled jobs in each pair's Johnson order, one
     // bit mask per slot; with a compile-time slot count all masks are built
-    // in a single walk over the unscheduled jobs
+    // in a single walk over the unscheduled jobs, or, when fewer jobs are
+    // scheduled than not, over the scheduled ones (their positions, taken
+    // out of the mask of all n positions)
     constexpr int SC = MT ? (MT * (MT - 1) / 2 + 31) / 32 : 1;
     mask_t UposAll[SC];
     if constexpr (MT > 0) {
 #pragma unroll
         for (int q = 0; q < SC; ++q) UposAll[q] = 0;
-        for (mask_t um = U; um; um &= um - 1) {
-            const uint8_t *rj = T.rank + (size_t)lowest_bit<NW>(um) * SC * 32 + lane;
+        const bool flip = 2 * u > n;
+        const mask_t jobs_n = (n >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << n) - 1);
+        for (mask_t um = flip ? (jobs_n & ~U) : U; um;) {
+            const int j = next_bit<NW>(um);
+            um = drop_bit<NW>(um, j);
+            const uint8_t *rj = T.rank + (size_t)j * SC * 32 + lane;
 #pragma unroll
             for (int q = 0; q < SC; ++q) UposAll[q] |= mask_t(1) << rj[q * 32];
+        }
+        if (flip) {
+            const mask_t all_pos = all_positions<NW>(n);
+#pragma unroll
+            for (int q = 0; q < SC; ++q) UposAll[q] ^= all_pos;
         }
     }
     int swept = 0;
@@ -492,12 +604,18 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
             }
         } else {
             Upos = 0;
-            for (mask_t um = U; um; um &= um - 1)
-                Upos |= mask_t(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + sl) * 32 + lane];
+            for (mask_t um = U; um;) {
+                const int j = next_bit<NW>(um);
+                um = drop_bit<NW>(um, j);
+                Upos |= mask_t(1) << T.rank[((size_t)j * T.S + sl) * 32 + lane];
+            }
         }
-        if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane);
-        else scan_slot<NW>(W, pt, E, Upos, u, lane);
-        // evaluation: the third pair term of every evaluated child
+        if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane, Bl);
+        else scan_slot<NW>(W, pt, E, Upos, u, lane, Bl);
+        // evaluation: the third pair term of every evaluated child,
+        // F_k + R_k + C + B_l of the child; Cb holds C + B_l(parent) and Bb
+        // holds B'_l - B_l(parent), so the forward child's term is G.x + Cb
+        // and the backward child's G.y + Cb + Bb
         const int2 *gk = W.G + k;
         const int *bb = W.Bb + l;
         const int *cb = W.Cb + lane;
@@ -513,7 +631,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
                     if (SURV && !((ev >> c) & 1)) continue;  // warp-uniform
                     const int C = cb[c * 32];
                     const int2 g = gk[c * mp];
-                    accf[c] = max(accf[c], g.x + C + Bl);
+                    accf[c] = addmax(g.x, C, accf[c]);
                     accb[c] = max(accb[c], g.y + C + bb[c * mp]);
                 }
             }
@@ -523,7 +641,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
                 const int C = cb[c * 32];
                 const int2 g = gk[c * mp];
                 int2 v = W.Acc[c * 32 + lane];
-                v.x = max(v.x, g.x + C + Bl);
+                v.x = addmax(g.x, C, v.x);
                 v.y = max(v.y, g.y + C + bb[c * mp]);
                 W.Acc[c * 32 + lane] = v;
             }
@@ -629,11 +747,11 @@ __device__ __forceinline__ int decompose_lb2(const SmemTables &T, const WarpScra
 }
 
 // Both phases: the bounds of all 2u children of the node.
-template <int NW, int MT, int WALK = 0>
+template <int NW, int MT, int WALK = 0, bool SCAN = false>
 __device__ __forceinline__ void decompose_node(const SmemTables &T, const WarpScratch &W, int n, int m_rt,
                                                int S_rt, int kind, int job0, int job1, int d1, int d2,
                                                ChildBounds<NW> &out) {
-    decompose_lb1<NW, MT>(T, W, n, m_rt, kind, job0, job1, d1, d2, out);
+    decompose_lb1<NW, MT, SCAN>(T, W, n, m_rt, kind, job0, job1, d1, d2, out);
     if ((kind & PFSP_LB2) && (MT ? MT : m_rt) >= 2)
         decompose_lb2<NW, MT, WALK>(T, W, n, m_rt, S_rt, out, INT_MAX, false, nullptr);
 }

@@ -24,7 +24,7 @@ struct BoundArgs {
     const int32_t *tab;
     int tab_words;
     int n, m, S;
-    int off_pm, off_tot, off_kl, off_rank, off_ptab;
+    int off_pm, off_tot, off_pq, off_kl, off_rank, off_ptab;
     int warp_words;
     int kind;
     pfsp_node_summary *summary;  // reduce mode: one per node
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
 
     SmemTables T;
     T.pm = smem + a.off_pm;
+    T.pq = smem + a.off_pq;
     T.tot = smem + a.off_tot;
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 1) bound_batch_kernel(Bound
             continue;
         }
         ChildBounds<NW> cb;
-        decompose_node<NW, MT, WALK>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
+        decompose_node<NW, MT, WALK, true>(T, W, n, m, a.S, a.kind, job0, job1, d1, d2, cb);
         if constexpr (REDUCE) {
             write_summary<NW>(cb, W, (a.kind & PFSP_LB2) != 0, a.ub, a.summary + node);
             __syncwarp();
@@ -259,6 +260,7 @@ cudaError_t launch_bound_batch(const pfsp_instance *inst, int kind, long long nu
     a.S = (kind & PFSP_LB2) ? L.Ssweep : 0;
     a.off_pm = L.off_pm;
     a.off_tot = L.off_tot;
+    a.off_pq = L.off_pq;
     a.off_kl = L.off_kl;
     a.off_rank = L.off_rank;
     a.off_ptab = L.off_ptab;

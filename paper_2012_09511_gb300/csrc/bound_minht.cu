@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(8 * 32, 1) bound_minht_kernel(MinhtArgs a) {
     stage_tables(smem, a.tab, a.tab_words, &bar);
     SmemTables T;
     T.pm = smem + a.off_pm;
+    T.pq = nullptr;  // the max-scan fronts are the bounding kernel's
     T.tot = smem + a.off_tot;
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);

@@ -36,7 +36,8 @@ TableLayout table_layout(int n, int m) {
     L.nj = (n + 3) & ~3;
     L.off_pm = 0;
     L.off_tot = L.off_pm + m * L.nj;
-    L.off_kl = L.off_tot + 32;
+    L.off_pq = L.off_tot + 32;
+    L.off_kl = L.off_pq + 2 * m * L.nj;
     L.off_rank = L.off_kl + L.S * 32;
     L.off_ptab = L.off_rank + L.S * n * 8;
     L.words = L.off_ptab + 2 * L.S * n * 32;
@@ -81,13 +82,24 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
         for (int j = 0; j < n; ++j) t += p[j * m + k];
         blob[L.off_tot + k] = t;
     }
+    for (int j = 0; j < n; ++j) {
+        int32_t pre = 0, suf = 0;
+        for (int k = 0; k < m; ++k) {
+            pre += p[j * m + k];
+            suf += p[j * m + (m - 1 - k)];
+            blob[L.off_pq + k * L.nj + j] = pre;
+            blob[L.off_pq + (2 * m - 1 - k) * L.nj + j] = suf;
+        }
+    }
+    // bit of position t in the kernels' position masks: 31 - t for n <= 32, t above
+    auto pos_bit = [n](int t) { return n <= 32 ? 31 - t : t; };
     int2 *ptab = reinterpret_cast<int2 *>(blob.data() + L.off_ptab);
     uint8_t *rank = reinterpret_cast<uint8_t *>(blob.data() + L.off_rank);
     for (int s = 0; s < L.S; ++s)
         for (int t = 0; t < n; ++t)
             for (int lane = 0; lane < 32; ++lane) {
                 ptab[(s * n + t) * 32 + lane] = make_int2(t, kNegInf);
-                rank[(t * L.S + s) * 32 + lane] = (uint8_t)t;
+                rank[(t * L.S + s) * 32 + lane] = (uint8_t)pos_bit(t);
             }
     int q = 0;
     std::vector<int> lag(n);
@@ -107,7 +119,7 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
                 int a = p[j * m + l] - p[j * m + k];
                 int b = lag[j] + p[j * m + l];
                 ptab[(s * n + t) * 32 + lane] = make_int2((int)((unsigned)a << 8) | j, b);
-                rank[(j * L.S + s) * 32 + lane] = (uint8_t)t;
+                rank[(j * L.S + s) * 32 + lane] = (uint8_t)pos_bit(t);
             }
         }
 }
@@ -190,7 +202,8 @@ int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out) {
     }
     memcpy(inst->p_host, p, sizeof(int32_t) * n * m);
     inst->lay = table_layout(n, m);
-    inst->lb2_ok = (size_t)inst->lay.words * 4 <= (size_t)kMaxTableBytes;
+    // the limit counts the LB2 tables proper (the prefix/suffix sums add 2 m nj words)
+    inst->lb2_ok = (size_t)(inst->lay.words - (inst->lay.off_kl - inst->lay.off_pq)) * 4 <= (size_t)kMaxTableBytes;
     std::vector<int32_t> blob;
     build_tables(inst->lay, p, blob, nullptr, inst->lay.P);
     cudaError_t e = cudaMalloc(&inst->d_tab, blob.size() * sizeof(int32_t));

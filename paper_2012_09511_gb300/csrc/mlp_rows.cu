@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
     stage_tables(smem, a.tab, a.tab_words, &bar);
     SmemTables T;
     T.pm = smem + a.off_pm;
+    T.pq = nullptr;  // the max-scan fronts are the bounding kernel's
     T.tot = smem + a.off_tot;
     T.kl = smem + a.off_kl;
     T.rank = reinterpret_cast<const uint8_t *>(smem + a.off_rank);
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
                     xf[m + k] = W.FRB[k].z * a.inv_scale;
                     xf[2 * m + k] = rc * a.inv_scale;
                     xb[k] = W.FRB[k].x * a.inv_scale;
-                    xb[m + k] = W.Bb[c * mp + k] * a.inv_scale;
+                    xb[m + k] = (W.Bb[c * mp + k] + W.FRB[k].z) * a.inv_scale;  // back after j
                     xb[2 * m + k] = rc * a.inv_scale;
                 }
                 Mk[(size_t)(1 + j) * a.O] = 1.0f;
@@ -137,13 +138,17 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
             const int k = klw & 0xff, l = klw >> 8;
             const int Bl = W.FRB[l].z;
             umask_t<NW> Upos = 0;
-            for (umask_t<NW> um = cb.U; um; um &= um - 1)
-                Upos |= umask_t<NW>(1) << T.rank[((size_t)lowest_bit<NW>(um) * T.S + s) * 32 + lane];
-            scan_slot<NW>(W, T.ptab + (size_t)s * n * 32 + lane, E, Upos, u, lane);
+            for (umask_t<NW> um = cb.U; um;) {
+                const int j = next_bit<NW>(um);
+                um = drop_bit<NW>(um, j);
+                Upos |= umask_t<NW>(1) << T.rank[((size_t)j * T.S + s) * 32 + lane];
+            }
+            scan_slot<NW>(W, T.ptab + (size_t)s * n * 32 + lane, E, Upos, u, lane, Bl);
             bool hit = false;
             for (int c = 0; c < u; ++c) {
+                // Cb holds C + B_l and Bb holds B'_l - B_l (parent's B_l)
                 const int C = W.Cb[c * 32 + lane];
-                const int ef = W.G[c * mp + k].x + C + Bl;
+                const int ef = W.G[c * mp + k].x + C;
                 const int eb = W.G[c * mp + k].y + C + W.Bb[c * mp + l];
                 hit |= (ef == lb[128 + c] && lb[128 + c] > lb[c]) || (eb == lb[192 + c] && lb[192 + c] > lb[64 + c]);
             }

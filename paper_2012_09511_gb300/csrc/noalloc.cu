@@ -74,7 +74,7 @@ extern "C" int pfsp_solve_noalloc(int n, int m, const int32_t *p, const pfsp_opt
     if (rc != PFSP_OK) return rc;
 
     const TableLayout L = table_layout(n, m);
-    if (opt->bound == PFSP_LB2 && (size_t)L.words * 4 > (size_t)kMaxTableBytes)
+    if (opt->bound == PFSP_LB2 && (size_t)(L.words - (L.off_kl - L.off_pq)) * 4 > (size_t)kMaxTableBytes)
         return set_error(PFSP_ERR_UNSUPPORTED, "LB2 tables exceed shared memory for this instance");
     std::vector<int32_t> blob;
     build_tables(L, p, blob, nullptr, L.P);

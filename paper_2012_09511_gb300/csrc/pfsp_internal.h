@@ -37,11 +37,14 @@ inline float default_min_steal(int n) {
 // copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):
 //   pm   [m][nj]       processing times by machine (nj = n rounded up to 4)
 //   tot  [32]          per-machine totals T_k = sum_j p[j][k]
+//   pq   [2][m][nj]    per job j: P_k = sum_{k' <= k} p[j][k'] (rows 0..m-1),
+//                      then Q_k = sum_{k' >= k} p[j][k'] (rows m..2m-1)
 //   kl   [S*32]        machine pair at slot position i: k | l << 8 (dummy: 0);
 //                      pairs sit in the instance's pair order (default: k = 0..m-2,
 //                      l = k+1..m-1), position i in slot i / 32, lane i % 32
-//   rank [n][S][32]    uint8: position t of job j in the Johnson order of
-//                      the lane's pair (dummy lanes: j)
+//   rank [n][S][32]    uint8: bit of job j in the lane's position masks:
+//                      31 - t (n <= 32) or t (n > 32), t its position in the
+//                      Johnson order of the lane's pair (dummy lanes: t = j)
 //   ptab [S][n][32]    int2 per (slot, position, lane): the lane's pair,
 //                      x = (a << 8) | job, y = b, for the job at position t of
 //                      the pair's Johnson order, with a = p[j][l] - p[j][k]
@@ -51,7 +54,7 @@ inline float default_min_steal(int n) {
 struct TableLayout {
     int n, m, P, S, nj;
     int Ssweep;  // slots holding the pairs LB2 uses (S unless LB2 uses a subset of the pairs)
-    int off_pm, off_tot, off_kl, off_rank, off_ptab, words;
+    int off_pm, off_tot, off_pq, off_kl, off_rank, off_ptab, words;
 };
 
 TableLayout table_layout(int n, int m);

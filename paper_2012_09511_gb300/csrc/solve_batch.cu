@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
         __syncthreads();
         SmemTables T;
         T.pm = smem + sa.off_pm;
+        T.pq = nullptr;  // the max-scan fronts are the bounding kernel's
         T.tot = smem + sa.off_tot;
         T.kl = smem + sa.off_kl;
         T.rank = reinterpret_cast<const uint8_t *>(smem + sa.off_rank);
