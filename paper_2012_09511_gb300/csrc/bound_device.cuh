@@ -55,7 +55,7 @@ struct SmemTables {
     const int *pm;        // [m][nj]
     const int *tot;       // [32]
     const int *kl;        // [S*32]
-    const int *pq;        // [2][m][nj] per job: P_k = sum of its times on machines 0..k, then Q_k = on k..m-1
+    const int *pq;        // int2 [n][m] per job and machine: {P_k, Q_k}, its times summed over 0..k and k..m-1
     const uint8_t *rank;  // [n][S][32] bit of job j in the lane's position masks (see pos_of_bit)
     const int2 *ptab;     // [S][n][32]
     int S;                // slots of the table layout (stride of rank); the sweep may use fewer
@@ -243,12 +243,15 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
         // unrolls to F'_k = P_k + max_{k' <= k} (F_k' - P_k' + p_jk') with P the
         // job's prefix sums over machines: one inclusive max-scan over lanes.
         // Prepending it to the back is the mirror image with the suffix sums
-        // Q: B'_k = Q_k + max_{k' >= k} (B_k' - Q_k' + p_jk').  The front's
+        // Q: B'_k = Q_k + max_{k' >= k} (B_k' - Q_k' + p_jk').  As
+        // P_k + Q_k = T_j + p_jk (T_j the job's total, P at the last machine),
+        // p_jk - P_k = Q_k - T_j and p_jk - Q_k = P_k - T_j: one 8-byte load of
+        // {P_k, Q_k} per lane and job (job-major rows, so the lanes read
+        // consecutive words) and T_j from the last machine's lane.  The front's
         // scan reads lower lanes only; the back's is clamped to the last
-        // machine, so lanes past it (rows of machine 0) feed no machine.
+        // machine, so lanes past it (entries of machine 0) feed no machine.
         constexpr int LG = MT == 0 ? 5 : MT <= 2 ? 1 : MT <= 4 ? 2 : MT <= 8 ? 3 : MT <= 16 ? 4 : 5;
-        const int kk = lane < m ? lane : 0;
-        const int *prow = T.pm + kk * nj, *Prow = T.pq + kk * nj, *Qrow = T.pq + (m + kk) * nj;
+        const int2 *pqrow = reinterpret_cast<const int2 *>(T.pq) + (lane < m ? lane : 0);
         const int steps = max(d1, d2);
         for (int s = 0; s < steps; ++s) {
             const int pos = n - 1 - s;
@@ -261,22 +264,22 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
                 jb = pos >= 32 ? jb1 : jb;
             }
             if (s < d1) {
-                const int p = prow[jf];
-                const int Pk = Prow[jf];
-                int x = Fk - Pk + p;
+                const int2 v = pqrow[jf * m];
+                const int Tj = __shfl_sync(PFSP_FULL, v.x, m - 1);
+                int x = Fk + v.y - Tj;
 #pragma unroll
                 for (int o = 0; o < LG; ++o) x = max(x, __shfl_up_sync(PFSP_FULL, x, 1 << o));
-                Fk = Pk + x;
-                Sk += p;
+                Fk = v.x + x;
+                Sk += v.x + v.y - Tj;
             }
             if (s < d2) {
-                const int p = prow[jb];
-                const int Qk = Qrow[jb];
-                int x = Bk - Qk + p;
+                const int2 v = pqrow[jb * m];
+                const int Tj = __shfl_sync(PFSP_FULL, v.x, m - 1);
+                int x = Bk + v.x - Tj;
 #pragma unroll
                 for (int o = 0; o < LG; ++o) x = max(x, shfl_down_clamped(x, 1 << o, m - 1));
-                Bk = Qk + x;
-                Sk += p;
+                Bk = v.y + x;
+                Sk += v.x + v.y - Tj;
             }
         }
     } else {
@@ -499,7 +502,10 @@ __device__ __forceinline__ umask_t<NW> warp_or(umask_t<NW> x) {
 
 // LB2 sweep over the slots.  NC > 0: the children's accumulators are NC
 // registers per direction (u <= NC); NC = 0: they live in W.Acc.  RW: the
-// walks keep their records in registers (u <= kRegWalk).
+// walks keep their records in registers (u <= kRegWalk).  LEAN: without the
+// first-slot peel and the masks built from the scheduled jobs, code that only
+// saves instructions (for kernels that inline several sweeps and would spill
+// with it).
 //
 // SURV with live_only (the early exit per child, cap < INT_MAX): a job both
 // of whose children have an LB1 at or above cap is not evaluated (a
@@ -512,7 +518,7 @@ __device__ __forceinline__ umask_t<NW> warp_or(umask_t<NW> x) {
 // decided after a slot (a pair term or its LB1 at or above cap) is not
 // evaluated in the later slots either.  Without live_only every child is
 // evaluated, as in the full sweep.
-template <int NW, int MT, int NC, bool RW, bool SURV = false>
+template <int NW, int MT, int NC, bool RW, bool SURV = false, bool LEAN = false>
 __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
                                          ChildBounds<NW> &out, int cap, bool slot_checks, const int *order,
                                          bool live_only = false) {
@@ -548,11 +554,19 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     // jobs evaluated in at least one slot: their accumulators are reduced
     // at the end (a job dropped at a slot check holds terms >= cap)
     const mask_t ev0 = ev;
+    // register accumulators: with PEEL the first slot swept assigns every
+    // accumulator that is read later (children below u), so none is set here.
+    // Not in the register-walk kernel of 20 or more machines, which sits at
+    // its 128-register cap (there the second copy of the evaluation costs a
+    // spill and was measured slower), not in the early-exit sweep (SURV) at 20
+    // machines, not with a run-time machine count, and not LEAN: those kernels
+    // spill with it.
+    constexpr bool PEEL = REGACC && !LEAN && MT > 0 && !((RW || SURV) && MT >= 20);
     int accf[REGACC ? NC : 1], accb[REGACC ? NC : 1];
-    if constexpr (REGACC) {
+    if constexpr (REGACC && !PEEL) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) { accf[c] = kNegInf; accb[c] = kNegInf; }
-    } else {
+    } else if constexpr (!REGACC) {
         for (int c = 0; c < u; ++c) W.Acc[c * 32 + lane] = make_int2(kNegInf, kNegInf);
     }
     const int u4 = (u + 3) & ~3;
@@ -567,7 +581,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
     if constexpr (MT > 0) {
 #pragma unroll
         for (int q = 0; q < SC; ++q) UposAll[q] = 0;
-        const bool flip = 2 * u > n;
+        const bool flip = !LEAN && 2 * u > n;
         const mask_t jobs_n = (n >= 8 * (int)sizeof(mask_t)) ? ~mask_t(0) : ((mask_t(1) << n) - 1);
         for (mask_t um = flip ? (jobs_n & ~U) : U; um;) {
             const int j = next_bit<NW>(um);
@@ -619,7 +633,42 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         const int2 *gk = W.G + k;
         const int *bb = W.Bb + l;
         const int *cb = W.Cb + lane;
-        if constexpr (REGACC) {
+        if constexpr (PEEL) {
+            if (si == 0) {
+                // every accumulator below u4 is written here (a child left
+                // out gets -inf), since the slot checks read them all
+#pragma unroll
+                for (int c0 = 0; c0 < NC; c0 += 4) {
+                    if (c0 >= u4) break;
+#pragma unroll
+                    for (int c = c0; c < c0 + 4; ++c) {
+                        if (SURV && !((ev >> c) & 1)) {  // warp-uniform
+                            accf[c] = kNegInf;
+                            accb[c] = kNegInf;
+                            continue;
+                        }
+                        const int C = cb[c * 32];
+                        const int2 g = gk[c * mp];
+                        accf[c] = g.x + C;
+                        accb[c] = g.y + C + bb[c * mp];
+                    }
+                }
+            } else {
+                const int cend = SURV ? ((ev ? 32 - __clz((unsigned)ev) : 0) + 3) & ~3 : u4;
+#pragma unroll
+                for (int c0 = 0; c0 < NC; c0 += 4) {
+                    if (c0 >= cend) break;
+#pragma unroll
+                    for (int c = c0; c < c0 + 4; ++c) {
+                        if (SURV && !((ev >> c) & 1)) continue;  // warp-uniform
+                        const int C = cb[c * 32];
+                        const int2 g = gk[c * mp];
+                        accf[c] = addmax(g.x, C, accf[c]);
+                        accb[c] = max(accb[c], g.y + C + bb[c * mp]);
+                    }
+                }
+            }
+        } else if constexpr (REGACC) {
             // children past the last evaluated one cost nothing (ev is a
             // 32-bit mask here: register accumulators hold u <= 32)
             const int cend = SURV ? ((ev ? 32 - __clz((unsigned)ev) : 0) + 3) & ~3 : u4;
@@ -732,18 +781,18 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
 // WALK = 0: walks through shared memory (any n).  Fixed per kernel, so that
 // a kernel carries the register demand of one path only.
 // Returns the number of 32-pair slots swept (fewer than S after an early exit).
-template <int NW, int MT, int WALK = 0, bool SURV = false>
+template <int NW, int MT, int WALK = 0, bool SURV = false, bool LEAN = false>
 __device__ __forceinline__ int decompose_lb2(const SmemTables &T, const WarpScratch &W, int n, int m_rt, int S_rt,
                                              ChildBounds<NW> &out, int cap, bool slot_checks, const int *order,
                                              bool live_only = false) {
     if (out.u == 0 || (MT ? MT : m_rt) < 2) return 0;
     static_assert(WALK == 0 || NW == 1, "register walks need n <= 32");
     if constexpr (WALK == 1)
-        return lb2_sweep<NW, MT, kRegWalk, true, SURV>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order,
-                                                         live_only);
+        return lb2_sweep<NW, MT, kRegWalk, true, SURV, LEAN>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order,
+                                                               live_only);
     else
-        return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false, SURV>(T, W, n, m_rt, S_rt, out, cap, slot_checks, order,
-                                                                  live_only);
+        return lb2_sweep<NW, MT, NW == 1 ? 32 : 0, false, SURV, LEAN>(T, W, n, m_rt, S_rt, out, cap, slot_checks,
+                                                                        order, live_only);
 }
 
 // Both phases: the bounds of all 2u children of the node.

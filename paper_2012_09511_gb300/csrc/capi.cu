@@ -37,7 +37,7 @@ TableLayout table_layout(int n, int m) {
     L.off_pm = 0;
     L.off_tot = L.off_pm + m * L.nj;
     L.off_pq = L.off_tot + 32;
-    L.off_kl = L.off_pq + 2 * m * L.nj;
+    L.off_kl = L.off_pq + ((2 * n * m + 3) & ~3);
     L.off_rank = L.off_kl + L.S * 32;
     L.off_ptab = L.off_rank + L.S * n * 8;
     L.words = L.off_ptab + 2 * L.S * n * 32;
@@ -87,8 +87,8 @@ void build_tables(const TableLayout &L, const int32_t *p, std::vector<int32_t> &
         for (int k = 0; k < m; ++k) {
             pre += p[j * m + k];
             suf += p[j * m + (m - 1 - k)];
-            blob[L.off_pq + k * L.nj + j] = pre;
-            blob[L.off_pq + (2 * m - 1 - k) * L.nj + j] = suf;
+            blob[L.off_pq + 2 * (j * m + k)] = pre;                // P_k
+            blob[L.off_pq + 2 * (j * m + (m - 1 - k)) + 1] = suf;  // Q_{m-1-k}
         }
     }
     // bit of position t in the kernels' position masks: 31 - t for n <= 32, t above
@@ -202,7 +202,7 @@ int pfsp_load_instance(int n, int m, const int32_t *p, pfsp_instance **out) {
     }
     memcpy(inst->p_host, p, sizeof(int32_t) * n * m);
     inst->lay = table_layout(n, m);
-    // the limit counts the LB2 tables proper (the prefix/suffix sums add 2 m nj words)
+    // the limit counts the LB2 tables proper (the prefix/suffix sums add about 2 n m words)
     inst->lb2_ok = (size_t)(inst->lay.words - (inst->lay.off_kl - inst->lay.off_pq)) * 4 <= (size_t)kMaxTableBytes;
     std::vector<int32_t> blob;
     build_tables(inst->lay, p, blob, nullptr, inst->lay.P);

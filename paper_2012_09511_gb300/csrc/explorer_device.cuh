@@ -66,9 +66,14 @@ struct Explorer {
     // phase timers and decomposition traces: compiled out of the fast kernels
     // (plain LB2, LB1-only, and the one beside the heuristic threads), which
     // run solves that ask for neither
-    static constexpr bool DIAG = KIND != kKindPlain && KIND != kKindLb1 && KIND != kKindCoop && KIND != kKindEE;
-    // early exit of the LB2 sweep: compiled out of the plain kernel
-    static constexpr bool EARLY = KIND != kKindPlain && KIND != kKindLb1;
+    static constexpr bool DIAG = KIND != kKindPlain && KIND != kKindBatch && KIND != kKindLb1 && KIND != kKindCoop &&
+                                 KIND != kKindEE;
+    // early exit of the LB2 sweep: compiled out of the plain kernels
+    static constexpr bool EARLY = KIND != kKindPlain && KIND != kKindBatch && KIND != kKindLb1;
+    // the batched pool inlines one explorer per machine count into a single
+    // kernel: its sweep leaves out the code that only saves instructions
+    // (lb2_sweep's LEAN), which there costs spills
+    static constexpr bool LEAN = KIND == kKindBatch;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -445,7 +450,7 @@ struct Explorer {
                 EARLY ? decompose_lb2<NW, MT, 0, true>(T, W, n, m, S, cb, ee_cap,
                                                        (a.learned & PFSP_EARLY_EXIT_SLOTS) != 0, order,
                                                        (a.learned & PFSP_EARLY_EXIT_CHILDREN) != 0)
-                      : decompose_lb2<NW, MT>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
+                      : decompose_lb2<NW, MT, 0, false, LEAN>(T, W, n, m, S, cb, INT_MAX, false, nullptr);
             if (counted) st.slots += swept;
         }
         tick(counted ? kPhLB2 : kPhInit);

@@ -37,8 +37,9 @@ inline float default_min_steal(int n) {
 // copies into its shared memory.  Word offsets are multiples of 4 (16 bytes):
 //   pm   [m][nj]       processing times by machine (nj = n rounded up to 4)
 //   tot  [32]          per-machine totals T_k = sum_j p[j][k]
-//   pq   [2][m][nj]    per job j: P_k = sum_{k' <= k} p[j][k'] (rows 0..m-1),
-//                      then Q_k = sum_{k' >= k} p[j][k'] (rows m..2m-1)
+//   pq   [n][m] int2  per job j and machine k: {P_k, Q_k} with
+//                      P_k = sum_{k' <= k} p[j][k'], Q_k = sum_{k' >= k} p[j][k']
+//                      (2 n m words, rounded up to a multiple of 4)
 //   kl   [S*32]        machine pair at slot position i: k | l << 8 (dummy: 0);
 //                      pairs sit in the instance's pair order (default: k = 0..m-2,
 //                      l = k+1..m-1), position i in slot i / 32, lane i % 32

@@ -223,10 +223,10 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
         }
         __syncwarp();
         switch (sa.m) {
-            case 5: run_explorer<NW, 5>(sa, T, Ws, X, me, nullptr); break;
-            case 10: run_explorer<NW, 10>(sa, T, Ws, X, me, nullptr); break;
-            case 20: run_explorer<NW, 20>(sa, T, Ws, X, me, nullptr); break;
-            default: run_explorer<NW, 0>(sa, T, Ws, X, me, nullptr); break;
+            case 5: run_explorer<NW, 5, kKindBatch>(sa, T, Ws, X, me, nullptr); break;
+            case 10: run_explorer<NW, 10, kKindBatch>(sa, T, Ws, X, me, nullptr); break;
+            case 20: run_explorer<NW, 20, kKindBatch>(sa, T, Ws, X, me, nullptr); break;
+            default: run_explorer<NW, 0, kKindBatch>(sa, T, Ws, X, me, nullptr); break;
         }
         if (lane == 0) atomicExch(b.inst_of + me, -1);
         __syncthreads();

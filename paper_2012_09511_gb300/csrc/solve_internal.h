@@ -29,6 +29,7 @@ constexpr int kKindMinht = 3;    // with the heads and tails refinement of LB1
 constexpr int kKindLb1 = 4;      // LB1 solves: the loop carries no LB2 code
 constexpr int kKindDiag = 5;     // with phase timers and decomposition traces (both bounds)
 constexpr int kKindEE = 6;       // with the early exit of the LB2 sweep (PFSP_EARLY_EXIT)
+constexpr int kKindBatch = 7;    // the paper's solver inside the batched pool (lean LB2 sweep)
 
 // Phases of an explorer's loop whose SM clock cycles are summed per solve
 // (pfsp_stats_t.phase_cycles) when the timers are on.  Each reading of the SM
