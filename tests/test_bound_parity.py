@@ -3,7 +3,8 @@
 Every child bound (LB1 and LB2, forward and backward) must be bit-identical
 to the oracle's from-scratch value; scheduled jobs must read -1.  Cases span
 several warps and CTAs, ragged tails, both job-mask widths (n <= 32 and
-n > 32), every m from 1 to 32, exhaustive node sets of tiny instances, the
+n > 32), every m from 1 to 32, nodes of every depth (both forms of the
+front/back computation), exhaustive node sets of tiny instances, the
 degenerate depths, and sampled nodes of the full 4,194,304-node batch of the
 20 x 20 bounding benchmark in the launch configuration the benchmark times.
 """
@@ -45,6 +46,20 @@ def _compare(pf, p, perm, d1, d2, threads=8):
 def test_random_nodes_bit_exact(pf, n, m, count):
     p = inputs.make_instance(n, m, 1000 + n * 64 + m)
     perm, d1, d2 = inputs.random_nodes(n, count, seed=n + m, dmax=min(10, n))
+    _compare(pf, p, perm, d1, d2)
+
+
+@pytest.mark.parametrize("n,m,count,dmax", [
+    (40, 20, 2000, 10), (50, 17, 1500, 10), (64, 16, 800, 10),  # 64-bit masks, fronts by max-scans
+    (50, 20, 1500, 45), (64, 20, 600, 60), (33, 25, 1000, 30),  # positions past 32 in both directions
+    (20, 20, 6000, 20), (32, 32, 1500, 32), (24, 18, 3000, 24),  # deep and shallow nodes alike
+])
+def test_deep_nodes_and_many_machines_bit_exact(pf, n, m, count, dmax):
+    # at 16 machines or more the kernel builds fronts and backs by max-scans
+    # over the machines, one per scheduled job; nodes of every depth reach
+    # the jobs held by the second register of each lane (positions >= 32)
+    p = inputs.make_instance(n, m, 7000 + n * 64 + m)
+    perm, d1, d2 = inputs.random_nodes(n, count, seed=3 * n + m, dmax=dmax)
     _compare(pf, p, perm, d1, d2)
 
 
