@@ -652,9 +652,42 @@ def run_native(args):
         out["batch"] = batch_leg(pfsp)
     if not args.no_learned and ws == 1:
         out["learned"] = learned_leg(pfsp)
+    out["summary"] = summary_of(out)  # last key: the end of the line carries the other legs' headlines
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def summary_of(out):
+    """The headline figures of every leg, compact, for the end of the line."""
+    def r(x, nd=4):
+        return None if x is None else round(float(x), nd)
+
+    sm = {"bounding": {"children_per_s": r(out["value"] / 1e9, 3), "unit": "1e9 children/s",
+                       "kernel_ms": r(out["roofline"]["kernel_ms"], 3), "roofline_frac": r(out["roofline"]["frac"]),
+                       "e2e_children_per_s": r(out["e2e"]["value"] / 1e9, 3)}}
+    if "reduce" in out:
+        sm["bounding"]["reduce_children_per_s"] = r(out["reduce"]["value"] / 1e9, 3)
+    if "solve" in out:
+        s = out["solve"]
+        sm["time_to_proof_20x10"] = {"seconds": r(s["time_to_proof_s"], 5), "nodes": s["decomposed_nodes"],
+                                     "nodes_per_s": r(s["decomposed_nodes_per_s"] / 1e6, 1), "unit": "1e6 nodes/s",
+                                     "counts_match_oracle": s["counts_and_optima_match_oracle"]}
+        if "lb1_30x15_rate" in s:
+            sm["lb1_30x15_nodes_per_s"] = r(s["lb1_30x15_rate"]["decomposed_nodes_per_s"] / 1e6, 1)
+    if "batch" in out:
+        b = out["batch"]
+        sm["batch_256"] = {"kernel_s": r(b["kernel_s"], 3), "nodes_per_s": r(b["decomposed_nodes_per_s"] / 1e6, 1),
+                           "all_optimal": b["all_optimal"], "optima_checked": b["optima_checked_against_oracle"],
+                           "optima_match_oracle": b["optima_match_oracle"]}
+    if "learned" in out:
+        lp = out["learned"].get("proofs", {})
+        sm["learned_vs_plain"] = {
+            shape: {rule: {"speedup_kernel": r(v[rule]["speedup_kernel"], 3),
+                           "node_ratio": r(v[rule]["node_ratio_learned_over_plain"], 4)}
+                    for rule in ("minmin_capped", "minmin") if rule in v}
+            for shape, v in lp.items()}
+    return sm
 
 
 def main():
