@@ -104,7 +104,9 @@ void pfsp_free_instance(pfsp_instance *inst);
  * Errors: PFSP_ERR_INVALID (NULL pointer for a requested output or input,
  * d1 + d2 > n, kind without LB1 or LB2 or with other bits),
  * PFSP_ERR_UNSUPPORTED (LB2 tables too large),
- * PFSP_ERR_OOM, PFSP_ERR_CUDA.
+ * PFSP_ERR_OOM, PFSP_ERR_CUDA.  On an error the outputs are not written
+ * (the depths are validated while the first chunks of the batch are bounded
+ * on the device, and results are copied back only after that).
  */
 int pfsp_bound_batch(const pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm,
                      const uint8_t *d1, const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out);

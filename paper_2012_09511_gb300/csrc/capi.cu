@@ -313,9 +313,80 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
 // NULL) or one summary per node (reduce mode, survivors below ub).
 static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm, const uint8_t *d1,
                       const uint8_t *d2, int32_t *lb1_out, int32_t *lb2_out, pfsp_node_summary *summary, int ub) {
-    int rc = PFSP_OK;
     auto t0 = std::chrono::steady_clock::now();
     const int n = inst->n;
+    if (num_nodes == 0) return PFSP_OK;
+    // Chunks of the batch alternate between two streams, so that the copies
+    // of one chunk (nodes in, both bound arrays out) overlap the kernel of the
+    // other; each stream reuses its own device buffers in stream order.
+    const int64_t chunk = std::min<int64_t>(num_nodes, kBoundChunk);
+    const int64_t nchunks = (num_nodes + chunk - 1) / chunk;
+    const int nst = nchunks > 1 ? 2 : 1;
+    const size_t in_bytes = (size_t)chunk * (n + 2);
+    const size_t out_bytes = summary ? (size_t)chunk * sizeof(pfsp_node_summary) : (size_t)chunk * 2 * n * sizeof(int32_t);
+    const bool want1 = !summary && (kind & PFSP_LB1), want2 = !summary && (kind & PFSP_LB2);
+    const size_t off_out1 = (in_bytes + 255) & ~(size_t)255;
+    const size_t off_out2 = off_out1 + (((want1 || summary) ? out_bytes : 0) + 255) / 256 * 256;
+    const size_t per_stream = (off_out2 + (want2 ? out_bytes : 0) + 255) / 256 * 256;
+    int rc = ensure_scratch(inst, per_stream * nst);
+    if (rc != PFSP_OK) return rc;
+    cudaStream_t st[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> evs((size_t)nchunks * 2, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < nst && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking);
+    for (size_t q = 0; q < evs.size() && e == cudaSuccess; ++q) e = cudaEventCreate(&evs[q]);
+    struct Bufs {
+        uint8_t *perm, *d1, *d2;
+        int32_t *o1, *o2;
+        pfsp_node_summary *os;
+    };
+    auto bufs = [&](int64_t c) {
+        char *base = (char *)inst->d_scratch + per_stream * (size_t)(c % nst);
+        const int64_t cn = std::min<int64_t>(chunk, num_nodes - c * chunk);
+        Bufs b;
+        b.perm = (uint8_t *)base;
+        b.d1 = b.perm + (size_t)cn * n;
+        b.d2 = b.d1 + cn;
+        b.o1 = want1 ? (int32_t *)(base + off_out1) : nullptr;
+        b.o2 = want2 ? (int32_t *)(base + off_out2) : nullptr;
+        b.os = summary ? (pfsp_node_summary *)(base + off_out1) : nullptr;
+        return b;
+    };
+    // nodes in and the kernel of chunk c
+    auto front = [&](int64_t c) {
+        const int q = (int)(c % nst);
+        const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
+        const Bufs b = bufs(c);
+        cudaError_t r = cudaMemcpyAsync(b.perm, perm + (size_t)off * n, (size_t)cn * n, cudaMemcpyHostToDevice, st[q]);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(b.d1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(b.d2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
+        if (r == cudaSuccess) r = cudaEventRecord(evs[2 * c], st[q]);
+        if (r == cudaSuccess)
+            r = summary ? launch_bound_batch(inst, kind, cn, b.perm, b.d1, b.d2, nullptr, nullptr, st[q], b.os, ub)
+                        : launch_bounds(inst, kind, cn, b.perm, b.d1, b.d2, b.o1, b.o2, st[q]);
+        if (r == cudaSuccess) r = cudaEventRecord(evs[2 * c + 1], st[q]);
+        return r;
+    };
+    // the results of chunk c back to the caller's buffers
+    auto back = [&](int64_t c) {
+        const int q = (int)(c % nst);
+        const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
+        const Bufs b = bufs(c);
+        const size_t ob = (size_t)cn * 2 * n * sizeof(int32_t);
+        cudaError_t r = cudaSuccess;
+        if (b.os)
+            r = cudaMemcpyAsync(summary + off, b.os, (size_t)cn * sizeof(pfsp_node_summary), cudaMemcpyDeviceToHost,
+                                st[q]);
+        if (r == cudaSuccess && b.o1) r = cudaMemcpyAsync(lb1_out + (size_t)off * 2 * n, b.o1, ob, cudaMemcpyDeviceToHost, st[q]);
+        if (r == cudaSuccess && b.o2) r = cudaMemcpyAsync(lb2_out + (size_t)off * 2 * n, b.o2, ob, cudaMemcpyDeviceToHost, st[q]);
+        return r;
+    };
+    // The first chunk of each stream goes in before the host validates the
+    // depths, so that the validation overlaps their copies and kernels; no
+    // result is copied back before it passes, so a rejected batch leaves the
+    // caller's buffers untouched (the kernel itself writes -1 for a node with
+    // d1 + d2 > n and reads nothing past its row).
+    for (int64_t c = 0; c < nst && e == cudaSuccess; ++c) e = front(c);
     // one pass over the depths: validation and the children count (a plain
     // reduction the host compiler vectorises)
     uint64_t depth_sum = 0;
@@ -330,57 +401,18 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
         }
         depth_sum += part;
     }
-    if (dmax > (unsigned)n)
+    if (dmax > (unsigned)n) {
         for (int64_t i = 0; i < num_nodes; ++i)
-            if ((int)d1[i] + (int)d2[i] > n)
-                return set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i],
-                                 n);
-    if (num_nodes == 0) return PFSP_OK;
-    // Chunks of the batch alternate between two streams, so that the copies
-    // of one chunk (nodes in, both bound arrays out) overlap the kernel of the
-    // other; each stream reuses its own device buffers in stream order.
-    const int64_t chunk = std::min<int64_t>(num_nodes, kBoundChunk);
-    const int64_t nchunks = (num_nodes + chunk - 1) / chunk;
-    const int nst = nchunks > 1 ? 2 : 1;
-    const size_t in_bytes = (size_t)chunk * (n + 2);
-    const size_t out_bytes = summary ? (size_t)chunk * sizeof(pfsp_node_summary) : (size_t)chunk * 2 * n * sizeof(int32_t);
-    const bool want1 = !summary && (kind & PFSP_LB1), want2 = !summary && (kind & PFSP_LB2);
-    const size_t off_out1 = (in_bytes + 255) & ~(size_t)255;
-    const size_t off_out2 = off_out1 + (((want1 || summary) ? out_bytes : 0) + 255) / 256 * 256;
-    const size_t per_stream = (off_out2 + (want2 ? out_bytes : 0) + 255) / 256 * 256;
-    rc = ensure_scratch(inst, per_stream * nst);
-    if (rc != PFSP_OK) return rc;
-    cudaStream_t st[2] = {nullptr, nullptr};
-    std::vector<cudaEvent_t> evs((size_t)nchunks * 2, nullptr);
-    cudaError_t e = cudaSuccess;
-    for (int q = 0; q < nst && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking);
-    for (size_t q = 0; q < evs.size() && e == cudaSuccess; ++q) e = cudaEventCreate(&evs[q]);
-    for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
-        const int q = (int)(c % nst);
-        const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
-        char *base = (char *)inst->d_scratch + per_stream * q;
-        uint8_t *dperm = (uint8_t *)base;
-        uint8_t *dd1 = dperm + (size_t)cn * n;
-        uint8_t *dd2 = dd1 + cn;
-        int32_t *o1 = want1 ? (int32_t *)(base + off_out1) : nullptr;
-        int32_t *o2 = want2 ? (int32_t *)(base + off_out2) : nullptr;
-        pfsp_node_summary *os = summary ? (pfsp_node_summary *)(base + off_out1) : nullptr;
-        const size_t ob = (size_t)cn * 2 * n * sizeof(int32_t);
-        e = cudaMemcpyAsync(dperm, perm + (size_t)off * n, (size_t)cn * n, cudaMemcpyHostToDevice, st[q]);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dd2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
-        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c], st[q]);
-        if (e == cudaSuccess)
-            e = summary ? launch_bound_batch(inst, kind, cn, dperm, dd1, dd2, nullptr, nullptr, st[q], os, ub)
-                        : launch_bounds(inst, kind, cn, dperm, dd1, dd2, o1, o2, st[q]);
-        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * c + 1], st[q]);
-        if (e == cudaSuccess && os)
-            e = cudaMemcpyAsync(summary + off, os, (size_t)cn * sizeof(pfsp_node_summary), cudaMemcpyDeviceToHost,
-                                st[q]);
-        if (e == cudaSuccess && o1)
-            e = cudaMemcpyAsync(lb1_out + (size_t)off * 2 * n, o1, ob, cudaMemcpyDeviceToHost, st[q]);
-        if (e == cudaSuccess && o2)
-            e = cudaMemcpyAsync(lb2_out + (size_t)off * 2 * n, o2, ob, cudaMemcpyDeviceToHost, st[q]);
+            if ((int)d1[i] + (int)d2[i] > n) {
+                rc = set_error(PFSP_ERR_INVALID, "node %lld: d1 + d2 = %d > n = %d", (long long)i, d1[i] + d2[i], n);
+                break;
+            }
+    }
+    if (rc == PFSP_OK) {
+        for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+            if (c >= nst) e = front(c);  // after back(c - nst): the stream's buffers are free again
+            if (e == cudaSuccess) e = back(c);
+        }
     }
     for (int q = 0; q < nst; ++q)
         if (st[q]) {
@@ -388,7 +420,7 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
             if (e == cudaSuccess) e = e2;
         }
     float ms = 0.f;
-    for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+    for (int64_t c = 0; c < nchunks && e == cudaSuccess && rc == PFSP_OK; ++c) {
         float t = 0.f;
         e = cudaEventElapsedTime(&t, evs[2 * c], evs[2 * c + 1]);
         ms += t;
@@ -398,6 +430,7 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
     for (int q = 0; q < nst; ++q)
         if (st[q]) cudaStreamDestroy(st[q]);
     if (e != cudaSuccess) return cuda_fail(e, summary ? "pfsp_bound_reduce" : "pfsp_bound_batch");
+    if (rc != PFSP_OK) return rc;
     memset(&inst->stats, 0, sizeof(inst->stats));
     const uint64_t children = 2 * ((uint64_t)num_nodes * (uint64_t)n - depth_sum);
     inst->stats.decomposed = (uint64_t)num_nodes;

@@ -99,18 +99,23 @@ def test_empty_batch_and_invalid_depths(pf):
 
 
 def test_invalid_depths_found_in_large_batches(pf):
-    # batches of a million nodes and more validate their depths on several host
-    # threads before any work: an invalid node in the last thread's range is
-    # refused, and so is one in the first
+    # batches of a million nodes and more (four chunks of the host pipeline):
+    # the host validates the depths while the first chunks run on the GPU, and
+    # copies nothing back before the validation passes, so an invalid node is
+    # refused wherever it sits (last chunk, first chunk) and the caller's
+    # buffers stay as they were
     n, m, N = 12, 5, (1 << 20) + 333
     inst = pf.pfsp_load_instance(inputs.make_instance(n, m, 2))
     perm, d1, d2 = inputs.random_nodes(n, N, seed=3, dmax=5)
     for bad in (N - 1, 7):
         e1, e2 = d1.copy(), d2.copy()
         e1[bad], e2[bad] = 7, 6  # 13 > n
+        h1 = np.full((N, 2, n), -7, dtype=np.int32)
+        h2 = np.full((N, 2, n), -7, dtype=np.int32)
         with pytest.raises(pf.PfspError) as e:
-            pf.pfsp_bound_batch(inst, 3, perm, e1, e2)
+            pf.pfsp_bound_batch(inst, 3, perm, e1, e2, lb1_out=h1, lb2_out=h2)
         assert e.value.code == pf.PFSP_ERR_INVALID and ("node %d" % bad) in str(e.value)
+        assert (h1 == -7).all() and (h2 == -7).all()
     g1, _ = pf.pfsp_bound_batch(inst, pf.PFSP_LB1, perm, d1, d2)
     assert pf.pfsp_stats(inst)["bounded_children"] == int(2 * (n - d1.astype(np.int64) - d2).sum())
     assert ((g1 >= 0).sum(axis=2) == (n - d1.astype(np.int64) - d2)[:, None]).all()
