@@ -16,7 +16,7 @@ The learned solver (not in the paper) orders the LB2 sweep and exits it early:
     slot checks, the sweep stops after the 32-pair slot at which one direction
     is decided.
 Every child that can survive gets its exact full-pair LB2, so pruning stays
-exact and the plain full-pair LB2 solver is the judge: under capped MinMin the
+exact and the plain full-pair LB2 solver is the reference: under capped MinMin the
 two build the same tree (node counts equal, checked), under the paper's
 MinMin the tie-breaking sums of decided children may differ and the node
 inflation is reported.  The comparison proves a known optimum (incumbent at
