@@ -41,7 +41,7 @@ WORKLOAD = "pfsp-bound-20x20-4M"
 METRIC = "bounded children/s (LB1 + full-pair LB2)"
 UNIT = "children/s"
 L2_FLUSH_BYTES = 256 << 20
-LEARNED_SLOT_CHECKS = False  # learned solver: check after every 32-pair slot
+LEARNED_SLOT_CHECKS = None  # learned solver's slot checks: learned.slot_checks_for(m)
 REDUCE_UB = 1500  # exclusive incumbent of the reduce mode's survivor masks (near the batch's median LB2)
 # INT32 ALU lanes per SM per clock on sm_103a (add, min/max, logic; measured
 # at 127.9 IMNMX thread-instructions per SM per clock)
@@ -438,7 +438,8 @@ def learned_leg(pfsp):
             c["counts_equal_plain"] = c["decomposed"]["learned"] == c["decomposed"]["plain"]
     return {"training": training,
             "learned_solver": "network pair order (root's children) + early exit per child%s" % (
-                " + slot checks" if LEARNED_SLOT_CHECKS else ""),
+                " + slot checks" if LEARNED_SLOT_CHECKS else
+                " + slot checks from four 32-pair slots (m >= 15)" if LEARNED_SLOT_CHECKS is None else ""),
             "ablations": "early_exit_index_order: the same early exit, pairs in index order; "
                          "pair_subset: LB2 over the network's top half of the 32-pair slots (weaker bound)",
             "proofs": rep,

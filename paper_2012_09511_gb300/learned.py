@@ -13,8 +13,10 @@ The learned solver (not in the paper) orders the LB2 sweep and exits it early:
   * early exit: a node one of whose directions has every child at or above
     the incumbent needs no sweep (reading R14); otherwise only the jobs with a
     child still below it are evaluated (PFSP_EARLY_EXIT_CHILDREN), and, with
-    slot checks, the sweep stops after the 32-pair slot at which one direction
-    is decided.
+    slot checks (on by default from four 32-pair slots, m >= 15), a job whose
+    two children are decided leaves the later slots and the sweep stops after
+    the slot at which one direction is decided: there the network's order
+    acts.
 Every child that can survive gets its exact full-pair LB2, so pruning stays
 exact and the plain full-pair LB2 solver is the reference: under capped MinMin the
 two build the same tree (node counts equal, checked), under the paper's
@@ -95,11 +97,22 @@ def order_pairs(pfsp, inst, mlp):
     return pfsp.pfsp_learn_pair_order(inst, mlp, perm, d1, d2)
 
 
-def learned_options(pfsp, slot_checks=False):
+def slot_checks_for(m):
+    """Whether the learned solver checks after every 32-pair slot for m
+    machines: from four slots on (m >= 15).  Measured on one GB300: at m = 20
+    the checks with the network's pair order are the fastest variant (18 x 20
+    proofs 1.8 % below the same early exit without them); at m = 10 (two slots,
+    the second holding 13 pairs) they cost about what they save."""
+    return m * (m - 1) // 2 > 96
+
+
+def learned_options(pfsp, slot_checks=None, m=None):
     """pfsp_solve options of the learned solver (the pair order is set on the
-    instance by order_pairs): the early exit per child, and optionally the
-    check after every 32-pair slot."""
+    instance by order_pairs): the early exit per child, and the check after
+    every 32-pair slot when slot_checks says so (None: slot_checks_for(m))."""
     flags = pfsp.PFSP_EARLY_EXIT | pfsp.PFSP_EARLY_EXIT_CHILDREN
+    if slot_checks is None:
+        slot_checks = m is not None and slot_checks_for(m)
     if slot_checks:
         flags |= pfsp.PFSP_EARLY_EXIT_SLOTS
     return {"learned": flags}
@@ -132,10 +145,12 @@ def _median_solve(pfsp, inst, reps, **kw):
     return r, statistics.median(ks), statistics.median(ws)
 
 
-def proof_variants(pfsp, p, opt, mlp, rule, reps=3, slot_checks=False, subset=True):
+def proof_variants(pfsp, p, opt, mlp, rule, reps=3, slot_checks=None, subset=True):
     """Proofs of the optimum `opt` of instance p (LB2, branching `rule`) by the
-    plain full-pair solver, the learned solver and the ablations."""
+    plain full-pair solver, the learned solver and the ablations (slot checks:
+    see learned_options)."""
     inst = pfsp.pfsp_load_instance(p)
+    ee = learned_options(pfsp, slot_checks, m=inst.m)
     base = dict(bound=2, init_ub=int(opt), branching=rule)
     out = {}
 
@@ -146,11 +161,11 @@ def proof_variants(pfsp, p, opt, mlp, rule, reps=3, slot_checks=False, subset=Tr
 
     pfsp.pfsp_set_lb2_pairs(inst, None)
     record("plain", *_median_solve(pfsp, inst, reps, **base))
-    record("early_exit_index_order", *_median_solve(pfsp, inst, reps, **learned_options(pfsp, slot_checks), **base))
+    record("early_exit_index_order", *_median_solve(pfsp, inst, reps, **ee, **base))
     t = time.perf_counter()
     order_pairs(pfsp, inst, mlp)
     t_rank = time.perf_counter() - t
-    record("learned", *_median_solve(pfsp, inst, reps, **learned_options(pfsp, slot_checks), **base),
+    record("learned", *_median_solve(pfsp, inst, reps, **ee, **base),
            extra_wall=t_rank)
     out["ranking_wall_s"] = t_rank
     if subset:
@@ -164,7 +179,7 @@ def proof_variants(pfsp, p, opt, mlp, rule, reps=3, slot_checks=False, subset=Tr
     return out
 
 
-def compare_proofs(pfsp, cases, mlps, rules=(("minmin", 0),), reps=3, slot_checks=False, subset_rules=("minmin",)):
+def compare_proofs(pfsp, cases, mlps, rules=(("minmin", 0),), reps=3, slot_checks=None, subset_rules=("minmin",)):
     """Time-to-proof of the plain full-pair LB2 solver and of the learned solver.
 
     cases: {name: (n, m, seeds)}; the optimum of each instance is found first
@@ -216,7 +231,7 @@ def compare_finding(pfsp, n, m, seeds, mlp, rule=0):
         pfsp.pfsp_set_pair_order(inst, None)
         a = pfsp.pfsp_solve(inst, bound=2, branching=rule, time_limit_s=30.0)
         order_pairs(pfsp, inst, mlp)
-        b = pfsp.pfsp_solve(inst, bound=2, branching=rule, time_limit_s=30.0, **learned_options(pfsp))
+        b = pfsp.pfsp_solve(inst, bound=2, branching=rule, time_limit_s=30.0, **learned_options(pfsp, m=m))
         same &= a["cmax"] == b["cmax"] and a["outcome"] == b["outcome"] == pfsp.PFSP_OPTIMAL
         for k, r in (("plain", a), ("learned", b)):
             tot[k] += r["kernel_seconds"]

@@ -26,3 +26,19 @@ def test_root_children_are_the_oracle_children_of_the_root():
         # the row's own partial schedule is the one the child stands for
         assert orc.lb2(p, list(perm[j, :1]), []) == lb2[0, j]
         assert orc.lb2(p, [], list(perm[n + j, -1:])) == lb2[1, j]
+
+
+class _Flags:
+    PFSP_EARLY_EXIT, PFSP_EARLY_EXIT_SLOTS, PFSP_EARLY_EXIT_CHILDREN = 4, 8, 16
+
+
+def test_slot_checks_from_four_slots():
+    # the learned solver checks after every 32-pair slot from four slots on
+    # (more than 96 pairs: m >= 15), where the network's order can act
+    assert [m for m in range(2, 33) if learned.slot_checks_for(m)] == list(range(15, 33))
+    f = _Flags()
+    assert learned.learned_options(f, m=20)["learned"] == 4 | 8 | 16
+    assert learned.learned_options(f, m=10)["learned"] == 4 | 16
+    assert learned.learned_options(f)["learned"] == 4 | 16
+    assert learned.learned_options(f, slot_checks=True, m=10)["learned"] == 4 | 8 | 16
+    assert learned.learned_options(f, slot_checks=False, m=20)["learned"] == 4 | 16
