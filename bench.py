@@ -412,8 +412,8 @@ def learned_leg(pfsp):
     """Learned solver vs the plain full-pair LB2 solver, proving known optima:
     n = 30, m = 10 (the ten seeds of learned.SEEDS_30X10, whose plain proofs
     take at least 50 ms each), n = 50, m = 5 (seeds 101-110; these proofs take
-    well under a millisecond) and n = 18, m = 20 (seeds 101-103, where the
-    pairs fill six 32-pair slots).  Both under capped MinMin (identical trees,
+    well under a millisecond), n = 18 and 20, m = 20 (seeds 101-103, where the
+    pairs fill six 32-pair slots and the slot checks are on).  Both under capped MinMin (identical trees,
     counts checked equal) and under the paper's MinMin (node inflation
     reported); kernel and wall times are the median of three solves.  The
     m-machine networks are trained on the GPU on the solver's own traces of
@@ -428,7 +428,7 @@ def learned_leg(pfsp):
         info["seconds"] = time.perf_counter() - t
         training["m=%d" % m] = info
     cases = {"30x10": (30, 10, learned.SEEDS_30X10), "50x5": (50, 5, range(101, 111)),
-             "18x20": (18, 20, range(101, 104))}
+             "18x20": (18, 20, range(101, 104)), "20x20": (20, 20, range(101, 104))}
     rules = (("minmin_capped", pfsp.PFSP_MINMIN_CAPPED), ("minmin", pfsp.PFSP_MINMIN))
     rep = learned.compare_proofs(pfsp, cases, mlps, rules=rules, reps=3, slot_checks=LEARNED_SLOT_CHECKS)
     find = learned.compare_finding(pfsp, 30, 10, learned.SEEDS_30X10, mlps[10], rule=pfsp.PFSP_MINMIN)
