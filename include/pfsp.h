@@ -361,12 +361,14 @@ int pfsp_solve_batch(const pfsp_instance *const *insts, int count, const pfsp_op
 
 /*
  * Autotuner of the batched pool (not in the paper): runs pfsp_solve_batch on
- * the first `sample` instances (0 = up to 32) for each point of a small grid
- * of launch parameters -- explorers per SM {4, 8, 12}, iterations between limit
- * checks and length publications {8, 32}, smallest interval a victim splits
- * {2, 720} -- and writes to *best the options (base plus the fastest point by
- * device time).  The children handled per warp are not a parameter: a warp
- * always bounds every child of the node it decomposes.
+ * `sample` instances spread evenly over the batch (every (count / sample)-th;
+ * 0 = up to 32) for each point of a small grid of launch parameters --
+ * explorers per SM {8, 12}, explorers per instance slot {4, 6, 12} (at most
+ * the explorers per SM), iterations between limit checks and length
+ * publications {8, 32}, smallest interval a victim splits {2, 8!} -- and
+ * writes to *best the options (base plus the fastest point by device time,
+ * the better of two timings each).  The children handled per warp are not a
+ * parameter: a warp always bounds every child of the node it decomposes.
  */
 int pfsp_autotune_batch(const pfsp_instance *const *insts, int count, const pfsp_options *base, int sample,
                         pfsp_options *best);
