@@ -74,6 +74,9 @@ struct Explorer {
     // kernel: its sweep leaves out the code that only saves instructions
     // (lb2_sweep's LEAN), which there costs spills
     static constexpr bool LEAN = KIND == kKindBatch;
+    // rows handed over with a stolen interval (SolveArgs.hand_dir): not in the
+    // batched pool
+    static constexpr bool HANDOFF = !LEAN;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -90,6 +93,7 @@ struct Explorer {
     long long t_mark;  // SM clock at the end of the last timed phase (lane 0)
     bool timed;        // phase timers on (a.phase != NULL)
     int ub_seen;       // incumbent read at the top of the current iteration
+    int hand_level;    // >= 0: rows 0..hand_level of a new interval's path were handed over
     int snap_seen;     // last snapshot request of the host heuristic threads answered
 
     __device__ Explorer(const SolveArgs &a_, const SmemTables &T_, const WarpScratch &W_, ExplorerSmem &X_, int me_,
@@ -119,6 +123,7 @@ struct Explorer {
         timed = a.phase != nullptr;
         ub_seen = INT_MAX;
         snap_seen = 0;
+        hand_level = -1;
         if (lane < kPhases) X.ph[lane] = 0ull;
         t_mark = timed ? clock64() : 0;
         __syncwarp();
@@ -140,6 +145,10 @@ struct Explorer {
         if (lane == 0) v = ld_volatile(a.ub);
         return __shfl_sync(PFSP_FULL, v, 0);
     }
+    // rows handed over with stolen intervals: explorers whose rows live in
+    // shared memory leave their global rows free to receive them
+    __device__ bool handoff_on() const { return HANDOFF && a.hand_dir != nullptr && a.rows_smem; }
+
     __device__ int active_count() const {
         int v = 0;
         if (lane == 0) v = ld_volatile(a.active);
@@ -593,6 +602,13 @@ struct Explorer {
     // select() returned).  The decompositions happen at the loop's single
     // expand call site, so that the kernel carries one copy of it.
     __device__ int init_step(int &init_phase, bool &counted, bool &have_node) {
+        if (init_phase == 0 && hand_level >= 0) {
+            // rows 0..hand_level were handed over with the interval: carry on
+            // as if row hand_level had just been built
+            I = hand_level;
+            hand_level = -1;
+            init_phase = 1;
+        }
         if (init_phase == 0) {
             I = -1;
             bool zero = true;
@@ -669,6 +685,7 @@ struct Explorer {
         const unsigned long long rseq = (req >> 20) & 0xfffffull;
         const bool same = (int)(req >> 40) == (a.my_inst & 0xffffff);
         int granted = 0;
+        int lc = -1;  // last level of the path the thief shares with this explorer
         if (lane == 0 && active && same && t < a.K) {
             // remaining territory [pos, end): pos = V[0..I], zeros below
             int s[64], q[64];
@@ -709,7 +726,31 @@ struct Explorer {
                 X.etop = 0;
                 atomicAdd(a.active, 1);
                 granted = 1;
+                // the thief's path follows q: its nodes above the first
+                // level L where q leaves this explorer's position are this
+                // explorer's, and so are rows 0..min(L, I)
+                int L = 0;
+                while (L < n && q[L] == (L <= I ? X.V[L] : 0)) ++L;
+                lc = min(L, I);
             }
+        }
+        if (handoff_on()) {
+            granted = __shfl_sync(PFSP_FULL, granted, 0);
+            lc = __shfl_sync(PFSP_FULL, lc, 0);
+            if (granted && lc >= 0) {
+                int32_t *tl = a.rows_lb + (size_t)t * a.row_stride;
+                uint8_t *tj = a.rows_job + (size_t)t * a.row_stride;
+                for (int i = lane; i < (lc + 1) * n; i += 32) {
+                    tl[i] = rl[i];
+                    tj[i] = rj[i];
+                }
+                for (int i = lane; i <= lc; i += 32) a.hand_dir[(size_t)t * 64 + i] = (uint8_t)X.dir[i];
+                if (lane == 0) a.hand_lc[t] = lc;
+                __threadfence();  // before lane 0's answer below
+            } else if (granted && lane == 0) {
+                a.hand_lc[t] = -1;
+            }
+            __syncwarp();
         }
         if (lane == 0) {
             __threadfence();
@@ -857,6 +898,27 @@ struct Explorer {
                 atomicCAS(a.stop, 0, 3);
             }
             return -1;
+        }
+        hand_level = -1;
+        if (handoff_on()) {
+            // rows 0..lc of the path to D, as the victim wrote them (read
+            // from L2, past this SM's L1): the path is rebuilt below them only
+            const int lc = __ldcg(a.hand_lc + me);
+            if (lc >= 0 && lc <= n - 2) {
+                const int32_t *hl = a.rows_lb + (size_t)me * a.row_stride;
+                const volatile uint8_t *hj = a.rows_job + (size_t)me * a.row_stride;
+                for (int i = lane; i < (lc + 1) * n; i += 32) {
+                    rl[i] = __ldcg(hl + i);
+                    rj[i] = hj[i];
+                }
+                const volatile uint8_t *hd = a.hand_dir + (size_t)me * 64;
+                for (int i = lane; i <= lc; i += 32) {
+                    X.dir[i] = hd[i];
+                    X.V[i] = X.D[i];
+                }
+                hand_level = lc;
+            }
+            __syncwarp();
         }
         st.steals += 1;
         return 1;

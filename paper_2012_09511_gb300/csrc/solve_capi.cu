@@ -348,6 +348,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const size_t o_mb = take((size_t)K * 8), o_rs = take((size_t)K * 8), o_le = take((size_t)K * 4);
     const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64), o_ph = take(8 * kPhases);
     const size_t o_lv = take((size_t)K), o_sp = take((size_t)K * 4), o_sq = take((size_t)K * 4);
+    const size_t o_hd = take((size_t)K * 64), o_hc = take((size_t)K * 4);
     const bool want_ckpt = rio && rio->ckpt;
     const size_t o_ck = take(want_ckpt ? (size_t)K * kCkptRecord : 0);
     const int64_t tcap = tr ? tr->capacity : 0;
@@ -372,6 +373,8 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.in_level = (uint8_t *)(b + o_lv);
     a.seq_posted = (unsigned *)(b + o_sp);
     a.seq_taken = (unsigned *)(b + o_sq);
+    a.hand_dir = (uint8_t *)(b + o_hd);  // used when the rows live in shared memory (a.rows_smem)
+    a.hand_lc = (int *)(b + o_hc);
     a.ckpt = want_ckpt ? (uint8_t *)(b + o_ck) : nullptr;
     a.counters = (unsigned long long *)(b + o_ct);
     a.phase = opt->phase_timers ? (unsigned long long *)(b + o_ph) : nullptr;
@@ -415,6 +418,7 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.in_level, hl.data(), hl.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.seq_posted, 0, (size_t)K * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.seq_taken, 0, (size_t)K * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.hand_lc, 0xff, (size_t)K * 4, st);
     if (e == cudaSuccess && want_ckpt) e = cudaMemsetAsync(a.ckpt, 0, (size_t)K * kCkptRecord, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc, hsc, sizeof(hsc), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev0, st);

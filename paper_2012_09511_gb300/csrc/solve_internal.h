@@ -96,6 +96,12 @@ struct SolveArgs {
     uint8_t *in_level;    // [K] start level of an incoming interval (0xff: first zero-rest level), or NULL
     unsigned *seq_posted; // [K] sequence number of each explorer's last posted steal request (or NULL)
     unsigned *seq_taken;  // [K] sequence number of the last answer it took in (or NULL)
+    // rows handed over with a stolen interval (NULL: none; only with rows_smem,
+    // whose explorers leave their rows in rows_job / rows_lb unused): the
+    // victim writes rows 0..L of the shared path into the thief's rows_job /
+    // rows_lb, their directions into hand_dir and L into hand_lc
+    uint8_t *hand_dir;    // [K][64]
+    int *hand_lc;         // [K]
     uint8_t *ckpt;        // [K][kCkptRecord] remaining interval of each explorer at a limit stop (NULL: off)
     unsigned long long *mailbox;   // [K] request: instance << 40 | sequence << 20 | thief, or kNoRequest
     unsigned long long *response;  // [K] answer to a thief: sequence << 2 | 1 granted / 2 denied
