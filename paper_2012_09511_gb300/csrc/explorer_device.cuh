@@ -145,9 +145,8 @@ struct Explorer {
         if (lane == 0) v = ld_volatile(a.ub);
         return __shfl_sync(PFSP_FULL, v, 0);
     }
-    // rows handed over with stolen intervals: explorers whose rows live in
-    // shared memory leave their global rows free to receive them
-    __device__ bool handoff_on() const { return HANDOFF && a.hand_dir != nullptr && a.rows_smem; }
+    // rows handed over with stolen intervals (SolveArgs.hand_*)
+    __device__ bool handoff_on() const { return HANDOFF && a.hand_dir != nullptr; }
 
     __device__ int active_count() const {
         int v = 0;
@@ -738,8 +737,8 @@ struct Explorer {
             granted = __shfl_sync(PFSP_FULL, granted, 0);
             lc = __shfl_sync(PFSP_FULL, lc, 0);
             if (granted && lc >= 0) {
-                int32_t *tl = a.rows_lb + (size_t)t * a.row_stride;
-                uint8_t *tj = a.rows_job + (size_t)t * a.row_stride;
+                int32_t *tl = a.hand_lb + (size_t)t * a.row_stride;
+                uint8_t *tj = a.hand_job + (size_t)t * a.row_stride;
                 for (int i = lane; i < (lc + 1) * n; i += 32) {
                     tl[i] = rl[i];
                     tj[i] = rj[i];
@@ -902,11 +901,12 @@ struct Explorer {
         hand_level = -1;
         if (handoff_on()) {
             // rows 0..lc of the path to D, as the victim wrote them (read
-            // from L2, past this SM's L1): the path is rebuilt below them only
+            // from L2, past this SM's L1, and stored into this explorer's
+            // rows by itself): the path is rebuilt below them only
             const int lc = __ldcg(a.hand_lc + me);
             if (lc >= 0 && lc <= n - 2) {
-                const int32_t *hl = a.rows_lb + (size_t)me * a.row_stride;
-                const volatile uint8_t *hj = a.rows_job + (size_t)me * a.row_stride;
+                const int32_t *hl = a.hand_lb + (size_t)me * a.row_stride;
+                const volatile uint8_t *hj = a.hand_job + (size_t)me * a.row_stride;
                 for (int i = lane; i < (lc + 1) * n; i += 32) {
                     rl[i] = __ldcg(hl + i);
                     rj[i] = hj[i];

@@ -349,6 +349,9 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     const size_t o_bp = take((size_t)K * 64), o_ct = take(8 * 8), o_sc = take(64), o_ph = take(8 * kPhases);
     const size_t o_lv = take((size_t)K), o_sp = take((size_t)K * 4), o_sq = take((size_t)K * 4);
     const size_t o_hd = take((size_t)K * 64), o_hc = take((size_t)K * 4);
+    // hand-off rows: the explorers' own global rows when their rows live in
+    // shared memory (unused then), else a buffer of their own
+    const size_t o_hj = take(a.rows_smem ? 0 : (size_t)K * n * n), o_hl = take(a.rows_smem ? 0 : (size_t)K * n * n * 4);
     const bool want_ckpt = rio && rio->ckpt;
     const size_t o_ck = take(want_ckpt ? (size_t)K * kCkptRecord : 0);
     const int64_t tcap = tr ? tr->capacity : 0;
@@ -373,8 +376,10 @@ static int solve_impl(const pfsp_instance *inst_c, const pfsp_options *opt, cons
     a.in_level = (uint8_t *)(b + o_lv);
     a.seq_posted = (unsigned *)(b + o_sp);
     a.seq_taken = (unsigned *)(b + o_sq);
-    a.hand_dir = (uint8_t *)(b + o_hd);  // used when the rows live in shared memory (a.rows_smem)
+    a.hand_dir = (uint8_t *)(b + o_hd);
     a.hand_lc = (int *)(b + o_hc);
+    a.hand_job = a.rows_smem ? a.rows_job : (uint8_t *)(b + o_hj);
+    a.hand_lb = a.rows_smem ? a.rows_lb : (int32_t *)(b + o_hl);
     a.ckpt = want_ckpt ? (uint8_t *)(b + o_ck) : nullptr;
     a.counters = (unsigned long long *)(b + o_ct);
     a.phase = opt->phase_timers ? (unsigned long long *)(b + o_ph) : nullptr;

@@ -96,10 +96,13 @@ struct SolveArgs {
     uint8_t *in_level;    // [K] start level of an incoming interval (0xff: first zero-rest level), or NULL
     unsigned *seq_posted; // [K] sequence number of each explorer's last posted steal request (or NULL)
     unsigned *seq_taken;  // [K] sequence number of the last answer it took in (or NULL)
-    // rows handed over with a stolen interval (NULL: none; only with rows_smem,
-    // whose explorers leave their rows in rows_job / rows_lb unused): the
-    // victim writes rows 0..L of the shared path into the thief's rows_job /
-    // rows_lb, their directions into hand_dir and L into hand_lc
+    // rows handed over with a stolen interval (hand_dir NULL: none): the
+    // victim writes rows 0..L of the shared path into the thief's slot of
+    // hand_job / hand_lb (the unused rows_job / rows_lb when the rows live in
+    // shared memory), their directions into hand_dir and L into hand_lc; the
+    // thief copies them into its own rows
+    uint8_t *hand_job;    // [K][row_stride]
+    int32_t *hand_lb;     // [K][row_stride]
     uint8_t *hand_dir;    // [K][64]
     int *hand_lc;         // [K]
     uint8_t *ckpt;        // [K][kCkptRecord] remaining interval of each explorer at a limit stop (NULL: off)
