@@ -74,9 +74,6 @@ struct Explorer {
     // kernel: its sweep leaves out the code that only saves instructions
     // (lb2_sweep's LEAN), which there costs spills
     static constexpr bool LEAN = KIND == kKindBatch;
-    // rows handed over with a stolen interval (SolveArgs.hand_dir): not in the
-    // batched pool
-    static constexpr bool HANDOFF = !LEAN;
     const SolveArgs &a;
     const SmemTables &T;
     const WarpScratch &W;
@@ -146,7 +143,7 @@ struct Explorer {
         return __shfl_sync(PFSP_FULL, v, 0);
     }
     // rows handed over with stolen intervals (SolveArgs.hand_*)
-    __device__ bool handoff_on() const { return HANDOFF && a.hand_dir != nullptr; }
+    __device__ bool handoff_on() const { return a.hand_dir != nullptr; }
 
     __device__ int active_count() const {
         int v = 0;

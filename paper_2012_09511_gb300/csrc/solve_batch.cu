@@ -38,6 +38,10 @@ struct BatchArgs {
     int K, row_stride, warp_stride, max_tab_words;
     uint8_t *rows_job;
     int32_t *rows_lb;
+    uint8_t *hand_job;   // [K][row_stride] rows handed over with stolen intervals
+    int32_t *hand_lb;    // [K][row_stride]
+    uint8_t *hand_dir;   // [K][64]
+    int *hand_lc;        // [K]
     uint8_t *in_start, *in_end;
     unsigned long long *mailbox, *response;
     float *len_est;
@@ -161,6 +165,10 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_batch_kernel(BatchA
                 sa.row_stride = b.row_stride;
                 sa.rows_job = b.rows_job;
                 sa.rows_lb = b.rows_lb;
+                sa.hand_job = b.hand_job;
+                sa.hand_lb = b.hand_lb;
+                sa.hand_dir = b.hand_dir;
+                sa.hand_lc = b.hand_lc;
                 sa.inst_of = b.inst_of;
                 sa.my_inst = i;
                 sa.in_start = b.in_start;
@@ -372,6 +380,8 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     const size_t o_ub = take((size_t)count * 4), o_bk = take((size_t)count * 8), o_ct = take((size_t)count * 64);
     const size_t o_sp = take((size_t)count * 4), o_misc = take(64);
     const size_t o_ip = take((size_t)count * 64), o_pl = take((size_t)count * 4), o_pc = take((size_t)count * 4);
+    const size_t o_hj = take((size_t)K * rs), o_hl = take((size_t)K * rs * 4), o_hd = take((size_t)K * 64),
+                 o_hc = take((size_t)K * 4);
     void *blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, off);
     if (e != cudaSuccess) {
@@ -391,6 +401,10 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
     b.max_tab_words = P.max_tab;
     b.rows_job = (uint8_t *)(B + o_rj);
     b.rows_lb = (int32_t *)(B + o_rl);
+    b.hand_job = (uint8_t *)(B + o_hj);
+    b.hand_lb = (int32_t *)(B + o_hl);
+    b.hand_dir = (uint8_t *)(B + o_hd);
+    b.hand_lc = (int *)(B + o_hc);
     b.in_start = (uint8_t *)(B + o_is);
     b.in_end = (uint8_t *)(B + o_ie);
     b.mailbox = (unsigned long long *)(B + o_mb);
@@ -449,6 +463,7 @@ extern "C" int pfsp_solve_batch(const pfsp_instance *const *insts, int count, co
         if (c == cudaSuccess) c = cudaMemsetAsync(b.counters, 0, (size_t)count * 64, st);
         if (c == cudaSuccess) c = cudaMemsetAsync(b.stop, 0, (size_t)count * 4, st);
         if (c == cudaSuccess) c = cudaMemsetAsync(b.perm_lock, 0, (size_t)count * 4, st);
+        if (c == cudaSuccess) c = cudaMemsetAsync(b.hand_lc, 0xff, (size_t)K * 4, st);
         if (c == cudaSuccess) c = cudaMemsetAsync(misc, 0, 64, st);
         if (c == cudaSuccess) c = P.nw == 1 ? batch_launch<1>(b, P.blocks, P.warps, P.smem, st)
                                             : batch_launch<2>(b, P.blocks, P.warps, P.smem, st);
