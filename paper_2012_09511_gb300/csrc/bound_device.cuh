@@ -72,9 +72,10 @@ struct WarpScratch {
     int *cidx;        // [64] cidx[j] = compact index of job j
     int2 *G;          // [nr][mp] {forward child: F'_k + R_k - p_jk, backward child: F_k + R_k - p_jk}
     int *Bb;          // [nr][mp] backward child back B'_k minus the parent's B_k
-    int2 *E;          // [nr][32] prefix pass records {PB, t | c << 8} (per lane); NULL for register walks
+    int *Epb;         // [nr][32] prefix pass records: the prefix constant PB of each step (per lane)
+    uint8_t *Et;      // [nr][32] the bit of the step's position (per lane); both NULL for register walks
     int *Cb;          // [nr][32] C of child c plus the parent's B_l (per lane)
-    int2 *X;          // [u][33] transpose buffer, aliasing E and Cb (or Cb and the words after it)
+    int2 *X;          // [u][33] transpose buffer (shared accumulators only), aliasing the records and Cb
     int2 *Acc;        // [nr][32] accumulators (only when not kept in registers)
 };
 
@@ -85,15 +86,16 @@ constexpr int kWarpHead = 256;
 constexpr int kRegWalk = 20;
 
 // reg_walk: the layout of kernels whose LB2 walks keep their records in
-// registers (n <= kRegWalk, register accumulators): no E region and no
+// registers (n <= kRegWalk, register accumulators): no record region and no
 // transpose buffer.
 __host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2, bool reg_walk = false) {
     if (!lb2) return kWarpHead;
     int nr = round4(n);
     int g = round4(nr * (m | 1));
-    // G takes 2g words; then E + Cb (96 nr: the transpose buffer aliases E
-    // and Cb), or Cb alone (32 nr) with register walks
-    const int walk = reg_walk ? 32 * nr : 96 * nr;
+    // G takes 2g words, Bb g; then the records (Epb 32 nr + Et 8 nr) and Cb
+    // (32 nr): 72 nr, or 96 nr with shared accumulators, whose transpose buffer
+    // (66 nr) aliases them; Cb alone (32 nr) with register walks
+    const int walk = reg_walk ? 32 * nr : (smem_acc ? 96 * nr : 72 * nr);
     return kWarpHead + 3 * g + walk + (smem_acc ? 64 * nr : 0);
 }
 
@@ -108,16 +110,20 @@ __device__ inline WarpScratch carve_warp(int *base, int n, int m, bool reg_walk 
     w.Bb = base + kWarpHead + 2 * g;
     if (reg_walk) {
         // register walks come with register accumulators: neither the
-        // transpose buffer nor shared accumulators are used
-        w.E = nullptr;
+        // records, the transpose buffer nor shared accumulators are used
+        w.Epb = nullptr;
+        w.Et = nullptr;
         w.Cb = w.Bb + g;
         w.X = nullptr;
         w.Acc = nullptr;
     } else {
-        w.E = reinterpret_cast<int2 *>(w.Bb + g);
-        w.Cb = w.Bb + g + 64 * nr;
-        w.X = w.E;
-        w.Acc = reinterpret_cast<int2 *>(w.Cb + 32 * nr);
+        w.Epb = w.Bb + g;
+        w.Et = reinterpret_cast<uint8_t *>(w.Epb + 32 * nr);
+        w.Cb = w.Epb + 40 * nr;
+        // shared accumulators (n > 32) only: the transpose buffer from the
+        // records on, the accumulators after the 96 nr words of the walk
+        w.X = reinterpret_cast<int2 *>(w.Epb);
+        w.Acc = n > 32 ? reinterpret_cast<int2 *>(w.Epb + 96 * nr) : nullptr;
     }
     return w;
 }
@@ -378,8 +384,10 @@ __device__ __forceinline__ void decompose_lb1(const SmemTables &T, const WarpScr
 // short chain), so the table loads of the four jobs issue together
 // instead of each waiting for the previous job's.
 template <int NW>
-__device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, int2 *E, umask_t<NW> Upos, int u,
-                                          int lane, int Bl) {
+__device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, umask_t<NW> Upos, int u, int lane,
+                                          int Bl) {
+    int *Epb = W.Epb + lane;
+    uint8_t *Et = W.Et + lane;
     int PB = kNegInf;
     for (int i = 0; i < u; i += 4) {
         int t[4];
@@ -394,22 +402,26 @@ __device__ __forceinline__ void scan_slot(const WarpScratch &W, const int2 *pt, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             // rows u..round4(u)-1 get a record that the backward walk never reads
-            const int c = W.cidx[e[q].x & 0xff];
-            E[(i + q) * 32] = make_int2(PB, (t[q] & 0xff) | (c << 8));
+            Epb[(i + q) * 32] = PB;
+            Et[(i + q) * 32] = (uint8_t)t[q];
             PB = addmax(PB, e[q].x >> 8, e[q].y);  // identity for a padding step
         }
     }
     int SA = Bl, SB = kNegInf;
     for (int i = u - 1; i >= 0; i -= 4) {
-        int2 q[4], e[4];
+        int pb[4], c[4];
+        int2 e[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) q[r] = (i - r >= 0) ? E[(i - r) * 32] : make_int2(0, 0);
+        for (int r = 0; r < 4; ++r) {
+            pb[r] = (i - r >= 0) ? Epb[(i - r) * 32] : 0;
+            e[r] = (i - r >= 0) ? pt[pos_of_bit<NW>(Et[(i - r) * 32]) * 32] : make_int2(0, kNegInf);
+        }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) e[r] = (i - r >= 0) ? pt[pos_of_bit<NW>(q[r].y & 0xff) * 32] : make_int2(0, kNegInf);
+        for (int r = 0; r < 4; ++r) c[r] = W.cidx[e[r].x & 0xff];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (i - r >= 0) {
-                W.Cb[(q[r].y >> 8) * 32 + lane] = addmax(q[r].x, SA, SB);
+                W.Cb[c[r] * 32 + lane] = addmax(pb[r], SA, SB);
                 SB = addmax(e[r].y, SA, SB);
                 SA += e[r].x >> 8;
             }
@@ -570,7 +582,6 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
         for (int c = 0; c < u; ++c) W.Acc[c * 32 + lane] = make_int2(kNegInf, kNegInf);
     }
     const int u4 = (u + 3) & ~3;
-    int2 *E = RW ? nullptr : W.E + lane;
     // positions of the unscheduled jobs in each pair's Johnson order, one
     // bit mask per slot; with a compile-time slot count all masks are built
     // in a single walk over the unscheduled jobs, or, when fewer jobs are
@@ -625,7 +636,7 @@ __device__ __forceinline__ int lb2_sweep(const SmemTables &T, const WarpScratch 
             }
         }
         if constexpr (RW) scan_slot_reg<NW>(W, pt, Upos, u, lane, Bl);
-        else scan_slot<NW>(W, pt, E, Upos, u, lane, Bl);
+        else scan_slot<NW>(W, pt, Upos, u, lane, Bl);
         // evaluation: the third pair term of every evaluated child,
         // F_k + R_k + C + B_l of the child; Cb holds C + B_l(parent) and Bb
         // holds B'_l - B_l(parent), so the forward child's term is G.x + Cb

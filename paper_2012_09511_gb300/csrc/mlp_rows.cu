@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
         }
         // pair targets: sweep the slots again and compare each pair's term
         // with the children's final LB2
-        int2 *E = W.E + lane;
         for (int s = 0; s < S && m >= 2 && u > 0; ++s) {
             const int klw = T.kl[s * 32 + lane];
             const int k = klw & 0xff, l = klw >> 8;
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(RowsArgs a) {
                 um = drop_bit<NW>(um, j);
                 Upos |= umask_t<NW>(1) << T.rank[((size_t)j * T.S + s) * 32 + lane];
             }
-            scan_slot<NW>(W, T.ptab + (size_t)s * n * 32 + lane, E, Upos, u, lane, Bl);
+            scan_slot<NW>(W, T.ptab + (size_t)s * n * 32 + lane, Upos, u, lane, Bl);
             bool hit = false;
             for (int c = 0; c < u; ++c) {
                 // Cb holds C + B_l and Bb holds B'_l - B_l (parent's B_l)
