@@ -93,9 +93,9 @@ __host__ __device__ inline int warp_words(int n, int m, bool smem_acc, bool lb2,
     int nr = round4(n);
     int g = round4(nr * (m | 1));
     // G takes 2g words, Bb g; then the records (Epb 32 nr + Et 8 nr) and Cb
-    // (32 nr): 72 nr, or 96 nr with shared accumulators, whose transpose buffer
-    // (66 nr) aliases them; Cb alone (32 nr) with register walks
-    const int walk = reg_walk ? 32 * nr : (smem_acc ? 96 * nr : 72 * nr);
+    // (32 nr): 72 nr, which the transpose buffer of shared accumulators (66 nr)
+    // aliases; Cb alone (32 nr) with register walks
+    const int walk = reg_walk ? 32 * nr : 72 * nr;
     return kWarpHead + 3 * g + walk + (smem_acc ? 64 * nr : 0);
 }
 
@@ -121,9 +121,9 @@ __device__ inline WarpScratch carve_warp(int *base, int n, int m, bool reg_walk 
         w.Et = reinterpret_cast<uint8_t *>(w.Epb + 32 * nr);
         w.Cb = w.Epb + 40 * nr;
         // shared accumulators (n > 32) only: the transpose buffer from the
-        // records on, the accumulators after the 96 nr words of the walk
+        // records on, the accumulators after the 72 nr words of the walk
         w.X = reinterpret_cast<int2 *>(w.Epb);
-        w.Acc = n > 32 ? reinterpret_cast<int2 *>(w.Epb + 96 * nr) : nullptr;
+        w.Acc = n > 32 ? reinterpret_cast<int2 *>(w.Epb + 72 * nr) : nullptr;
     }
     return w;
 }
