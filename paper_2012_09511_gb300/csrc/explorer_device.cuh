@@ -33,7 +33,7 @@ struct ExplorerSmem {
     int E[64];      // end of the interval (digits); etop = coefficient of n!
     int D[64];      // start of an incoming interval
     int perm[64];   // staging of the decoded node
-    double w[64];   // (n-1-i)! as double, for length estimates
+    float lw[64];   // log2 (n-1-i)!, for length estimates
     int etop;
     unsigned seq;   // sequence number of this explorer's last steal request
     int lvl;        // start level of the interval (-1: the first level below which D is all zero)
@@ -44,7 +44,8 @@ struct ExplorerSmem {
     int sorder[16];    // LB2 slot order of the current node
     unsigned long long ph[kPhases];  // SM clock cycles spent in each phase (lane 0 updates)
 };
-constexpr int kExplorerWords = (64 * 5 + 64 * 2 + 8 + 64 + 16 + 16 + 2 * kPhases);  // a multiple of 8 words
+constexpr int kExplorerWords = (64 * 5 + 64 + 8 + 64 + 16 + 16 + 2 * kPhases);  // a multiple of 8 words
+static_assert(sizeof(ExplorerSmem) == 4 * kExplorerWords, "explorer scratch size");
 static_assert(kExplorerWords % 8 == 0, "explorer scratch keeps 32-byte alignment");
 
 struct Stats {
@@ -113,9 +114,9 @@ struct Explorer {
         pending_nodes = 0;
         deadline = a.time_limit_ns ? global_ns() + a.time_limit_ns : 0ull;
         for (int i = lane; i < 64; i += 32) {
-            double w = 1.0;
-            for (int t = 2; t <= n - 1 - i; ++t) w *= t;
-            X.w[i] = w;
+            float lw = 0.0f;
+            for (int t = 2; t <= n - 1 - i; ++t) lw += log2f((float)t);
+            X.lw[i] = lw;
         }
         timed = a.phase != nullptr;
         ub_seen = INT_MAX;
@@ -168,25 +169,42 @@ struct Explorer {
         return false;  // equal
     }
 
-    // log2 of (end - pos), or -1 if empty (estimate for victim choice only)
-    __device__ float log2_length() const {
-        double t = 0.0;
-        for (int h = 0; h < NW; ++h) {
-            int i = lane + 32 * h;
-            if (i < n) {
-                int v = i <= I ? X.V[i] : 0;
-                t += (double)(X.E[i] - v) * X.w[i];
-            }
+    // The length of the remaining interval [pos, end) (pos = V[0..I] with
+    // zeros below, end = E plus etop * n!) as acc * (n-1-lv)!, in integer
+    // arithmetic (the FP64 units of this GPU are few and slow).  The digit
+    // differences are folded level by level with Horner's rule in the
+    // factorial base (the weight of level i-1 is n-i times that of level i),
+    // from level i0 (every level above it equal in pos and end; 0 with etop)
+    // until acc reaches 2^24 or the last level is folded.  The levels left out
+    // add less than one unit of (n-1-lv)!, so acc * (n-1-lv)! is the length to
+    // within a relative 2^-24, and exactly when lv = n - 1.  A prefix of end is
+    // never below the same prefix of pos, so acc >= 0.  One lane.
+    __device__ int fold_length(int i0, int &lv) const {
+        int acc = X.etop, i = X.etop ? 0 : i0;
+        for (; i < n; ++i) {
+            acc = acc * (n - i) + (X.E[i] - (i <= I ? X.V[i] : 0));  // < 2^30
+            if (acc >= (1 << 24)) break;
         }
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(PFSP_FULL, t, o);
-        if (X.etop) t += X.w[0] * n;
-        if (t < 1.0) return -1.0f;
-        // log2(t) to within 0.09: the exponent plus the mantissa's fraction
-        // (log2(1 + f) ~ f), read from the bits; cheaper than a double log2
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
-        const int ex = (int)((bits >> 52) & 0x7ffull) - 1023;
-        const float fr = (float)(unsigned)((bits >> 20) & 0xffffffffull) * 2.3283064365386963e-10f;
-        return (float)ex + fr;
+        lv = min(i, n - 1);
+        return acc;
+    }
+
+    // log2 of (end - pos), or -1 if empty (estimate for victim choice only);
+    // the value of lane 0
+    __device__ float log2_length() const {
+        int i0 = n;
+        for (int h = NW - 1; h >= 0; --h) {
+            const int i = lane + 32 * h;
+            const unsigned d = __ballot_sync(PFSP_FULL, i < n && X.E[i] != (i <= I ? X.V[i] : 0));
+            if (d) i0 = 32 * h + __ffs(d) - 1;
+        }
+        float l = -1.0f;
+        if (lane == 0) {
+            int lv;
+            const int acc = fold_length(i0, lv);
+            if (acc >= 1) l = __log2f((float)acc) + X.lw[lv];
+        }
+        return l;
     }
 
     // Find the next node: the first live cell at or after V[I] on level I,
@@ -706,10 +724,14 @@ struct Explorer {
                 int p = i <= I ? X.V[i] : 0;
                 cmp = q[i] > p ? 1 : (q[i] < p ? -1 : 0);
             }
-            // length estimate for the minimum steal size
-            double len = X.etop ? X.w[0] * n : 0.0;
-            for (int i = 0; i < n; ++i) len += (double)(X.E[i] - (i <= I ? X.V[i] : 0)) * X.w[i];
-            if (cmp > 0 && len >= (double)a.min_steal) {
+            // the minimum steal size: compared exactly when the fold reached
+            // the last level, else (a length of 2^24 leaves or more) on the
+            // log2 scale
+            int lv;
+            const int acc = fold_length(0, lv);
+            const bool big = lv == n - 1 ? (float)acc >= a.min_steal
+                                         : __log2f((float)acc) + X.lw[lv] >= log2f(fmaxf(a.min_steal, 1.0f));
+            if (cmp > 0 && big) {
                 uint8_t *ds = a.in_start + (size_t)t * 64;
                 uint8_t *de = a.in_end + (size_t)t * 65;
                 for (int i = 0; i < n; ++i) {
