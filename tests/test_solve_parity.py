@@ -257,6 +257,23 @@ def test_n20_m10_lb2_optimum_and_proof_counts(pf, seed):
     _check_perm(p, f)
 
 
+@pytest.mark.parametrize("min_steal", [2.0, 40320.0, 1e30])
+def test_minimum_split_keeps_the_proof_tree(pf, min_steal):
+    # a victim splits its interval only when it holds at least min_steal
+    # leaves (the work stealing of Section 3.4 with a minimum split); the
+    # proof's tree is the same whatever the threshold, and above every
+    # interval's length (20! < 1e30) no steal is granted at all
+    g = {r["seed"]: r for r in _golden()}[10]
+    inst = pf.pfsp_load_instance(inputs.make_instance(20, 10, 10))
+    r = pf.pfsp_solve(inst, bound=2, init_ub=g["optimum"], min_steal=min_steal)
+    assert r["outcome"] == pf.PFSP_PROVEN_NO_BETTER
+    assert (r["decomposed"], r["bounded_children"]) == (g["proof_decomposed"], g["proof_bounded"])
+    if min_steal > 1e20:
+        assert r["steals"] == 0
+    else:
+        assert r["steals"] > 0
+
+
 def test_steal_wait_expiry_returns_timeout(pf):
     # a thief's bounded wait for a victim's answer (the steal handshake of
     # Section 3.4) made to run out on purpose: with one poll allowed, the first
