@@ -22,6 +22,7 @@ scaling); the only collectives are a barrier and a max of the timings.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -555,10 +556,17 @@ def run_native(args):
         if ws > 1:
             dist.barrier()
         ts = []
-        for _ in range(e2e_steps):
-            t0 = time.perf_counter()
-            call()
-            ts.append(time.perf_counter() - t0)
+        # no garbage collection pass in the middle of a timed step
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            for _ in range(e2e_steps):
+                t0 = time.perf_counter()
+                call()
+                ts.append(time.perf_counter() - t0)
+        finally:
+            if gc_was:
+                gc.enable()
         return ts
 
     def rates(ts):
