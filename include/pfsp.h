@@ -113,7 +113,13 @@ int pfsp_bound_batch(const pfsp_instance *inst, int kind, int64_t num_nodes, con
 
 /* (pfsp_bound_batch moves the batch in chunks of 262,144 nodes over two CUDA
  * streams, so that the copies of one chunk overlap the kernel of another; the
- * overlap is complete with page-locked host buffers.) */
+ * overlap is complete with page-locked host buffers.  When both requested
+ * outputs are page-locked memory that the GPU maps, the chunks after the
+ * first two are written in place by the kernel over the host link, so that
+ * no copy is left after the last kernel; the first two, like every chunk of
+ * pageable outputs, go through device buffers, and nothing reaches the
+ * outputs before the depths are validated.  The same holds for the summaries
+ * of pfsp_bound_reduce.) */
 
 /* Same as pfsp_bound_batch on device buffers, enqueued on `stream`.  Depths
  * are not validated on the device beyond clamping (a node with d1 + d2 > n

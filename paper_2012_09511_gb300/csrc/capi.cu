@@ -309,6 +309,30 @@ int pfsp_bound_batch_dev(const pfsp_instance *inst, int kind, int64_t num_nodes,
     return PFSP_OK;
 }
 
+// The device address of host buffer [h, h + bytes) when all of it is
+// page-locked memory that the current device maps as one contiguous range
+// (both ends checked), else NULL: pageable memory, or a range the checks
+// cannot vouch for, is never handed to a kernel.
+static char *mapped_host(void *h, size_t bytes) {
+    if (!h || bytes == 0) return nullptr;
+    int dev = 0, can_map = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, dev) != cudaSuccess || !can_map) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaPointerAttributes a0, a1;
+    if (cudaPointerGetAttributes(&a0, h) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, (const char *)h + (bytes - 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if ((char *)a1.devicePointer != (char *)a0.devicePointer + (bytes - 1)) return nullptr;
+    return (char *)a0.devicePointer;
+}
+
 // Host-pointer bounding, shared by both modes: the bound arrays (summary
 // NULL) or one summary per node (reduce mode, survivors below ub).
 static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const uint8_t *perm, const uint8_t *d1,
@@ -330,6 +354,17 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
     const size_t per_stream = (off_out2 + (want2 ? out_bytes : 0) + 255) / 256 * 256;
     int rc = ensure_scratch(inst, per_stream * nst);
     if (rc != PFSP_OK) return rc;
+    // The chunks after the first nst write their results straight into the
+    // caller's buffers when those are page-locked host memory that the GPU
+    // maps: the kernel's stores cross the host link while it runs, so no copy
+    // is left to wait for after the last kernel.  Pageable buffers, and the
+    // first chunks (whose results wait for the host's validation of the
+    // depths), go through device buffers and copies.
+    const size_t row_bytes = (size_t)2 * n * sizeof(int32_t);
+    char *z1 = want1 ? mapped_host(lb1_out, (size_t)num_nodes * row_bytes) : nullptr;
+    char *z2 = want2 ? mapped_host(lb2_out, (size_t)num_nodes * row_bytes) : nullptr;
+    char *zs = summary ? mapped_host(summary, (size_t)num_nodes * sizeof(pfsp_node_summary)) : nullptr;
+    const bool direct = nchunks > nst && (!want1 || z1) && (!want2 || z2) && (!summary || zs);
     cudaStream_t st[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> evs((size_t)nchunks * 2, nullptr);
     cudaError_t e = cudaSuccess;
@@ -356,7 +391,12 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
     auto front = [&](int64_t c) {
         const int q = (int)(c % nst);
         const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
-        const Bufs b = bufs(c);
+        Bufs b = bufs(c);
+        if (direct && c >= nst) {
+            b.o1 = want1 ? (int32_t *)(z1 + (size_t)off * row_bytes) : nullptr;
+            b.o2 = want2 ? (int32_t *)(z2 + (size_t)off * row_bytes) : nullptr;
+            b.os = summary ? (pfsp_node_summary *)(zs + (size_t)off * sizeof(pfsp_node_summary)) : nullptr;
+        }
         cudaError_t r = cudaMemcpyAsync(b.perm, perm + (size_t)off * n, (size_t)cn * n, cudaMemcpyHostToDevice, st[q]);
         if (r == cudaSuccess) r = cudaMemcpyAsync(b.d1, d1 + off, cn, cudaMemcpyHostToDevice, st[q]);
         if (r == cudaSuccess) r = cudaMemcpyAsync(b.d2, d2 + off, cn, cudaMemcpyHostToDevice, st[q]);
@@ -369,6 +409,7 @@ static int bound_host(pfsp_instance *inst, int kind, int64_t num_nodes, const ui
     };
     // the results of chunk c back to the caller's buffers
     auto back = [&](int64_t c) {
+        if (direct && c >= nst) return cudaSuccess;  // written in place by the kernel
         const int q = (int)(c % nst);
         const int64_t off = c * chunk, cn = std::min<int64_t>(chunk, num_nodes - off);
         const Bufs b = bufs(c);

@@ -199,6 +199,56 @@ def test_host_entry_point_chunks_match_one_launch(pf):
     assert none2 is None and (lb1_only == h1).all()
 
 
+def test_host_entry_point_into_pinned_buffers(pf):
+    # with page-locked output buffers, the chunks after the first two write
+    # their results in place from the kernel instead of through device
+    # buffers and copies: every value must still equal one launch of the
+    # device entry point (both modes, two calls in a row), and a batch refused
+    # for an invalid depth must leave the pinned buffers as they were
+    import torch
+    n, m = 14, 6
+    N = 5 * 262144 + 999
+    p = inputs.make_instance(n, m, 34)
+    perm, d1, d2 = inputs.random_nodes(n, N, seed=6, dmax=6)
+    inst = pf.pfsp_load_instance(p)
+    dev = torch.device("cuda:0")
+    o1 = torch.empty((N, 2, n), dtype=torch.int32, device=dev)
+    o2 = torch.empty_like(o1)
+    tp, t1, t2 = (torch.from_numpy(x).to(dev) for x in (perm, d1, d2))
+    pf.pfsp_bound_batch_dev(inst, 3, N, tp.data_ptr(), t1.data_ptr(), t2.data_ptr(), o1.data_ptr(), o2.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    w1, w2 = o1.cpu().numpy(), o2.cpu().numpy()
+    h1 = torch.full((N, 2, n), -7, dtype=torch.int32).pin_memory()
+    h2 = torch.full((N, 2, n), -7, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        pf.pfsp_bound_batch(inst, 3, perm, d1, d2, lb1_out=h1.numpy(), lb2_out=h2.numpy())
+        assert (h1.numpy() == w1).all() and (h2.numpy() == w2).all()
+        h1.fill_(-7)
+        h2.fill_(-7)
+    _, only2 = pf.pfsp_bound_batch(inst, pf.PFSP_LB2, perm, d1, d2, lb2_out=h2.numpy())
+    assert (only2 == w2).all()
+    h2.fill_(-7)
+    for bad in (N - 1, 5):
+        e1 = d1.copy()
+        e1[bad] = n  # d1 + d2 > n
+        e2 = d2.copy()
+        e2[bad] = 1
+        with pytest.raises(pf.PfspError) as e:
+            pf.pfsp_bound_batch(inst, 3, perm, e1, e2, lb1_out=h1.numpy(), lb2_out=h2.numpy())
+        assert e.value.code == pf.PFSP_ERR_INVALID
+        assert (h1.numpy() == -7).all() and (h2.numpy() == -7).all()
+    # reduce mode: summaries in place against the copy path on pageable memory
+    ub = int(np.median(w2[w2 >= 0]))
+    want = pf.pfsp_bound_reduce(inst, pf.PFSP_LB2, perm, d1, d2, ub)
+    raw = torch.zeros(N * pf.SUMMARY_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    hs = raw.numpy().view(pf.SUMMARY_DTYPE)
+    for _ in range(2):
+        got = pf.pfsp_bound_reduce(inst, pf.PFSP_LB2, perm, d1, d2, ub, out=hs)
+        assert got.tobytes() == want.tobytes()
+        raw.zero_()
+
+
 @pytest.mark.parametrize("n,m,subset", [
     (16, 20, "adjacent"), (16, 20, "random40"), (14, 20, "random33"), (12, 7, "adjacent"), (12, 7, "random5"),
     (35, 10, "random20"),
